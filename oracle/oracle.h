@@ -1,0 +1,134 @@
+/*
+ * FP64 CPU oracle for segment-search confocal UWB imaging
+ * (Ettefagh, Moghaddam, Vahidian, "A Novel Low-Complexity Framework in
+ * Ultra-Wideband Imaging for Breast Cancer Detection", arXiv:1709.02549).
+ *
+ * TEST INFRASTRUCTURE. This library exists to check the CUDA path. Only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load it;
+ * the product path never calls it and shares no code with it.
+ *
+ * Every function is a plain loop over the definition it cites, in double
+ * precision, with no blocking, fusion or reordering beyond what the definition
+ * states. OpenMP (when available) only splits independent focal points across
+ * threads; each focal point's arithmetic is the same in any thread count.
+ */
+#ifndef UWB_ORACLE_H
+#define UWB_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_ITERS 32
+
+/* beamformers */
+#define ORC_DAS 0
+#define ORC_DMAS 1          /* pairwise products, Section II.B; literal i<j loop */
+
+/* decimation modes, Section III "Spatial Decimation" */
+#define ORC_DECIM_MANUAL 0
+#define ORC_DECIM_AUTO 1
+
+/* decision metrics, Section III "ROI Selection" */
+#define ORC_METRIC_HYBRID 0   /* Eq. 5 */
+#define ORC_METRIC_MEAN 1
+#define ORC_METRIC_VARIANCE 2
+#define ORC_METRIC_HYBRID_UNCLIPPED 3 /* Eq. 5 exactly as printed */
+
+/* stop reasons */
+#define ORC_STOP_NONE 0
+#define ORC_STOP_METRIC 1     /* Eq. 6-7 rule failed */
+#define ORC_STOP_MINSIZE 2    /* no child segment left to choose */
+#define ORC_STOP_CAP 3        /* iteration cap */
+#define ORC_STOP_NO_TARGET 4  /* all decimated energies are zero */
+
+/* status */
+#define ORC_OK 0
+#define ORC_ERR_ARG -1
+#define ORC_ERR_NONFINITE -4
+
+/* Focal-point lattice: point idx (per axis) sits at origin + idx * pitch. */
+typedef struct {
+  int dim;
+  int n[3];
+  double origin[3];
+  double pitch[3];
+} orc_grid;
+
+typedef struct {
+  int mode;                   /* ORC_DECIM_MANUAL | ORC_DECIM_AUTO */
+  int decimation;             /* manual factor D >= 1 */
+  double min_tumor_diameter;  /* auto mode: smallest tumour to detect [m] */
+  int metric;                 /* ORC_METRIC_* */
+  int min_segment;            /* smallest child side, in full-resolution points */
+  int frame_num, frame_den;   /* sliding-frame fraction of the child side */
+  int max_iters;              /* 0 = ceil(log2(max grid side)) + 2 */
+} orc_rule;
+
+typedef struct {
+  int status;
+  int iters;                  /* accepted segmentations */
+  int n_logged;               /* iterations performed (the last may be rejected) */
+  int stop_reason;
+  int decim;                  /* D */
+  int offset[3];              /* decimated lattice offset per axis */
+  int dcount[3];              /* decimated lattice points per axis */
+  int roi_lo[3], roi_hi[3];   /* final region, full-resolution index box [lo, hi) */
+  int loc_idx[3];             /* argmax of the final image, -1 if none */
+  double loc_xyz[3];
+  double peak;                /* image value at loc */
+  double profile_max;         /* max of the decimated energies */
+  long long points_evaluated; /* decimated points + final-region points */
+  /* per performed iteration */
+  int child[ORC_MAX_ITERS];
+  int n_children[ORC_MAX_ITERS];     /* children that survived the filters */
+  int box_lo[ORC_MAX_ITERS][3];
+  int box_hi[ORC_MAX_ITERS][3];
+  double metric_top[ORC_MAX_ITERS];
+  double metric_gap[ORC_MAX_ITERS];  /* (top - runner-up) / |top|, 1e300 if alone */
+  double between[ORC_MAX_ITERS];     /* B_i, Eq. 7 */
+  double within[ORC_MAX_ITERS];      /* W_i, Eq. 6 */
+  double stop_margin[ORC_MAX_ITERS]; /* robustness of the continue/stop outcome */
+} orc_result;
+
+/* Image over a box lattice of the focal grid (Eq. 1 with tau = 2|r-a|/v,
+ * Eq. 3 for DAS, Section II.B for DMAS). Lattice point (kx,ky,kz) is grid
+ * index lo + step * k; out is [cnt_z][cnt_y][cnt_x]. */
+int orc_image(const float* traces, int M, int N, const float* antennas,
+              const orc_grid* g, double v, double fs, int window, int beamformer,
+              const int lo[3], const int step[3], const int cnt[3], double* out);
+
+/* Spatial decimation factor, Section III (manual / automatic modes) and the
+ * worked example of Section IV. */
+int orc_decimation(const orc_rule* r, const orc_grid* g);
+
+/* Offset of the decimated lattice along an axis of n points. */
+int orc_lattice_offset(int n, int D);
+
+/* ROI selection loop on a normalised decimated profile e[kz][ky][kx]
+ * (Section III "ROI Selection", Eq. 5-7, sliding framing). Fills the
+ * selection fields of res (not loc / peak / points_evaluated). */
+int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
+               orc_result* res);
+
+/* Whole framework: decimated profile, normalisation, selection, final
+ * full-resolution imaging of the region and its argmax (Section III). */
+int orc_localize(const float* traces, int M, int N, const float* antennas,
+                 const orc_grid* g, double v, double fs, int window, int beamformer,
+                 const orc_rule* r, orc_result* res);
+
+/* Eq. 5 hybrid metric for one candidate, weight clipped to [0, 1], and the
+ * printed formula without the clip (exposed for the tests). */
+double orc_hybrid_metric(double mean_i, double var_i, double var_prev);
+double orc_hybrid_metric_unclipped(double mean_i, double var_i, double var_prev);
+
+/* Eq. 6 / Eq. 7 for two scalar classes a and b (exposed for the tests). */
+void orc_scatter(const double* a, int na, const double* b, int nb,
+                 double* within, double* between);
+
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

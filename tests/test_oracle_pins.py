@@ -1,0 +1,377 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+worked example, closed forms, identities between different oracle calls,
+invariances and hand-worked cases stored under tests/golden/.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import phantom
+from conftest import read_golden
+
+V, FS = 1.0e8, 50.0e9          # 1000 samples per metre of one-way path
+RNG = np.random.default_rng(1234)
+
+
+def line_grid(x0, n=1, pitch=1e-3):
+    """A 2-D grid whose point (0, 0) sits at (x0, 0)."""
+    return {"dim": 2, "n": [n, 1, 1], "origin": [x0, 0.0, 0.0], "pitch": [pitch, 1.0, 1.0]}
+
+
+def one_point(traces, ants, x, window, bf=oracle.DAS):
+    return oracle.image(traces, ants, line_grid(x), V, FS, window, bf)[0, 0, 0]
+
+
+# ------------------------------------------------------------------ image (Eq. 1, 3)
+
+def test_single_antenna_integer_delay_reads_the_stored_sample():
+    # antenna at the origin, focal point 37 mm away: round trip = 74 mm = 37 samples
+    tr = RNG.standard_normal((1, 128)).astype(np.float32)
+    ant = np.zeros((1, 3), np.float32)
+    got = one_point(tr, ant, 0.037, window=1)
+    assert got == pytest.approx(float(tr[0, 37]) ** 2, rel=1e-10)
+
+
+def test_single_antenna_fractional_delay_interpolates_linearly():
+    # a linear trace is reproduced exactly by linear interpolation: Y(u) = a + b u
+    a, b = 0.25, -0.01
+    n = np.arange(128)
+    tr = (a + b * n).astype(np.float32)[None, :]
+    ant = np.zeros((1, 3), np.float32)
+    u = 37.25                                  # 37.25 mm -> 37.25 samples
+    got = one_point(tr, ant, u / 1000.0, window=1)
+    expect = (float(np.float32(a)) + b * u) ** 2
+    assert got == pytest.approx(expect, rel=1e-6)
+
+
+def test_window_is_centred_on_the_delay():
+    # W = 20 samples centred on u (offset -10): for a linear trace
+    # I = sum_{k=0}^{19} (a + b (u - 10 + k))^2
+    a, b = 1.0, 0.5
+    tr = (a + b * np.arange(256)).astype(np.float32)[None, :]
+    ant = np.zeros((1, 3), np.float32)
+    u = 80.5
+    got = one_point(tr, ant, u / 1000.0, window=20)
+    expect = sum((a + b * (u - 10 + k)) ** 2 for k in range(20))
+    assert got == pytest.approx(expect, rel=1e-9)
+
+
+def test_samples_outside_the_trace_are_zero():
+    tr = RNG.standard_normal((1, 40)).astype(np.float32)
+    ant = np.zeros((1, 3), np.float32)
+    # u = 3: window covers t = -7 .. 12, samples below 0 are zero
+    got = one_point(tr, ant, 0.003, window=20)
+    assert got == pytest.approx(float(np.sum(tr[0, 0:13].astype(np.float64) ** 2)), rel=1e-9)
+    # u = 35: window t = 25 .. 44, samples from 40 on are zero
+    got = one_point(tr, ant, 0.035, window=20)
+    assert got == pytest.approx(float(np.sum(tr[0, 25:40].astype(np.float64) ** 2)), rel=1e-9)
+
+
+def _random_scene(M, N=256, seed=0):
+    rng = np.random.default_rng(seed)
+    tr = rng.standard_normal((M, N)).astype(np.float32)
+    ang = rng.uniform(0, 2 * np.pi, M)
+    ants = np.stack([0.06 * np.cos(ang), 0.06 * np.sin(ang), np.zeros(M)], 1).astype(np.float32)
+    grid = {"dim": 2, "n": [7, 5, 1], "origin": [-0.01, -0.012, 0.0],
+            "pitch": [0.0031, 0.0047, 1.0]}
+    return tr, ants, grid
+
+
+@pytest.mark.parametrize("M", [2, 3, 5, 6])
+def test_dmas_single_sample_equals_pair_identity_of_das(M):
+    # W = 1: DMAS = (sum_{i<j} x_i x_j)^2 = (((sum x)^2 - sum x^2) / 2)^2, where
+    # (sum x)^2 is the all-antenna DAS image and x_i^2 the one-antenna DAS image.
+    tr, ants, grid = _random_scene(M, seed=M)
+    dmas = oracle.image(tr, ants, grid, V, FS, 1, oracle.DMAS)
+    das_all = oracle.image(tr, ants, grid, V, FS, 1, oracle.DAS)
+    das_each = sum(oracle.image(tr[i:i + 1], ants[i:i + 1], grid, V, FS, 1, oracle.DAS)
+                   for i in range(M))
+    expect = ((das_all - das_each) / 2.0) ** 2
+    np.testing.assert_allclose(dmas, expect, rtol=1e-9, atol=1e-12 * expect.max())
+
+
+def test_dmas_two_antennas_is_product_of_single_antenna_energies():
+    # M = 2, W = 1: (x_1 x_2)^2 = x_1^2 * x_2^2
+    tr, ants, grid = _random_scene(2, seed=11)
+    dmas = oracle.image(tr, ants, grid, V, FS, 1, oracle.DMAS)
+    e1 = oracle.image(tr[:1], ants[:1], grid, V, FS, 1, oracle.DAS)
+    e2 = oracle.image(tr[1:], ants[1:], grid, V, FS, 1, oracle.DAS)
+    np.testing.assert_allclose(dmas, e1 * e2, rtol=1e-10)
+
+
+def _shift(tr, s):
+    """Y'[n] = Y[n + s], zero where n + s falls outside the trace."""
+    out = np.zeros_like(tr)
+    n = tr.shape[1]
+    if s >= 0:
+        out[:, :n - s] = tr[:, s:]
+    else:
+        out[:, -s:] = tr[:, :n + s]
+    return out
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+@pytest.mark.parametrize("W", [2, 5, 20])
+def test_window_sum_equals_sum_of_shifted_single_samples(bf, W):
+    # x_i(k) = Y_i(u_i - h + k) = Y'_i(u_i) with Y' shifted by k - h, so the
+    # W-sample image is the sum of W one-sample images of shifted traces.
+    tr, ants, grid = _random_scene(4, seed=W)
+    full = oracle.image(tr, ants, grid, V, FS, W, bf)
+    h = W // 2
+    parts = sum(oracle.image(_shift(tr, k - h), ants, grid, V, FS, 1, bf) for k in range(W))
+    np.testing.assert_allclose(full, parts, rtol=1e-9)
+
+
+@pytest.mark.parametrize("bf,power", [(oracle.DAS, 2), (oracle.DMAS, 4)])
+def test_trace_scaling(bf, power):
+    tr, ants, grid = _random_scene(5, seed=3)
+    base = oracle.image(tr, ants, grid, V, FS, 6, bf)
+    scaled = oracle.image(tr * np.float32(4.0), ants, grid, V, FS, 6, bf)
+    np.testing.assert_allclose(scaled, base * 4.0 ** power, rtol=1e-10)
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_antenna_permutation_invariance(bf):
+    tr, ants, grid = _random_scene(6, seed=5)
+    perm = np.random.default_rng(9).permutation(6)
+    a = oracle.image(tr, ants, grid, V, FS, 4, bf)
+    b = oracle.image(tr[perm], ants[perm], grid, V, FS, 4, bf)
+    np.testing.assert_allclose(a, b, rtol=1e-10)
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_noiseless_point_scatterer_peaks_at_its_own_pixel(bf):
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], snr_db=None)
+    g = cfg.grid()
+    rng = np.random.default_rng(77)
+    for _ in range(4):
+        ix, iy = rng.integers(8, 56, size=2)
+        p = [g["origin"][0] + ix * g["pitch"][0], g["origin"][1] + iy * g["pitch"][1], 0.0]
+        tr = phantom.point_scatterer_traces(cfg, [p], [1.0])
+        img = oracle.image(tr, phantom.antenna_positions(cfg).astype(np.float32), g,
+                           cfg.v, cfg.fs, cfg.window, bf)
+        k = int(np.argmax(img))
+        assert (k % 64, k // 64) == (ix, iy)
+
+
+# ------------------------------------------------------------- decimation (Section III-IV)
+
+def test_automatic_decimation_worked_example():
+    gold = read_golden("decimation_worked_example.txt")
+    d = float(gold["min_tumor_diameter_m"][0])
+    res = float(gold["resolution_m"][0])
+    grid = {"dim": 2, "n": [100, 100, 1], "origin": [0, 0, 0], "pitch": [res, res, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_AUTO, min_tumor_diameter=d)
+    assert oracle.decimation(rule, grid) == int(gold["decimation"][0])
+
+
+def test_manual_decimation_is_taken_as_given():
+    grid = {"dim": 2, "n": [100, 100, 1], "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    for D in (1, 3, 13):
+        assert oracle.decimation(oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=D),
+                                 grid) == D
+
+
+@pytest.mark.parametrize("n,D", [(64, 4), (512, 30), (256, 18), (10, 3), (7, 7), (5, 1)])
+def test_decimated_lattice_is_centred(n, D):
+    o = oracle.lattice_offset(n, D)
+    last = o + D * ((n - 1 - o) // D)
+    assert 0 <= o < D and last <= n - 1 and n - 1 - last - o in (0, 1)
+
+
+# ------------------------------------------------------------- Eq. 5, Eq. 6-7
+
+def test_hybrid_metric_limits_stated_in_the_paper():
+    mu, var = 0.31, 0.07
+    # equal variances in consecutive steps: the mean dominates (is the metric)
+    assert oracle.hybrid_metric(mu, var, var) == pytest.approx(mu, rel=1e-15)
+    assert oracle.hybrid_metric_unclipped(mu, var, var) == pytest.approx(mu, rel=1e-15)
+    # a flat previous region against a dispersed one: the variance dominates
+    assert oracle.hybrid_metric(mu, var, 0.0) == pytest.approx(var, rel=1e-15)
+    assert oracle.hybrid_metric_unclipped(mu, var, 0.0) == pytest.approx(var, rel=1e-15)
+    # a weight halfway: the midpoint of mean and variance
+    assert oracle.hybrid_metric(mu, var, var / 2) == pytest.approx((mu + var) / 2, rel=1e-14)
+    # a child flatter than its parent: clipped weight 0 -> the mean;
+    # the printed formula extrapolates beyond both terms
+    assert oracle.hybrid_metric(mu, var, 3 * var) == pytest.approx(mu, rel=1e-15)
+    assert oracle.hybrid_metric_unclipped(mu, var, 3 * var) > max(mu, var)
+
+
+def test_scatter_hand_example():
+    gold = read_golden("scatter_hand_example.txt")
+    a = [float(x) for x in gold["a"]]
+    b = [float(x) for x in gold["b"]]
+    w, bb = oracle.scatter(a, b)
+    assert w == pytest.approx(float(gold["within"][0]), rel=1e-15)
+    assert bb == pytest.approx(float(gold["between"][0]), rel=1e-15)
+
+
+def test_scatter_decomposes_total_scatter():
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        a = rng.random(rng.integers(1, 40))
+        b = rng.random(rng.integers(1, 40)) * 3
+        w, bb = oracle.scatter(a, b)
+        pooled = np.concatenate([a, b])
+        assert w + bb == pytest.approx(float(np.sum((pooled - pooled.mean()) ** 2)), rel=1e-12)
+        w2, b2 = oracle.scatter(a, a + 0.0)
+        assert b2 == pytest.approx(0.0, abs=1e-14)
+
+
+# ------------------------------------------------------------- selection loop (Section III)
+
+def _spike_profile(n, at, D=1):
+    e = np.zeros((1, n[1], n[0]))
+    e[0, at[1], at[0]] = 1.0
+    return e
+
+
+def test_selection_hand_worked_spike():
+    gold = read_golden("select_spike_16x16.txt")
+    n = [int(x) for x in gold["grid"]] + [1]
+    at = [int(x) for x in gold["spike"]]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1,
+                            min_segment=int(gold["min_segment"][0]))
+    r = oracle.select(_spike_profile(n, at), grid, rule, 1)
+    assert r["child"] == [int(x) for x in gold["children"]]
+    assert r["box_lo"][0][:2] == [int(x) for x in gold["box1_lo"]]
+    assert r["box_hi"][0][:2] == [int(x) for x in gold["box1_hi"]]
+    assert r["box_lo"][1][:2] == [int(x) for x in gold["box2_lo"]]
+    assert r["box_hi"][1][:2] == [int(x) for x in gold["box2_hi"]]
+    assert r["roi_lo"][:2] == [int(x) for x in gold["roi_lo"]]
+    assert r["roi_hi"][:2] == [int(x) for x in gold["roi_hi"]]
+    assert r["iters"] == int(gold["iters"][0])
+    assert r["n_logged"] == int(gold["n_logged"][0])
+    assert r["stop_reason"] == int(gold["stop_reason"][0])
+    assert r["within"][0] == pytest.approx(float(gold["within1"][0]), rel=1e-12)
+    assert r["between"][0] == pytest.approx(float(gold["between1"][0]), rel=1e-6)
+    assert r["between"][1] == pytest.approx(float(gold["between2"][0]), rel=1e-6)
+
+
+ALL_METRICS = [oracle.METRIC_HYBRID, oracle.METRIC_MEAN, oracle.METRIC_VARIANCE,
+               oracle.METRIC_HYBRID_UNCLIPPED]
+
+
+@pytest.mark.parametrize("metric", ALL_METRICS)
+def test_selection_keeps_a_lone_spike(metric):
+    # zero energy everywhere but one point: only the child holding it has a
+    # non-zero mean and variance, so every metric must keep it
+    n = [64, 64, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, metric=metric,
+                            min_segment=2, max_iters=12)
+    rng = np.random.default_rng(8)
+    for _ in range(6):
+        at = rng.integers(0, 64, size=2)
+        r = oracle.select(_spike_profile(n, at), grid, rule, 1)
+        assert r["n_logged"] >= 1
+        for lo, hi in zip(r["box_lo"], r["box_hi"]):
+            assert lo[0] <= at[0] < hi[0] and lo[1] <= at[1] < hi[1]
+        assert r["roi_lo"][0] <= at[0] < r["roi_hi"][0]
+        assert r["roi_lo"][1] <= at[1] < r["roi_hi"][1]
+
+
+@pytest.mark.parametrize("metric", ALL_METRICS)
+def test_selection_mirrors_with_the_profile(metric):
+    # reflecting the energies in x reflects every choice (child bit 0 flips),
+    # as long as every split is symmetric: the first two regions have even sides
+    n = [64, 64, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, metric=metric,
+                            max_iters=2)
+    rng = np.random.default_rng(18)
+    for _ in range(6):
+        base = rng.random((1, 64, 64)) ** 4
+        r = oracle.select(base, grid, rule, 1)
+        rm = oracle.select(base[:, :, ::-1].copy(), grid, rule, 1)
+        assert [c ^ 1 for c in r["child"]] == rm["child"]
+        assert r["stop_reason"] == rm["stop_reason"] and r["iters"] == rm["iters"]
+        for lo, hi, lom, him in zip(r["box_lo"], r["box_hi"], rm["box_lo"], rm["box_hi"]):
+            assert (lom[0], him[0]) == (64 - hi[0], 64 - lo[0])
+            assert (lom[1], him[1]) == (lo[1], hi[1])
+
+
+def test_selection_stops_when_no_child_is_large_enough():
+    n = [8, 8, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, min_segment=5)
+    r = oracle.select(_spike_profile(n, [2, 3]), grid, rule, 1)
+    assert r["stop_reason"] == oracle.STOP_MINSIZE and r["iters"] == 0
+    assert r["roi_lo"][:2] == [0, 0] and r["roi_hi"][:2] == [8, 8]
+
+
+def test_selection_iteration_cap():
+    n = [64, 64, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    e = np.zeros((1, 64, 64))
+    e[0, 30, 40] = 1.0
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, max_iters=1)
+    r = oracle.select(e, grid, rule, 1)
+    assert r["stop_reason"] == oracle.STOP_CAP and r["iters"] == 1
+    assert r["roi_lo"] == r["box_lo"][0] and r["roi_hi"] == r["box_hi"][0]
+
+
+# ------------------------------------------------------------- whole method
+
+def test_scaling_the_traces_changes_no_decision():
+    cfg = phantom.CONFIGS["das2d_64"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 3)
+    g = cfg.grid()
+    a = oracle.localize(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DMAS)
+    b = oracle.localize(sc["traces"] * np.float32(8.0), sc["antennas"], g, cfg.v, cfg.fs,
+                        cfg.window, oracle.DMAS)
+    for key in ("child", "box_lo", "box_hi", "roi_lo", "roi_hi", "loc_idx", "iters",
+                "stop_reason"):
+        assert a[key] == b[key]
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_no_accuracy_loss_on_noiseless_single_scatterers(bf):
+    # the paper's claim: the framework finds the location the full-resolution
+    # beamformer finds
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], snr_db=None)
+    g = cfg.grid()
+    for s in range(8):
+        sc = phantom.make_scan(cfg, phantom.BASE_SEED + 100 + s)
+        full = oracle.image(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, bf)
+        k = int(np.argmax(full))
+        r = oracle.localize(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, bf)
+        assert r["loc_idx"][:2] == [k % 64, k // 64]
+        assert r["points_evaluated"] < 64 * 64
+
+
+def test_all_zero_traces_report_no_target():
+    cfg = phantom.CONFIGS["das2d_64"]
+    tr = np.zeros((cfg.n_antennas, cfg.n_samples), np.float32)
+    r = oracle.localize(tr, phantom.antenna_positions(cfg), cfg.grid(), cfg.v, cfg.fs,
+                        cfg.window, oracle.DAS)
+    assert r["status"] == 0 and r["stop_reason"] == oracle.STOP_NO_TARGET
+    assert r["loc_idx"] == [-1, -1, -1]
+
+
+def test_nonfinite_trace_is_reported():
+    cfg = phantom.CONFIGS["das2d_64"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED)
+    tr = sc["traces"].copy()
+    tr[:, :] = np.nan
+    r = oracle.localize(tr, sc["antennas"], cfg.grid(), cfg.v, cfg.fs, cfg.window, oracle.DAS)
+    assert r["status"] == -4
+
+
+def test_three_d_localisation_runs_on_a_small_cube():
+    cfg = phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(24, 24, 24),
+                               n_antennas=12, n_samples=1024, snr_db=None, n_clutter=0,
+                               n_tumors=(1, 1), tumor_amp=(1.0, 1.0))
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED)
+    g = cfg.grid()
+    full = oracle.image(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DAS)
+    k = int(np.argmax(full))
+    r = oracle.localize(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DAS,
+                        oracle.make_rule(min_segment=2))
+    assert r["loc_idx"] == [k % 24, (k // 24) % 24, k // 576]
+    assert all(0 <= c < 8 for c in r["child"])
