@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Localised scans/s of the segment-search framework (arXiv:1709.02549,
+Section III) on GB300, against full-resolution GPU imaging of the same scans.
+
+One step = one call of ``uwb_localize_batch`` over a batch of synthetic scans
+resident in HBM: decimated energy profile, device-resident ROI selection,
+final full-resolution imaging of each ROI and its argmax (5 kernel launches).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+instead (the reference arm of this method: the plain implementation written
+from the paper), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import pathlib
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import phantom  # noqa: E402
+
+METRIC = "localised scans/s (DAS/DMAS, 1 GB300) vs full-res GPU image at same loc. error"
+UNIT = "scans/s"
+BEAMFORMERS = {"das": 0, "dmas": 1, "literal": 2}
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+# Derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz max SM clock.
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+
+# DRAM traffic of the final-region kernel per launch, from an ncu capture of the
+# file versions whose hash is stored alongside (None until captured / after a
+# kernel change).
+NCU_TRAFFIC = {"sha": None, "bytes_per_point": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("image_common.cuh", "image_literal.cu", "image_das.cu", "image_dmas.cu"):
+        h.update((ROOT / "paper_1709_02549_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def flops_per_point(bf: int, M: int, W: int) -> float:
+    """Algorithmic FLOPs of one focal point (see the kernel roofline notes):
+    per antenna 10 for the delay (3 sub, 3 mul-add, sqrt, scale) and 3 per
+    window sample for the interpolation; then the combine: DAS W*M adds,
+    identity-DMAS W*(3M + 3), literal DMAS W*M(M-1) (M(M-1)/2 multiply-adds per
+    sample); then 2W to square and sum over the window."""
+    per_antenna = M * (10 + 3 * W)
+    if bf == 0:
+        combine = W * M
+    elif bf == 1:
+        combine = W * (3 * M + 3)
+    else:
+        combine = W * M * (M - 1)
+    return float(per_antenna + combine + 2 * W)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_first_scan(rank: int, batch: int) -> int:
+    """Scans of rank r: seeds base + r*batch ... (independent scans, no exchange)."""
+    return rank * batch
+
+
+def workload_name(cfg, bf_name, batch):
+    g = cfg.grid_n
+    return (f"{cfg.name}: {g[0]}x{g[1]}" + (f"x{g[2]}" if cfg.dim == 3 else "") +
+            f" grid over {cfg.extent * 100:.0f} cm, {cfg.n_antennas} antennas "
+            f"({cfg.array}, r={cfg.radius * 100:.0f} cm), {cfg.n_samples} samples/trace at "
+            f"{cfg.fs / 1e9:.0f} GS/s, W={cfg.window}, {cfg.n_clutter} clutter, "
+            f"{cfg.snr_db} dB SNR; {bf_name} beamformer; {batch} scans per GPU per step")
+
+
+def nearest_error_mm(xyz, tumors):
+    if tumors is None or len(tumors) == 0:
+        return float("nan")
+    return float(np.min(np.linalg.norm(np.asarray(tumors) - np.asarray(xyz), axis=1)) * 1e3)
+
+
+def run_reference(args, cfg, bf):
+    """FP64 C oracle on the host cores, each step a bounded sample of scans."""
+    import oracle
+    oracle.build()
+    grid = cfg.grid()
+    obf = oracle.DAS if bf == 0 else oracle.DMAS
+    rule = oracle.make_rule()
+    per_step = args.ref_scans_per_step
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in range(per_step)]
+    for _ in range(args.warmup):
+        for sc in scans:
+            oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf,
+                            rule)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sc in scans:
+            oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf,
+                            rule)
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    cores = oracle.num_threads()
+    sample = f"{per_step} scans per step of the same workload, oracle localisation (FP64)"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(cfg, args.beamformer, per_step),
+                   "batch_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline(cfg, bf, seconds):
+    """The oracle as it stands, on the host cores: scans localised until about
+    `seconds` of oracle time (scan synthesis not timed)."""
+    import oracle
+    oracle.build()
+    grid = cfg.grid()
+    obf = oracle.DAS if bf == 0 else oracle.DMAS
+    rule = oracle.make_rule()
+    n, busy = 0, 0.0
+    while busy < seconds:
+        sc = phantom.make_scan(cfg, phantom.BASE_SEED + 100000 + n)
+        t1 = time.perf_counter()
+        oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf, rule)
+        busy += time.perf_counter() - t1
+        n += 1
+    return {"value": n / busy, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} scans of the same workload localised by the FP64 oracle "
+                      f"({busy:.1f} s of oracle time)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="uwb", choices=["uwb", "reference"])
+    ap.add_argument("--config", default="dmas2d_512", choices=sorted(phantom.CONFIGS))
+    ap.add_argument("--beamformer", default="literal", choices=sorted(BEAMFORMERS))
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--fullres-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-scans-per-step", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    cfg = phantom.CONFIGS[args.config]
+    bf = BEAMFORMERS[args.beamformer]
+    world, rank, local = dist_setup()
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, cfg, bf)), flush=True)
+        return
+
+    import torch
+    import paper_1709_02549_gb300 as uwb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    B = args.batch
+    batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
+    grid = cfg.grid()
+    M, N = cfg.n_antennas, cfg.n_samples
+    traces_host = torch.from_numpy(batch["traces"]).pin_memory()
+    traces = traces_host.to("cuda")
+    ants = torch.from_numpy(batch["antennas"]).to("cuda")
+    rule = uwb.uwb_default_rule()
+    ws = torch.empty(uwb.uwb_localize_workspace(B, M, N, grid, bf, rule), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        uwb.uwb_localize_batch(traces, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule, ws, out,
+                               None, stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each (flush not timed) ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    uwb.uwb_phase_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    calls, phase_ms = uwb.uwb_phase_times()
+    uwb.uwb_phase_timing(False)
+    clock_info = clocks.stop()
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    res = uwb.results_from_device(out)
+    status_ok = bool(np.all(res["status"] == 0))
+    roi_points = np.prod(res["roi_hi"] - res["roi_lo"], axis=1).astype(np.float64)
+    pts_eval = res["points_evaluated"].astype(np.float64)
+    fpp = flops_per_point(bf, M, cfg.window)
+    final_ms = phase_ms[2] / max(calls, 1)
+    final_flops = float(roi_points.sum()) * fpp
+    achieved_tflops = final_flops / (final_ms / 1e3) / 1e12 if final_ms > 0 else None
+    sha = kernel_sha()
+    traffic = None
+    if NCU_TRAFFIC["sha"] == sha and NCU_TRAFFIC["bytes_per_point"]:
+        traffic = NCU_TRAFFIC["bytes_per_point"] * float(roi_points.sum())
+    roofline = {
+        "bound": "alu",
+        "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (achieved_tflops / FP32_PEAK_TFLOPS) if achieved_tflops else None,
+        "traffic": traffic,
+        "kernel": f"k_image<{['DAS', 'DMAS', 'DMAS_LITERAL'][bf]}> final-region pass",
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
+        "launch_ms": final_ms,
+        "flops_per_launch": final_flops,
+        "phase_ms_per_step": [p / max(calls, 1) for p in phase_ms],
+        "kernel_sha": sha,
+    }
+
+    # ---- full-resolution GPU images of the same scans (same beamformer) ----
+    P = int(np.prod(grid["n"]))
+    img = torch.empty(B, P, device="cuda")
+    peak = torch.empty(B, dtype=torch.int64, device="cuda")
+    uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img, peak)
+    torch.cuda.synchronize()
+    fr_ms = 0.0
+    for _ in range(args.fullres_steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img, peak)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        fr_ms += s0.elapsed_time(s1)
+    fr_value = B * args.fullres_steps / (fr_ms / 1e3)
+    pk = peak.cpu().numpy()
+    del img
+    gx, gy = grid["n"][0], grid["n"][1]
+    full_idx = np.stack([pk % gx, (pk // gx) % gy, pk // (gx * gy)], 1)
+    agree = float(np.mean(np.all(full_idx == res["loc_idx"], axis=1)))
+    err_fw, err_fr = [], []
+    for s in range(B):
+        xyz_fr = [grid["origin"][a] + full_idx[s, a] * grid["pitch"][a] for a in range(3)]
+        err_fw.append(nearest_error_mm(res["loc_xyz"][s], batch["tumors"][s]))
+        err_fr.append(nearest_error_mm(xyz_fr, batch["tumors"][s]))
+
+    # ---- end to end through the public API: H2D of traces, localise, D2H ----
+    out_host = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        traces.copy_(traces_host, non_blocking=True)
+        step()
+        out_host.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        traces.copy_(traces_host, non_blocking=True)
+        step()
+        out_host.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * B * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(traces.numel() * 4),
+           "d2h_bytes_per_step": int(out.numel())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg, bf, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, args.beamformer, B),
+                       "batch_per_gpu": B, "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written before every timed step (not timed)",
+                       "decision_rule": "auto decimation (1 cm), hybrid Eq. 5 metric, "
+                                        "min_segment 4, framing 1/4"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clock_info,
+            "gpu_launches": 5 * args.steps,
+            "fullres": {"value": fr_value, "unit": UNIT, "ms_per_step": fr_ms / args.fullres_steps,
+                        "loc_agreement": agree},
+            "speedup_vs_fullres": value / fr_value,
+            "loc_error_mm": {"framework_mean": float(np.nanmean(err_fw)),
+                             "fullres_mean": float(np.nanmean(err_fr))},
+            "points_per_scan": {"mean": float(pts_eval.mean()), "full": P},
+            "status_ok": status_ok,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * uwb.h -- C ABI of the GB300 segment-search confocal imaging library.
+ *
+ * Method: Ettefagh, Moghaddam, Vahidian, "A Novel Low-Complexity Framework in
+ * Ultra-Wideband Imaging for Breast Cancer Detection" (arXiv:1709.02549):
+ * monostatic confocal DAS (Section II.A, Eq. 1 and Eq. 3) and DMAS
+ * (Section II.B) images, evaluated only where the coarse-to-fine segment
+ * search of Section III asks for them (spatial decimation, ROI selection with
+ * the Eq. 5 metric and the Eq. 6-7 stopping rule, sliding framing, final
+ * full-resolution imaging of the ROI).
+ *
+ * Conventions shared by every entry point
+ *  - Every array argument is a DEVICE pointer owned by the caller; the library
+ *    never frees or keeps it. uwb_grid and uwb_rule are HOST structs, read
+ *    during the call only.
+ *  - traces: float32, [batch][M][N] row-major (scan, antenna, sample); sample n
+ *    of antenna i is the echo at time n / fs. Samples outside [0, N) read as 0.
+ *  - antennas: float32 [M][3] metres (x, y, z), shared by every scan when
+ *    antenna_stride == 0, else scan b uses antennas + b * antenna_stride.
+ *  - Focal grid: point (ix, iy, iz) sits at origin + (ix, iy, iz) * pitch;
+ *    images are [batch][nz][ny][nx] float32 with x fastest. 2-D grids have
+ *    dim == 2 and n[2] == 1.
+ *  - Delay: round trip tau_i(r) = 2 |r - a_i| / v, in samples u_i = tau_i fs
+ *    (Eq. 1, read with the round trip and the medium speed v; the printed
+ *    form divides by 2 and uses c). The aligned signal is
+ *    x_i(k) = Y_i(u_i - floor(W/2) + k), k = 0..W-1, linearly interpolated.
+ *  - DAS energy  I(r) = sum_k (sum_i x_i(k))^2                      (Eq. 3)
+ *    DMAS energy I(r) = sum_k (sum_{i<j} x_i(k) x_j(k))^2      (Section II.B)
+ *    UWB_DMAS forms the pair sum as ((sum_i x_i)^2 - sum_i x_i^2) / 2;
+ *    UWB_DMAS_LITERAL multiplies every pair. Both compute the same quantity.
+ *  - Arithmetic is float32 (delays, interpolation, accumulation); the segment
+ *    metrics of uwb_localize are float64.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and returns a status: UWB_OK or a negative
+ *    UWB_ERR_* code for errors found on the host before any launch.
+ *    uwb_last_error() describes the last failure of the calling thread.
+ *    Errors found on the device (a bounded wait that ran out, non-finite
+ *    energies) are reported in uwb_result.status or by uwb_device_status().
+ *  - Staging waits inside kernels are bounded; a kernel that gives up records
+ *    UWB_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef UWB_H
+#define UWB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define UWB_OK 0
+#define UWB_ERR_ARG -1          /* invalid argument (null pointer, size, range) */
+#define UWB_ERR_CUDA -2         /* a CUDA runtime / driver call failed */
+#define UWB_ERR_TIMEOUT -3      /* a bounded device wait ran out */
+#define UWB_ERR_NONFINITE -4    /* NaN or Inf in the decimated energy profile */
+#define UWB_ERR_UNSUPPORTED -5  /* sizes outside what this build handles */
+#define UWB_ERR_WORKSPACE -6    /* workspace missing, misaligned or too small */
+
+/* beamformers */
+#define UWB_DAS 0
+#define UWB_DMAS 1            /* pair sum through ((sum x)^2 - sum x^2) / 2 */
+#define UWB_DMAS_LITERAL 2    /* pair sum by multiplying every pair i < j */
+
+/* spatial decimation modes (Section III, "Spatial Decimation") */
+#define UWB_DECIM_MANUAL 0    /* factor given in uwb_rule.decimation */
+#define UWB_DECIM_AUTO 1      /* from uwb_rule.min_tumor_diameter (Section IV) */
+
+/* decision metrics (Section III, "ROI Selection") */
+#define UWB_METRIC_HYBRID 0            /* Eq. 5, weight clipped to [0, 1] */
+#define UWB_METRIC_MEAN 1
+#define UWB_METRIC_VARIANCE 2
+#define UWB_METRIC_HYBRID_UNCLIPPED 3  /* Eq. 5 exactly as printed */
+
+/* why the selection loop stopped */
+#define UWB_STOP_NONE 0
+#define UWB_STOP_METRIC 1     /* Eq. 6-7: between-class scatter stopped growing or
+                                 within-class scatter stopped shrinking */
+#define UWB_STOP_MINSIZE 2    /* no child segment was large enough to choose */
+#define UWB_STOP_CAP 3        /* iteration cap reached */
+#define UWB_STOP_NO_TARGET 4  /* every decimated energy is zero */
+
+#define UWB_MAX_ITERS 32
+
+/* Focal-point lattice (Section II.A: "the breast tissue is divided into
+ * several focal points according to the desired resolution"). */
+typedef struct uwb_grid {
+  int dim;           /* 2 or 3 */
+  int n[3];          /* points per axis; n[2] == 1 when dim == 2 */
+  double origin[3];  /* position of point (0,0,0) in metres */
+  double pitch[3];   /* spacing per axis in metres (the final resolution) */
+} uwb_grid;
+
+/* Decision rule of the segment search (Section III). */
+typedef struct uwb_rule {
+  int mode;                   /* UWB_DECIM_MANUAL | UWB_DECIM_AUTO */
+  int decimation;             /* manual factor D >= 1 */
+  double min_tumor_diameter;  /* auto: D = floor(d / (sqrt(2) * min pitch)), >= 1 */
+  int metric;                 /* UWB_METRIC_* */
+  int min_segment;            /* a child segment needs every side >= this many points */
+  int frame_num, frame_den;   /* sliding framing: a chosen child grows by
+                                 ceil(frame_num / frame_den * side) points per side */
+  int max_iters;              /* 0 = ceil(log2(max grid side)) + 2; <= UWB_MAX_ITERS */
+} uwb_rule;
+
+/* Result of one localised scan; written by the device. */
+typedef struct uwb_result {
+  int status;             /* UWB_OK or UWB_ERR_NONFINITE / UWB_ERR_TIMEOUT */
+  int iters;              /* accepted segmentations (Table I's iteration count) */
+  int n_logged;           /* iterations performed; the last may have been rejected */
+  int stop_reason;        /* UWB_STOP_* */
+  int decim;              /* spatial decimation factor D */
+  int offset[3];          /* decimated lattice: offset per axis */
+  int dcount[3];          /*                    points per axis */
+  int roi_lo[3];          /* final region, full-resolution index box [lo, hi) */
+  int roi_hi[3];
+  int loc_idx[3];         /* argmax of the final image; -1 when there is none */
+  long long points_evaluated;  /* decimated points + final-region points */
+  double loc_xyz[3];      /* position of loc_idx in metres */
+  double peak;            /* energy at loc_idx */
+  double profile_max;     /* largest decimated energy */
+  int child[UWB_MAX_ITERS];        /* chosen child per iteration: bit 0 = high x
+                                      half, bit 1 = high y, bit 2 = high z */
+  int n_children[UWB_MAX_ITERS];   /* candidate children per iteration */
+  int box_lo[UWB_MAX_ITERS][3];    /* framed region chosen per iteration */
+  int box_hi[UWB_MAX_ITERS][3];
+  double metric_top[UWB_MAX_ITERS];  /* winning metric */
+  double metric_gap[UWB_MAX_ITERS];  /* (top - runner-up) / |top|; 1e300 if alone */
+  double between[UWB_MAX_ITERS];     /* Eq. 7 between-class scatter B_i */
+  double within[UWB_MAX_ITERS];      /* Eq. 6 within-class scatter W_i */
+  double stop_margin[UWB_MAX_ITERS]; /* relative margin of the continue/stop test */
+} uwb_result;
+
+/* Defaults: automatic decimation for a 1 cm tumour, hybrid metric,
+ * min_segment 4, framing 1/4, default iteration cap. Returns UWB_OK or
+ * UWB_ERR_ARG for a null pointer. */
+int uwb_default_rule(uwb_rule* rule);
+
+/* Spatial decimation factor D the rule gives on this grid (Section III
+ * manual/automatic modes; Section IV worked example: 1 cm tumour at 1 mm
+ * resolution gives 7). Returns D >= 1, or UWB_ERR_ARG. */
+int uwb_decimation(const uwb_grid* grid, const uwb_rule* rule);
+
+/* Full-resolution DAS image of one scan (Eq. 1 + Eq. 3) over every focal
+ * point of `grid`. image: [nz][ny][nx] float32 output. peak_index: optional
+ * ([1] int64): the linear index of the image maximum (lowest index on ties),
+ * or -1 for an empty grid; NULL to skip. */
+int uwb_das_image(const float* traces, int M, int N, const float* antennas,
+                  const uwb_grid* grid, double v, double fs, int window,
+                  float* image, long long* peak_index, void* stream);
+
+/* Full-resolution DMAS image of one scan (Section II.B); literal_pairs != 0
+ * multiplies every antenna pair, 0 uses the algebraic pair-sum identity. */
+int uwb_dmas_image(const float* traces, int M, int N, const float* antennas,
+                   const uwb_grid* grid, double v, double fs, int window,
+                   int literal_pairs, float* image, long long* peak_index,
+                   void* stream);
+
+/* Batched full-resolution images: `batch` scans of equal M, N and grid in one
+ * launch. traces [batch][M][N]; image [batch][P]; peak_index [batch] or NULL.
+ * beamformer: UWB_DAS | UWB_DMAS | UWB_DMAS_LITERAL. */
+int uwb_image_batch(int batch, int beamformer, const float* traces, int M, int N,
+                    const float* antennas, long long antenna_stride,
+                    const uwb_grid* grid, double v, double fs, int window,
+                    float* image, long long* peak_index, void* stream);
+
+/* Bytes of device workspace uwb_localize_batch needs for these sizes
+ * (0 on invalid arguments). The workspace must be 256-byte aligned. */
+size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid,
+                              int beamformer, const uwb_rule* rule);
+
+/* The segment-search framework (Section III) on one scan, entirely on the
+ * device: decimated profile, normalisation to its maximum, ROI selection
+ * loop (Eq. 5 metric, Eq. 6-7 stopping rule, sliding framing), final
+ * full-resolution imaging of the ROI and its argmax. out: [1] uwb_result
+ * (device). image: optional [P] float32; when given, the decimated energies
+ * and the final-region energies are written at their focal points (the
+ * paper's mixed-resolution final image) and other points are left untouched.
+ * workspace: device memory of at least uwb_localize_workspace(1, ...) bytes,
+ * owned by the caller, not kept after the stream reaches the end of the call. */
+int uwb_localize(const float* traces, int M, int N, const float* antennas,
+                 const uwb_grid* grid, double v, double fs, int window,
+                 int beamformer, const uwb_rule* rule, void* workspace,
+                 size_t ws_bytes, uwb_result* out, float* image, void* stream);
+
+/* uwb_localize over `batch` independent scans in one set of launches. Scans
+ * share M, N, grid, v, fs, window and rule. out: [batch]; image [batch][P]
+ * or NULL. */
+int uwb_localize_batch(int batch, const float* traces, int M, int N,
+                       const float* antennas, long long antenna_stride,
+                       const uwb_grid* grid, double v, double fs, int window,
+                       int beamformer, const uwb_rule* rule, void* workspace,
+                       size_t ws_bytes, uwb_result* out, float* image, void* stream);
+
+/* Optional phase timing of uwb_localize / uwb_localize_batch (profiling aid).
+ * While enabled, each call records CUDA events on its own stream around its
+ * phases: 0 = decimated energy profile, 1 = segment selection and work
+ * planning, 2 = final-region imaging, 3 = result decoding. The events add no
+ * work to the kernels. uwb_phase_timing(1) switches timing on and discards
+ * earlier records; uwb_phase_timing(0) switches it off. uwb_phase_times waits
+ * for the recorded events, writes the summed milliseconds of each phase into
+ * ms[0..3], forgets the records and returns how many calls they covered (or a
+ * negative UWB_ERR_* code). */
+int uwb_phase_timing(int enable);
+int uwb_phase_times(double* ms);
+
+/* Device-side status word shared by the image entry points: UWB_OK, or the
+ * first error a kernel recorded (UWB_ERR_TIMEOUT). Synchronises the current
+ * device; clear != 0 resets the word. Returns the word, or UWB_ERR_CUDA. */
+int uwb_device_status(int clear);
+
+/* Text of the last error of the calling thread ("" if none). */
+const char* uwb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UWB_H */

@@ -1,0 +1,253 @@
+"""Python binding of libuwb.so (segment-search confocal UWB imaging on GB300).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. Functions carry the C names of ``include/uwb.h`` and take torch CUDA
+tensors (float32, contiguous) for the arrays; ``grid`` is a dict
+``{"dim", "n", "origin", "pitch"}`` and ``rule`` a :class:`UwbRule`.
+There is no CPU fallback: if the library is not built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+__all__ = [
+    "UWB_OK", "UWB_DAS", "UWB_DMAS", "UWB_DMAS_LITERAL", "UwbGrid", "UwbRule", "UwbResult",
+    "RESULT_DTYPE", "lib", "make_grid", "uwb_default_rule", "uwb_decimation", "uwb_das_image",
+    "uwb_dmas_image", "uwb_image_batch", "uwb_localize_workspace", "uwb_localize",
+    "uwb_localize_batch", "uwb_device_status", "uwb_last_error", "results_from_device",
+    "uwb_phase_timing", "uwb_phase_times",
+    "UwbError",
+]
+
+LIB_PATH = pathlib.Path(__file__).resolve().parent / "libuwb.so"
+
+UWB_OK = 0
+UWB_ERR_ARG, UWB_ERR_CUDA, UWB_ERR_TIMEOUT = -1, -2, -3
+UWB_ERR_NONFINITE, UWB_ERR_UNSUPPORTED, UWB_ERR_WORKSPACE = -4, -5, -6
+UWB_DAS, UWB_DMAS, UWB_DMAS_LITERAL = 0, 1, 2
+UWB_DECIM_MANUAL, UWB_DECIM_AUTO = 0, 1
+UWB_METRIC_HYBRID, UWB_METRIC_MEAN, UWB_METRIC_VARIANCE, UWB_METRIC_HYBRID_UNCLIPPED = 0, 1, 2, 3
+UWB_STOP_NONE, UWB_STOP_METRIC, UWB_STOP_MINSIZE, UWB_STOP_CAP, UWB_STOP_NO_TARGET = 0, 1, 2, 3, 4
+UWB_MAX_ITERS = 32
+
+
+class UwbError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed with status {code}: {uwb_last_error()}")
+        self.code = code
+
+
+class UwbGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("origin", ctypes.c_double * 3), ("pitch", ctypes.c_double * 3)]
+
+
+class UwbRule(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("decimation", ctypes.c_int),
+                ("min_tumor_diameter", ctypes.c_double), ("metric", ctypes.c_int),
+                ("min_segment", ctypes.c_int), ("frame_num", ctypes.c_int),
+                ("frame_den", ctypes.c_int), ("max_iters", ctypes.c_int)]
+
+
+_I3 = ctypes.c_int * 3
+_ITI = ctypes.c_int * UWB_MAX_ITERS
+_IT3 = (ctypes.c_int * 3) * UWB_MAX_ITERS
+_ITD = ctypes.c_double * UWB_MAX_ITERS
+
+
+class UwbResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("n_logged", ctypes.c_int),
+                ("stop_reason", ctypes.c_int), ("decim", ctypes.c_int), ("offset", _I3),
+                ("dcount", _I3), ("roi_lo", _I3), ("roi_hi", _I3), ("loc_idx", _I3),
+                ("points_evaluated", ctypes.c_longlong), ("loc_xyz", ctypes.c_double * 3),
+                ("peak", ctypes.c_double), ("profile_max", ctypes.c_double),
+                ("child", _ITI), ("n_children", _ITI), ("box_lo", _IT3), ("box_hi", _IT3),
+                ("metric_top", _ITD), ("metric_gap", _ITD), ("between", _ITD),
+                ("within", _ITD), ("stop_margin", _ITD)]
+
+
+RESULT_DTYPE = np.dtype(UwbResult)
+RESULT_BYTES = ctypes.sizeof(UwbResult)
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libuwb.so (built by ``paper_1709_02549_gb300.build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(str(LIB_PATH))
+        vp, i, ll, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double, \
+            ctypes.c_size_t
+        gp, rp = ctypes.POINTER(UwbGrid), ctypes.POINTER(UwbRule)
+        sig = {
+            "uwb_default_rule": (i, [rp]),
+            "uwb_decimation": (i, [gp, rp]),
+            "uwb_das_image": (i, [vp, i, i, vp, gp, d, d, i, vp, vp, vp]),
+            "uwb_dmas_image": (i, [vp, i, i, vp, gp, d, d, i, i, vp, vp, vp]),
+            "uwb_image_batch": (i, [i, i, vp, i, i, vp, ll, gp, d, d, i, vp, vp, vp]),
+            "uwb_localize_workspace": (sz, [i, i, i, gp, i, rp]),
+            "uwb_localize": (i, [vp, i, i, vp, gp, d, d, i, i, rp, vp, sz, vp, vp, vp]),
+            "uwb_localize_batch": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, sz, vp, vp,
+                                       vp]),
+            "uwb_device_status": (i, [i]),
+            "uwb_phase_timing": (i, [i]),
+            "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
+            "uwb_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def make_grid(grid) -> UwbGrid:
+    if isinstance(grid, UwbGrid):
+        return grid
+    n = list(grid["n"]) + [1] * (3 - len(grid["n"]))
+    origin = list(grid["origin"]) + [0.0] * (3 - len(grid["origin"]))
+    pitch = list(grid["pitch"]) + [1.0] * (3 - len(grid["pitch"]))
+    return UwbGrid(int(grid["dim"]), _I3(*n), (ctypes.c_double * 3)(*origin),
+                   (ctypes.c_double * 3)(*pitch))
+
+
+def uwb_last_error() -> str:
+    return (lib().uwb_last_error() or b"").decode()
+
+
+def _check(code: int, what: str) -> int:
+    if code < 0:
+        raise UwbError(code, what)
+    return code
+
+
+def _ptr(t, name: str, allow_none: bool = False):
+    """Device address of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, name: str, allow_none: bool = False):
+    import torch
+    if t is not None and t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    return _ptr(t, name, allow_none)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def uwb_default_rule(**overrides) -> UwbRule:
+    r = UwbRule()
+    _check(lib().uwb_default_rule(ctypes.byref(r)), "uwb_default_rule")
+    for k, v in overrides.items():
+        setattr(r, k, v)
+    return r
+
+
+def uwb_decimation(grid, rule: UwbRule) -> int:
+    return _check(lib().uwb_decimation(ctypes.byref(make_grid(grid)), ctypes.byref(rule)),
+                  "uwb_decimation")
+
+
+def uwb_das_image(traces, antennas, grid, v, fs, window, image, peak_index=None, stream=None):
+    M, N = traces.shape[-2:]
+    _check(lib().uwb_das_image(_f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                               ctypes.byref(make_grid(grid)), float(v), float(fs), int(window),
+                               _f32(image, "image"), _ptr(peak_index, "peak_index", True),
+                               _stream(stream)), "uwb_das_image")
+
+
+def uwb_dmas_image(traces, antennas, grid, v, fs, window, literal_pairs, image, peak_index=None,
+                   stream=None):
+    M, N = traces.shape[-2:]
+    _check(lib().uwb_dmas_image(_f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                                ctypes.byref(make_grid(grid)), float(v), float(fs), int(window),
+                                int(bool(literal_pairs)), _f32(image, "image"),
+                                _ptr(peak_index, "peak_index", True), _stream(stream)),
+           "uwb_dmas_image")
+
+
+def uwb_image_batch(beamformer, traces, antennas, grid, v, fs, window, image, peak_index=None,
+                    stream=None):
+    """traces [B, M, N]; antennas [M, 3] (shared) or [B, M, 3]; image [B, P]."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_image_batch(B, int(beamformer), _f32(traces, "traces"), M, N,
+                                 _f32(antennas, "antennas"), stride,
+                                 ctypes.byref(make_grid(grid)), float(v), float(fs), int(window),
+                                 _f32(image, "image"), _ptr(peak_index, "peak_index", True),
+                                 _stream(stream)), "uwb_image_batch")
+
+
+def uwb_localize_workspace(batch, M, N, grid, beamformer, rule: UwbRule) -> int:
+    n = lib().uwb_localize_workspace(int(batch), int(M), int(N), ctypes.byref(make_grid(grid)),
+                                     int(beamformer), ctypes.byref(rule))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_localize_workspace")
+    return n
+
+
+def uwb_localize(traces, antennas, grid, v, fs, window, beamformer, rule: UwbRule, workspace,
+                 out, image=None, stream=None):
+    """out: CUDA uint8 tensor of RESULT_BYTES bytes (device uwb_result)."""
+    M, N = traces.shape[-2:]
+    _check(lib().uwb_localize(_f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                              ctypes.byref(make_grid(grid)), float(v), float(fs), int(window),
+                              int(beamformer), ctypes.byref(rule), _ptr(workspace, "workspace"),
+                              workspace.numel() * workspace.element_size(), _ptr(out, "out"),
+                              _f32(image, "image", True), _stream(stream)), "uwb_localize")
+
+
+def uwb_localize_batch(traces, antennas, grid, v, fs, window, beamformer, rule: UwbRule,
+                       workspace, out, image=None, stream=None):
+    """traces [B, M, N]; antennas [M, 3] or [B, M, 3]; out uint8 [B * RESULT_BYTES]."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_localize_batch(B, _f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                                    stride, ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                    int(window), int(beamformer), ctypes.byref(rule),
+                                    _ptr(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(),
+                                    _ptr(out, "out"), _f32(image, "image", True),
+                                    _stream(stream)), "uwb_localize_batch")
+
+
+def uwb_phase_timing(enable: bool) -> None:
+    _check(lib().uwb_phase_timing(int(bool(enable))), "uwb_phase_timing")
+
+
+def uwb_phase_times():
+    """(calls, [ms of phase 0..3]) summed since timing was switched on."""
+    ms = (ctypes.c_double * 4)()
+    calls = _check(lib().uwb_phase_times(ms), "uwb_phase_times")
+    return calls, list(ms)
+
+
+def uwb_device_status(clear: bool = False) -> int:
+    return lib().uwb_device_status(int(bool(clear)))
+
+
+def results_from_device(out) -> np.ndarray:
+    """Copies a device uwb_result array (uint8 tensor) to a numpy record array."""
+    host = out.detach().to("cpu").numpy()
+    return host.view(RESULT_DTYPE)

@@ -1,0 +1,401 @@
+// Device-resident segment search (Section III, "ROI Selection"): one warp per
+// scan runs the whole coarse-to-fine loop on the decimated energy profile --
+// quadrant/octant split, per-child mean and variance in float64, the Eq. 5
+// decision metric, sliding framing of the chosen child, and the Eq. 6-7
+// stopping rule -- then writes the final region as a lattice box for the
+// full-resolution pass. No host round trip between steps.
+//
+// Readings where the paper is silent or inconsistent (the same ones the
+// float64 reference implementation takes):
+//  * energies are divided by the profile maximum before any metric (Eq. 5
+//    adds a mean to a variance, which is only scale-free after normalising);
+//  * sigma^2_{i-1} of Eq. 5 is the variance of the region being split (the
+//    whole region at the first iteration); population variance; a child with
+//    zero variance scores its mean; the Eq. 5 weight is clipped to [0, 1]
+//    (UWB_METRIC_HYBRID) or used as printed (UWB_METRIC_HYBRID_UNCLIPPED);
+//  * the two classes of Eq. 6-7 are the decimated energies of the regions of
+//    consecutive iterations; the loop continues while B grows and W shrinks,
+//    tested from the second iteration, and returns the last accepted region;
+//  * children without a decimated point or with a side below min_segment are
+//    not candidates; ties go to the lowest child index (bit 0 = high x half,
+//    bit 1 = high y, bit 2 = high z).
+#include <float.h>
+
+#include "uwb_internal.cuh"
+
+namespace uwb {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Decimated-lattice index range [klo, khi) per axis of the points inside a
+// full-resolution box [lo, hi).
+struct KBox {
+  int klo[3], khi[3];
+  long long n;
+};
+
+__device__ KBox lattice_in_box(const SelParams& P, const int lo[3], const int hi[3]) {
+  KBox b;
+  b.n = 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int s = P.step[a];
+    const int dl = lo[a] - P.off[a], dh = hi[a] - P.off[a];
+    int kl = dl <= 0 ? 0 : (dl + s - 1) / s;
+    int kh = dh <= 0 ? 0 : (dh + s - 1) / s;
+    kl = min(kl, P.cnt[a]);
+    kh = min(kh, P.cnt[a]);
+    if (kh < kl) kh = kl;
+    b.klo[a] = kl;
+    b.khi[a] = kh;
+    b.n *= (kh - kl);
+  }
+  return b;
+}
+
+struct Stats {
+  long long n;
+  double sum, mean, scatter;  // scatter = sum of squared deviations from the mean
+};
+
+// Two-pass statistics of the normalised energies inside a box (warp-wide).
+__device__ Stats box_stats(const SelParams& P, const float* prof, double pmax, const KBox& b) {
+  const int lane = threadIdx.x & 31;
+  Stats st;
+  st.n = b.n;
+  st.sum = st.mean = st.scatter = 0.0;
+  if (b.n == 0) return st;
+  const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
+  double s = 0.0;
+  for (long long j = lane; j < b.n; j += 32) {
+    const int kx = b.klo[0] + static_cast<int>(j % nx);
+    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
+    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
+    s += static_cast<double>(prof[kx + static_cast<long long>(P.cnt[0]) *
+                                           (ky + static_cast<long long>(P.cnt[1]) * kz)]) /
+         pmax;
+  }
+  st.sum = warp_sum(s);
+  st.mean = st.sum / static_cast<double>(b.n);
+  double q = 0.0;
+  for (long long j = lane; j < b.n; j += 32) {
+    const int kx = b.klo[0] + static_cast<int>(j % nx);
+    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
+    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
+    const double e = static_cast<double>(prof[kx + static_cast<long long>(P.cnt[0]) *
+                                                   (ky + static_cast<long long>(P.cnt[1]) * kz)]) /
+                     pmax;
+    q += (e - st.mean) * (e - st.mean);
+  }
+  st.scatter = warp_sum(q);
+  return st;
+}
+
+__device__ __forceinline__ double rel_gap(double hi, double lo) {
+  const double d = fmax(fabs(hi), fabs(lo));
+  return d == 0.0 ? 0.0 : (hi - lo) / d;
+}
+
+__device__ double decision_metric(int metric, double mu, double var, double var_prev) {
+  if (metric == UWB_METRIC_MEAN) return mu;
+  if (metric == UWB_METRIC_VARIANCE) return var;
+  if (var == 0.0) return mu;
+  double a = (var - var_prev) / var;  // Eq. 5 weight
+  if (metric == UWB_METRIC_HYBRID) a = fmin(fmax(a, 0.0), 1.0);
+  return (1.0 - a) * mu + a * var;
+}
+
+__global__ void __launch_bounds__(256) k_select(const SelParams P) {
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (s >= P.B) return;
+  const float* prof = P.profile + static_cast<long long>(s) * P.prof_stride;
+  uwb_result* R = P.out + s;
+  LatBox* box = P.boxes + s;
+
+  // clear the result record
+  {
+    int* w = reinterpret_cast<int*>(R);
+    for (int j = lane; j < static_cast<int>(sizeof(uwb_result) / 4); j += 32) w[j] = 0;
+    __syncwarp();
+  }
+  const long long Pd = static_cast<long long>(P.cnt[0]) * P.cnt[1] * P.cnt[2];
+  float fmx = 0.f;
+  bool bad = false;
+  for (long long j = lane; j < Pd; j += 32) {
+    const float v = prof[j];
+    bad |= !isfinite(v);
+    fmx = fmaxf(fmx, v);
+  }
+  bad = __any_sync(0xFFFFFFFFu, bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(0xFFFFFFFFu, fmx, o));
+
+  if (lane == 0) {
+    R->decim = P.D;
+    for (int a = 0; a < 3; ++a) {
+      R->offset[a] = P.off[a];
+      R->dcount[a] = P.cnt[a];
+      R->loc_idx[a] = -1;
+    }
+    R->profile_max = fmx;
+  }
+  if (bad || fmx == 0.f) {
+    if (lane == 0) {
+      R->status = bad ? UWB_ERR_NONFINITE : UWB_OK;
+      R->stop_reason = bad ? UWB_STOP_NONE : UWB_STOP_NO_TARGET;
+      for (int a = 0; a < 3; ++a) {
+        box->lo[a] = 0;
+        box->step[a] = 1;
+        box->cnt[a] = 0;
+      }
+      box->tiles = 0;
+    }
+    return;
+  }
+  const double pmax = static_cast<double>(fmx);
+  const int dim = P.dim;
+  const int nchild = 1 << dim;
+  const uwb_rule& rule = P.rule;
+
+  int Rlo[3] = {0, 0, 0}, Rhi[3] = {P.gn[0], P.gn[1], P.gn[2]};
+  Stats sa = box_stats(P, prof, pmax, lattice_in_box(P, Rlo, Rhi));
+  double var_prev = sa.scatter / static_cast<double>(sa.n);
+  double B_prev = 0.0, W_prev = 0.0;
+  int iters = 0, n_logged = 0, stop = UWB_STOP_NONE;
+
+  for (int i = 1; i <= P.max_iters; ++i) {
+    const int li = i - 1;
+    int mid[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mid[a] = Rlo[a] + (Rhi[a] - Rlo[a]) / 2;
+    int best = -1, nvalid = 0;
+    double best_m = 0.0, second_m = 0.0;
+    int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+    for (int c = 0; c < nchild; ++c) {
+      int clo[3], chi[3];
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a < dim) {
+          const int bit = (c >> a) & 1;
+          clo[a] = bit ? mid[a] : Rlo[a];
+          chi[a] = bit ? Rhi[a] : mid[a];
+          if (chi[a] - clo[a] < rule.min_segment) ok = false;
+        } else {
+          clo[a] = Rlo[a];
+          chi[a] = Rhi[a];
+        }
+      }
+      if (!ok) continue;
+      const KBox kb = lattice_in_box(P, clo, chi);
+      if (kb.n == 0) continue;
+      const Stats sc = box_stats(P, prof, pmax, kb);
+      const double m =
+          decision_metric(rule.metric, sc.mean, sc.scatter / static_cast<double>(sc.n), var_prev);
+      if (nvalid == 0 || m > best_m) {
+        if (nvalid > 0) second_m = best_m;
+        best_m = m;
+        best = c;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          blo[a] = clo[a];
+          bhi[a] = chi[a];
+        }
+      } else if (nvalid == 1 || m > second_m) {
+        second_m = m;
+      }
+      ++nvalid;
+    }
+    if (nvalid == 0) {
+      stop = UWB_STOP_MINSIZE;
+      iters = i - 1;
+      break;
+    }
+    // sliding framing of the chosen child
+    int Nlo[3], Nhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim) {
+        const int side = bhi[a] - blo[a];
+        const int grow = (side * rule.frame_num + rule.frame_den - 1) / rule.frame_den;
+        Nlo[a] = max(blo[a] - grow, 0);
+        Nhi[a] = min(bhi[a] + grow, P.gn[a]);
+      } else {
+        Nlo[a] = blo[a];
+        Nhi[a] = bhi[a];
+      }
+    }
+    // Eq. 6-7 between the regions of consecutive iterations
+    const Stats sb = box_stats(P, prof, pmax, lattice_in_box(P, Nlo, Nhi));
+    const double Wi = sa.scatter + sb.scatter;
+    const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
+    const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
+                      static_cast<double>(sb.n) * (sb.mean - pooled) * (sb.mean - pooled);
+    double margin = 1e300;
+    bool cont = true;
+    if (i >= 2) {
+      const double mB = rel_gap(Bi, B_prev), mW = rel_gap(W_prev, Wi);
+      cont = (Bi > B_prev) && (Wi < W_prev);
+      margin = cont ? fmin(mB, mW) : fmax(-mB, -mW);
+    }
+    if (lane == 0) {
+      R->child[li] = best;
+      R->n_children[li] = nvalid;
+      R->metric_top[li] = best_m;
+      R->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
+      for (int a = 0; a < 3; ++a) {
+        R->box_lo[li][a] = Nlo[a];
+        R->box_hi[li][a] = Nhi[a];
+      }
+      R->within[li] = Wi;
+      R->between[li] = Bi;
+      R->stop_margin[li] = margin;
+    }
+    n_logged = i;
+    if (!cont) {
+      stop = UWB_STOP_METRIC;
+      iters = i - 1;
+      break;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Rlo[a] = Nlo[a];
+      Rhi[a] = Nhi[a];
+    }
+    sa = sb;
+    var_prev = sa.scatter / static_cast<double>(sa.n);
+    B_prev = Bi;
+    W_prev = Wi;
+    iters = i;
+    if (i == P.max_iters) {
+      stop = UWB_STOP_CAP;
+      break;
+    }
+  }
+  if (lane == 0) {
+    R->status = UWB_OK;
+    R->iters = iters;
+    R->n_logged = n_logged;
+    R->stop_reason = stop;
+    int tiles = 1;
+    for (int a = 0; a < 3; ++a) {
+      R->roi_lo[a] = Rlo[a];
+      R->roi_hi[a] = Rhi[a];
+      box->lo[a] = Rlo[a];
+      box->step[a] = 1;
+      box->cnt[a] = Rhi[a] - Rlo[a];
+      tiles *= (box->cnt[a] + P.tdim[a] - 1) / P.tdim[a];
+    }
+    box->tiles = tiles;
+  }
+}
+
+// Exclusive prefix sum of the per-scan tile counts (one CTA).
+__global__ void __launch_bounds__(1024) k_plan(const LatBox* boxes, int* prefix, int B) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < B; base += blockDim.x) {
+    const int idx = base + tid;
+    const int v = idx < B ? boxes[idx].tiles : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = blockDim.x >> 5;
+      int w = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o) w += u;
+      }
+      if (lane < nw) warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    const int before = (warp > 0 ? warp_tot[warp - 1] : 0) + incl - v;
+    if (idx < B) prefix[idx] = carry + before;
+    __syncthreads();
+    if (tid == 0) carry_s = carry + warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (tid == 0) prefix[B] = carry_s;
+}
+
+// Decodes each scan's argmax key into the result record.
+__global__ void k_finish(const FinishParams P, const int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.B) return;
+  uwb_result* R = P.out + s;
+  const LatBox b = P.boxes[s];
+  const unsigned long long key = P.keys[s];
+  const long long roi = b.tiles > 0 ? static_cast<long long>(b.cnt[0]) * b.cnt[1] * b.cnt[2] : 0;
+  R->points_evaluated = P.Pd + roi;
+  if (status && *status != UWB_OK) R->status = *status;
+  if (key != 0ull && b.tiles > 0) {
+    const long long lin = static_cast<long long>(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+    const int ix = static_cast<int>(lin % P.gn[0]);
+    const int iy = static_cast<int>((lin / P.gn[0]) % P.gn[1]);
+    const int iz = static_cast<int>(lin / (static_cast<long long>(P.gn[0]) * P.gn[1]));
+    const int idx[3] = {ix, iy, iz};
+    for (int a = 0; a < 3; ++a) {
+      R->loc_idx[a] = idx[a];
+      R->loc_xyz[a] = P.org[a] + static_cast<double>(idx[a]) * P.pit[a];
+    }
+    R->peak = static_cast<double>(__uint_as_float(static_cast<unsigned int>(key >> 32)));
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      R->loc_idx[a] = -1;
+      R->loc_xyz[a] = 0.0;
+    }
+    R->peak = 0.0;
+  }
+}
+
+// argmax keys -> linear index (or -1), in place.
+__global__ void k_keys_to_index(unsigned long long* keys, int B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const unsigned long long key = keys[s];
+  const long long idx =
+      key ? static_cast<long long>(0xFFFFFFFFull - (key & 0xFFFFFFFFull)) : -1ll;
+  reinterpret_cast<long long*>(keys)[s] = idx;
+}
+
+}  // namespace
+
+cudaError_t launch_select(const SelParams& p, cudaStream_t st) {
+  const int warps = 8;
+  k_select<<<(p.B + warps - 1) / warps, warps * 32, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st) {
+  k_plan<<<1, 1024, 0, st>>>(boxes, prefix, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t st) {
+  k_finish<<<(p.B + 127) / 128, 128, 0, st>>>(p, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keys_to_index(unsigned long long* keys, int B, cudaStream_t st) {
+  k_keys_to_index<<<(B + 127) / 128, 128, 0, st>>>(keys, B);
+  return cudaGetLastError();
+}
+
+}  // namespace uwb

@@ -1,0 +1,702 @@
+// C ABI of libuwb.so: argument checks, the spatial-decimation rule, workspace
+// layout, TMA descriptor encoding, tile/warp shape choice and the launch
+// sequence of the device-resident segment search.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "uwb_internal.cuh"
+
+// Status word of the image entry points (they take no workspace); kernels
+// record UWB_ERR_TIMEOUT here when a bounded staging wait runs out.
+__device__ int g_uwb_status_word;
+
+namespace uwb {
+namespace {
+
+thread_local char t_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof t_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(UWB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Device {
+  bool ready = false;
+  int sms = 0;
+  int* status = nullptr;
+};
+
+std::mutex g_mu;
+Device g_devs[64];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+bool g_encode_tried = false;
+
+int device(Device** out) {
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (d < 0 || d >= 64) return fail(UWB_ERR_UNSUPPORTED, "device ordinal %d", d);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Device& dev = g_devs[d];
+  if (!dev.ready) {
+    e = cudaDeviceGetAttribute(&dev.sms, cudaDevAttrMultiProcessorCount, d);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&dev.status), g_uwb_status_word);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    dev.ready = true;
+  }
+  if (!g_encode_tried) {
+    g_encode_tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    else
+      cudaGetLastError();
+  }
+  *out = &dev;
+  return UWB_OK;
+}
+
+// ---- optional phase timing (events recorded on the caller's stream)
+constexpr int kPhases = 4;
+struct PhaseEvents {
+  cudaEvent_t ev[kPhases + 1];
+};
+std::mutex g_timing_mu;
+bool g_timing = false;
+std::vector<PhaseEvents> g_phase_records;
+
+void drop_records() {
+  for (auto& r : g_phase_records)
+    for (auto e : r.ev) cudaEventDestroy(e);
+  g_phase_records.clear();
+}
+
+// Events of one call, or nullptr when timing is off.
+struct PhaseTimer {
+  PhaseEvents pe;
+  bool on = false;
+  int next = 0;
+  explicit PhaseTimer(cudaStream_t st) : stream(st) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (!g_timing) return;
+    for (int i = 0; i <= kPhases; ++i)
+      if (cudaEventCreate(&pe.ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(pe.ev[j]);
+        cudaGetLastError();
+        return;
+      }
+    on = true;
+  }
+  void mark() {
+    if (on && next <= kPhases) cudaEventRecord(pe.ev[next++], stream);
+  }
+  void commit() {
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    if (next == kPhases + 1) {
+      g_phase_records.push_back(pe);
+    } else {
+      for (auto e : pe.ev) cudaEventDestroy(e);
+    }
+    on = false;
+  }
+  ~PhaseTimer() {
+    if (on)
+      for (auto e : pe.ev) cudaEventDestroy(e);
+  }
+  cudaStream_t stream;
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Scans of one call: shared sizes and geometry.
+struct Geo {
+  int B, M, N, W, h;
+  double v, fs;
+  float kscale;
+  uwb_grid g;
+  long long P;
+};
+
+int check_common(int batch, const float* traces, int M, int N, const float* ant,
+                 const uwb_grid* grid, double v, double fs, int window, Geo* geo) {
+  if (batch < 1 || batch > (1 << 24)) return fail(UWB_ERR_ARG, "batch %d out of range", batch);
+  if (!traces || !ant) return fail(UWB_ERR_ARG, "null traces or antennas");
+  if (M < 1 || M > 4096) return fail(UWB_ERR_ARG, "antenna count M=%d out of [1, 4096]", M);
+  if (N < 1) return fail(UWB_ERR_ARG, "trace length N=%d < 1", N);
+  if (window < 1 || window > 4096) return fail(UWB_ERR_ARG, "window %d out of [1, 4096]", window);
+  if (!finite_pos(v) || !finite_pos(fs)) return fail(UWB_ERR_ARG, "v and fs must be finite and > 0");
+  if (!grid) return fail(UWB_ERR_ARG, "null grid");
+  if (grid->dim != 2 && grid->dim != 3) return fail(UWB_ERR_ARG, "grid dim %d not 2 or 3", grid->dim);
+  long long P = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (grid->n[a] < 1) return fail(UWB_ERR_ARG, "grid n[%d] = %d < 1", a, grid->n[a]);
+    if (!std::isfinite(grid->origin[a])) return fail(UWB_ERR_ARG, "grid origin not finite");
+    if (a < grid->dim && !finite_pos(grid->pitch[a]))
+      return fail(UWB_ERR_ARG, "grid pitch[%d] must be finite and > 0", a);
+    P *= grid->n[a];
+  }
+  if (grid->dim == 2 && grid->n[2] != 1) return fail(UWB_ERR_ARG, "2-D grid needs n[2] == 1");
+  if (P > 0x7FFFFFFELL) return fail(UWB_ERR_ARG, "grid of %lld points exceeds 2^31 - 2", P);
+  const double ks = 2.0 * fs / v;
+  if (!std::isfinite(static_cast<float>(ks))) return fail(UWB_ERR_ARG, "2 fs / v overflows float");
+  geo->B = batch;
+  geo->M = M;
+  geo->N = N;
+  geo->W = window;
+  geo->h = window / 2;
+  geo->v = v;
+  geo->fs = fs;
+  geo->kscale = static_cast<float>(ks);
+  geo->g = *grid;
+  if (grid->dim == 2) geo->g.pitch[2] = 1.0;
+  geo->P = P;
+  return UWB_OK;
+}
+
+struct Variant {
+  int bf, v, threads;
+  int tdim[3];
+  int wpad;
+};
+
+int pick_variant(int bf, int M, int W, int dim, Variant* out) {
+  Variant var;
+  var.bf = bf;
+  if (bf == BF_DMAS_LIT) {
+    if (M > 64) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 64 (M=%d)", M);
+    var.v = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
+    const int kc = var.v <= 16 ? 4 : (var.v <= 32 ? 2 : 1);
+    var.wpad = (W + kc - 1) / kc * kc;
+    var.threads = 128;
+    if (dim == 2) {
+      var.tdim[0] = 16; var.tdim[1] = 8; var.tdim[2] = 1;
+    } else {
+      var.tdim[0] = 8; var.tdim[1] = 4; var.tdim[2] = 4;
+    }
+  } else {
+    var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : 32;
+    var.wpad = (W + var.v - 1) / var.v * var.v;
+    var.threads = 256;
+    if (dim == 2) {
+      var.tdim[0] = 32; var.tdim[1] = 8; var.tdim[2] = 1;
+    } else {
+      var.tdim[0] = 16; var.tdim[1] = 4; var.tdim[2] = 4;
+    }
+  }
+  *out = var;
+  return UWB_OK;
+}
+
+// Warp sub-block shape: the one whose 32 focal points span the fewest delay
+// samples (fewest shared-memory bank collisions), preferring wide x.
+void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
+  double best = 1e300;
+  for (int wx = 32; wx >= 1; wx >>= 1)
+    for (int wy = 32 / wx; wy >= 1; wy >>= 1) {
+      const int wz = 32 / (wx * wy);
+      if (wx * wy * wz != 32) continue;
+      if (tdim[0] % wx || tdim[1] % wy || tdim[2] % wz) continue;
+      const double cost = (wx - 1) * delta[0] + (wy - 1) * delta[1] + (wz - 1) * delta[2];
+      if (cost < best - 1e-12) {
+        best = cost;
+        wdim[0] = wx; wdim[1] = wy; wdim[2] = wz;
+      }
+    }
+}
+
+// Samples staged per antenna: what a shared-memory budget allows, at most
+// one TMA box width (256).
+int pick_span(int bf, int M, int threads) {
+  const size_t budget = bf == BF_DMAS_LIT ? 100 * 1024 : 56 * 1024;
+  const size_t fixed = image_smem_bytes(bf, M, 0, threads);
+  long long span = fixed >= budget ? 4 : static_cast<long long>((budget - fixed) / (4 * M));
+  span &= ~3LL;
+  if (span > 256) span = 256;
+  if (span < 4) span = 4;
+  return static_cast<int>(span);
+}
+
+int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* map) {
+  memset(map, 0, sizeof *map);
+  if (!g_encode) return 0;
+  if ((reinterpret_cast<uintptr_t>(traces) & 15) || (geo.N & 3) || geo.M > 256 || span > 256)
+    return 0;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(geo.N), static_cast<cuuint64_t>(geo.M),
+                        static_cast<cuuint64_t>(geo.B)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(geo.N) * 4,
+                           static_cast<cuuint64_t>(geo.N) * geo.M * 4};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(geo.M), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(traces),
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 1 : 0;
+}
+
+int occupancy(const Variant& var, size_t smem) {
+  switch (var.bf) {
+    case BF_DAS: return occupancy_image_das(var.v, var.threads, smem);
+    case BF_DMAS_ID: return occupancy_image_dmas(var.v, var.threads, smem);
+    default: return occupancy_image_literal(var.v, var.threads, smem);
+  }
+}
+
+cudaError_t launch(const Variant& var, const ImgParams& p, const CUtensorMap* map, int ctas,
+                   size_t smem, cudaStream_t st) {
+  switch (var.bf) {
+    case BF_DAS: return launch_image_das(var.v, p, map, ctas, var.threads, smem, st);
+    case BF_DMAS_ID: return launch_image_dmas(var.v, p, map, ctas, var.threads, smem, st);
+    default: return launch_image_literal(var.v, p, map, ctas, var.threads, smem, st);
+  }
+}
+
+int tiles_of(const int cnt[3], const int tdim[3]) {
+  long long t = 1;
+  for (int a = 0; a < 3; ++a) t *= (cnt[a] + tdim[a] - 1) / tdim[a];
+  return static_cast<int>(t);
+}
+
+ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
+                      long long ant_stride, const Variant& var, int span, int use_tma,
+                      int* status) {
+  ImgParams p;
+  memset(&p, 0, sizeof p);
+  p.traces = traces;
+  p.trace_stride = static_cast<long long>(geo.M) * geo.N;
+  p.ant = ant;
+  p.ant_stride = ant_stride;
+  p.B = geo.B;
+  p.M = geo.M;
+  p.N = geo.N;
+  p.W = geo.W;
+  p.h = geo.h;
+  p.kscale = geo.kscale;
+  for (int a = 0; a < 3; ++a) {
+    p.org[a] = static_cast<float>(geo.g.origin[a]);
+    p.pit[a] = static_cast<float>(geo.g.pitch[a]);
+    p.gn[a] = geo.g.n[a];
+    p.tdim[a] = var.tdim[a];
+  }
+  p.gP = geo.P;
+  p.span = span;
+  p.wpad = var.wpad;
+  p.use_tma = use_tma;
+  p.status = status;
+  return p;
+}
+
+int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
+                     long long work_bound, const double step[3], cudaStream_t st) {
+  double delta[3];
+  for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
+  if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
+  pick_warp(var.tdim, delta, p.wdim);
+  const size_t smem = image_smem_bytes(var.bf, p.M, p.span, var.threads);
+  const int occ = occupancy(var, smem);
+  if (occ < 1) return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
+  long long ctas = static_cast<long long>(dev.sms) * occ;
+  if (work_bound < ctas) ctas = work_bound;
+  if (ctas < 1) return UWB_OK;
+  cudaError_t e = launch(var, p, map, static_cast<int>(ctas), smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
+  return UWB_OK;
+}
+
+int bf_of(int beamformer) {
+  switch (beamformer) {
+    case UWB_DAS: return BF_DAS;
+    case UWB_DMAS: return BF_DMAS_ID;
+    case UWB_DMAS_LITERAL: return BF_DMAS_LIT;
+    default: return -1;
+  }
+}
+
+int image_impl(int batch, int beamformer, const float* traces, int M, int N, const float* ant,
+               long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
+               float* image, long long* peak_index, void* stream) {
+  Geo geo;
+  int st = check_common(batch, traces, M, N, ant, grid, v, fs, window, &geo);
+  if (st) return st;
+  if (!image) return fail(UWB_ERR_ARG, "null image");
+  if (ant_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  const int bf = bf_of(beamformer);
+  if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  Variant var;
+  if ((st = pick_variant(bf, M, window, grid->dim, &var))) return st;
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int span = pick_span(bf, M, var.threads);
+  CUtensorMap map;
+  const int use_tma = encode_traces(geo, traces, span, &map);
+  ImgParams p = base_params(geo, traces, ant, ant_stride, var, span, use_tma, dev->status);
+  for (int a = 0; a < 3; ++a) {
+    p.uni.lo[a] = 0;
+    p.uni.step[a] = 1;
+    p.uni.cnt[a] = geo.g.n[a];
+  }
+  p.uni.tiles = tiles_of(p.uni.cnt, var.tdim);
+  p.image = image;
+  p.keys = reinterpret_cast<unsigned long long*>(peak_index);
+  cudaError_t e;
+  if (peak_index) {
+    e = cudaMemsetAsync(peak_index, 0, sizeof(long long) * batch, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  }
+  const double step[3] = {1, 1, 1};
+  if ((st = run_image_kernel(*dev, var, p, &map, static_cast<long long>(batch) * p.uni.tiles,
+                             step, cs)))
+    return st;
+  if (peak_index) {
+    e = launch_keys_to_index(p.keys, batch, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "argmax decode launch");
+  }
+  return UWB_OK;
+}
+
+int check_rule(const uwb_rule* r) {
+  if (!r) return fail(UWB_ERR_ARG, "null rule");
+  if (r->mode != UWB_DECIM_MANUAL && r->mode != UWB_DECIM_AUTO)
+    return fail(UWB_ERR_ARG, "unknown decimation mode %d", r->mode);
+  if (r->mode == UWB_DECIM_MANUAL && r->decimation < 1)
+    return fail(UWB_ERR_ARG, "manual decimation %d < 1", r->decimation);
+  if (r->mode == UWB_DECIM_AUTO && !finite_pos(r->min_tumor_diameter))
+    return fail(UWB_ERR_ARG, "min_tumor_diameter must be finite and > 0");
+  if (r->metric < UWB_METRIC_HYBRID || r->metric > UWB_METRIC_HYBRID_UNCLIPPED)
+    return fail(UWB_ERR_ARG, "unknown metric %d", r->metric);
+  if (r->min_segment < 1) return fail(UWB_ERR_ARG, "min_segment %d < 1", r->min_segment);
+  if (r->frame_num < 0 || r->frame_den < 1 || r->frame_num > 1000000)
+    return fail(UWB_ERR_ARG, "framing %d/%d invalid", r->frame_num, r->frame_den);
+  if (r->max_iters < 0 || r->max_iters > UWB_MAX_ITERS)
+    return fail(UWB_ERR_ARG, "max_iters %d out of [0, %d]", r->max_iters, UWB_MAX_ITERS);
+  return UWB_OK;
+}
+
+// Section III: manual factor as given; automatic factor spaces the decimated
+// points by the side of the square inscribed in the smallest tumour to find
+// (d / sqrt 2), in units of the finest pitch (Section IV: 1 cm at 1 mm -> 7).
+int decimation_of(const uwb_grid& g, const uwb_rule& r) {
+  if (r.mode == UWB_DECIM_MANUAL) return r.decimation;
+  double res = g.pitch[0];
+  for (int a = 1; a < g.dim; ++a) res = std::fmin(res, g.pitch[a]);
+  const double q = std::floor(r.min_tumor_diameter / std::sqrt(2.0) / res + 1e-9);
+  if (!(q >= 1.0)) return 1;
+  return q > 1e9 ? 1000000000 : static_cast<int>(q);
+}
+
+struct Decim {
+  int D, off[3], step[3], cnt[3];
+  long long Pd;
+  int max_iters;
+};
+
+Decim decimate(const uwb_grid& g, const uwb_rule& r) {
+  Decim d;
+  d.D = decimation_of(g, r);
+  d.Pd = 1;
+  int nmax = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < g.dim) {
+      d.off[a] = ((g.n[a] - 1) % d.D) / 2;  // centred lattice
+      d.step[a] = d.D;
+      d.cnt[a] = (g.n[a] - 1 - d.off[a]) / d.D + 1;
+      nmax = g.n[a] > nmax ? g.n[a] : nmax;
+    } else {
+      d.off[a] = 0;
+      d.step[a] = 1;
+      d.cnt[a] = g.n[a];
+    }
+    d.Pd *= d.cnt[a];
+  }
+  int lg = 0;
+  while ((1LL << lg) < nmax) ++lg;
+  d.max_iters = r.max_iters > 0 ? r.max_iters : lg + 2;
+  if (d.max_iters > UWB_MAX_ITERS) d.max_iters = UWB_MAX_ITERS;
+  return d;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+struct WsLayout {
+  size_t keys, status, profile, boxes, prefix, total;
+};
+
+WsLayout ws_layout(int B, long long Pd) {
+  WsLayout w;
+  size_t off = 0;
+  w.keys = off;
+  off += static_cast<size_t>(B) * 8;       // argmax keys ...
+  w.status = off;                           // ... followed by the status word
+  off = align256(off + 4);
+  w.profile = off;
+  off += align256(static_cast<size_t>(B) * static_cast<size_t>(Pd) * 4);
+  w.boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.prefix = off;
+  off += align256(static_cast<size_t>(B + 1) * 4);
+  w.total = off;
+  return w;
+}
+
+int localize_impl(int batch, const float* traces, int M, int N, const float* ant,
+                  long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
+                  int beamformer, const uwb_rule* rule, void* workspace, size_t ws_bytes,
+                  uwb_result* out, float* image, void* stream) {
+  Geo geo;
+  int st = check_common(batch, traces, M, N, ant, grid, v, fs, window, &geo);
+  if (st) return st;
+  if ((st = check_rule(rule))) return st;
+  if (!out) return fail(UWB_ERR_ARG, "null result array");
+  if (ant_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  const int bf = bf_of(beamformer);
+  if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  Variant var;
+  if ((st = pick_variant(bf, M, window, grid->dim, &var))) return st;
+  const Decim dc = decimate(geo.g, *rule);
+  const WsLayout wl = ws_layout(batch, dc.Pd);
+  if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255)
+    return fail(UWB_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < wl.total)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, wl.total);
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  auto* keys = reinterpret_cast<unsigned long long*>(ws + wl.keys);
+  auto* status = reinterpret_cast<int*>(ws + wl.status);
+  auto* profile = reinterpret_cast<float*>(ws + wl.profile);
+  auto* boxes = reinterpret_cast<LatBox*>(ws + wl.boxes);
+  auto* prefix = reinterpret_cast<int*>(ws + wl.prefix);
+
+  cudaError_t e = cudaMemsetAsync(ws + wl.keys, 0, wl.status + 4 - wl.keys, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+
+  const int span = pick_span(bf, M, var.threads);
+  CUtensorMap map;
+  const int use_tma = encode_traces(geo, traces, span, &map);
+  PhaseTimer timer(cs);
+  timer.mark();
+
+  // 1. energies of the decimated lattice (Section III, "Spatial Decimation")
+  ImgParams p1 = base_params(geo, traces, ant, ant_stride, var, span, use_tma, status);
+  for (int a = 0; a < 3; ++a) {
+    p1.uni.lo[a] = dc.off[a];
+    p1.uni.step[a] = dc.step[a];
+    p1.uni.cnt[a] = dc.cnt[a];
+  }
+  p1.uni.tiles = tiles_of(p1.uni.cnt, var.tdim);
+  p1.compact = profile;
+  p1.compact_stride = dc.Pd;
+  p1.image = image;
+  const double dstep[3] = {static_cast<double>(dc.step[0]), static_cast<double>(dc.step[1]),
+                           static_cast<double>(dc.step[2])};
+  if ((st = run_image_kernel(*dev, var, p1, &map,
+                             static_cast<long long>(batch) * p1.uni.tiles, dstep, cs)))
+    return st;
+
+  timer.mark();
+
+  // 2. ROI selection loop (Section III, "ROI Selection"), one warp per scan
+  SelParams sp;
+  memset(&sp, 0, sizeof sp);
+  sp.profile = profile;
+  sp.prof_stride = dc.Pd;
+  sp.B = batch;
+  sp.dim = geo.g.dim;
+  for (int a = 0; a < 3; ++a) {
+    sp.gn[a] = geo.g.n[a];
+    sp.off[a] = dc.off[a];
+    sp.step[a] = dc.step[a];
+    sp.cnt[a] = dc.cnt[a];
+    sp.tdim[a] = var.tdim[a];
+  }
+  sp.D = dc.D;
+  sp.rule = *rule;
+  sp.max_iters = dc.max_iters;
+  sp.boxes = boxes;
+  sp.out = out;
+  if ((e = launch_select(sp, cs)) != cudaSuccess) return cuda_fail(e, "select launch");
+  if ((e = launch_plan(boxes, prefix, batch, cs)) != cudaSuccess) return cuda_fail(e, "plan launch");
+
+  timer.mark();
+
+  // 3. final imaging of each scan's region at full resolution + argmax
+  ImgParams p2 = base_params(geo, traces, ant, ant_stride, var, span, use_tma, status);
+  p2.boxes = boxes;
+  p2.prefix = prefix;
+  p2.uni.tiles = 1;
+  p2.keys = keys;
+  p2.image = image;
+  int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
+  const double step1[3] = {1, 1, 1};
+  if ((st = run_image_kernel(*dev, var, p2, &map,
+                             static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                             cs)))
+    return st;
+
+  timer.mark();
+
+  FinishParams fp;
+  memset(&fp, 0, sizeof fp);
+  fp.keys = keys;
+  fp.boxes = boxes;
+  fp.out = out;
+  fp.B = batch;
+  for (int a = 0; a < 3; ++a) {
+    fp.gn[a] = geo.g.n[a];
+    fp.org[a] = geo.g.origin[a];
+    fp.pit[a] = geo.g.pitch[a];
+  }
+  fp.Pd = dc.Pd;
+  if ((e = launch_finish(fp, status, cs)) != cudaSuccess) return cuda_fail(e, "finish launch");
+  timer.mark();
+  timer.commit();
+  return UWB_OK;
+}
+
+}  // namespace
+}  // namespace uwb
+
+using namespace uwb;
+
+extern "C" {
+
+int uwb_default_rule(uwb_rule* rule) {
+  if (!rule) return fail(UWB_ERR_ARG, "null rule");
+  rule->mode = UWB_DECIM_AUTO;
+  rule->decimation = 1;
+  rule->min_tumor_diameter = 0.01;
+  rule->metric = UWB_METRIC_HYBRID;
+  rule->min_segment = 4;
+  rule->frame_num = 1;
+  rule->frame_den = 4;
+  rule->max_iters = 0;
+  return UWB_OK;
+}
+
+int uwb_decimation(const uwb_grid* grid, const uwb_rule* rule) {
+  Geo geo;
+  const float dummy = 0.f;
+  int st = check_common(1, &dummy, 1, 1, &dummy, grid, 1.0, 1.0, 1, &geo);
+  if (st) return st;
+  if ((st = check_rule(rule))) return st;
+  return decimation_of(geo.g, *rule);
+}
+
+int uwb_das_image(const float* traces, int M, int N, const float* antennas, const uwb_grid* grid,
+                  double v, double fs, int window, float* image, long long* peak_index,
+                  void* stream) {
+  return image_impl(1, UWB_DAS, traces, M, N, antennas, 0, grid, v, fs, window, image,
+                    peak_index, stream);
+}
+
+int uwb_dmas_image(const float* traces, int M, int N, const float* antennas,
+                   const uwb_grid* grid, double v, double fs, int window, int literal_pairs,
+                   float* image, long long* peak_index, void* stream) {
+  return image_impl(1, literal_pairs ? UWB_DMAS_LITERAL : UWB_DMAS, traces, M, N, antennas, 0,
+                    grid, v, fs, window, image, peak_index, stream);
+}
+
+int uwb_image_batch(int batch, int beamformer, const float* traces, int M, int N,
+                    const float* antennas, long long antenna_stride, const uwb_grid* grid,
+                    double v, double fs, int window, float* image, long long* peak_index,
+                    void* stream) {
+  return image_impl(batch, beamformer, traces, M, N, antennas, antenna_stride, grid, v, fs,
+                    window, image, peak_index, stream);
+}
+
+size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid, int beamformer,
+                              const uwb_rule* rule) {
+  Geo geo;
+  const float dummy = 0.f;
+  if (check_common(batch, &dummy, M, N, &dummy, grid, 1.0, 1.0, 1, &geo)) return 0;
+  if (check_rule(rule) || bf_of(beamformer) < 0) return 0;
+  return ws_layout(batch, decimate(geo.g, *rule).Pd).total;
+}
+
+int uwb_localize(const float* traces, int M, int N, const float* antennas, const uwb_grid* grid,
+                 double v, double fs, int window, int beamformer, const uwb_rule* rule,
+                 void* workspace, size_t ws_bytes, uwb_result* out, float* image, void* stream) {
+  return localize_impl(1, traces, M, N, antennas, 0, grid, v, fs, window, beamformer, rule,
+                       workspace, ws_bytes, out, image, stream);
+}
+
+int uwb_localize_batch(int batch, const float* traces, int M, int N, const float* antennas,
+                       long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                       int window, int beamformer, const uwb_rule* rule, void* workspace,
+                       size_t ws_bytes, uwb_result* out, float* image, void* stream) {
+  return localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                       beamformer, rule, workspace, ws_bytes, out, image, stream);
+}
+
+int uwb_phase_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  drop_records();
+  g_timing = enable != 0;
+  return UWB_OK;
+}
+
+int uwb_phase_times(double* ms) {
+  if (!ms) return fail(UWB_ERR_ARG, "null ms");
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (int p = 0; p < kPhases; ++p) ms[p] = 0.0;
+  const int calls = static_cast<int>(g_phase_records.size());
+  for (auto& r : g_phase_records) {
+    cudaError_t e = cudaEventSynchronize(r.ev[kPhases]);
+    if (e != cudaSuccess) {
+      drop_records();
+      return cuda_fail(e, "cudaEventSynchronize");
+    }
+    for (int p = 0; p < kPhases; ++p) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, r.ev[p], r.ev[p + 1]);
+      if (e != cudaSuccess) {
+        drop_records();
+        return cuda_fail(e, "cudaEventElapsedTime");
+      }
+      ms[p] += t;
+    }
+  }
+  drop_records();
+  return calls;
+}
+
+int uwb_device_status(int clear) {
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, dev->status, sizeof word, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  if (clear) {
+    e = cudaMemset(dev->status, 0, sizeof word);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  }
+  return word;
+}
+
+const char* uwb_last_error(void) { return t_err; }
+
+}  // extern "C"

@@ -8,6 +8,22 @@ if str(ROOT) not in sys.path:
 GOLDEN = ROOT / "tests" / "golden"
 
 
+import pytest
+
+
+@pytest.fixture(scope="session")
+def uwb():
+    """The CUDA library's Python binding, built in-tree if needed (nvcc
+    cross-compiles without a GPU)."""
+    from paper_1709_02549_gb300 import build
+    try:
+        build.build()
+    except RuntimeError as e:  # no nvcc on this machine
+        pytest.skip(f"libuwb.so cannot be built here: {e}")
+    import paper_1709_02549_gb300 as u
+    return u
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
 

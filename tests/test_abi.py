@@ -1,0 +1,92 @@
+"""The C ABI library on the host: it loads, exports every declared entry point,
+and rejects bad arguments before touching the GPU (no compute calls here)."""
+import ctypes
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_functions():
+    text = (ROOT / "include" / "uwb.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(uwb_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(uwb):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(uwb.lib(), name), name
+
+
+def test_structure_sizes_match_the_header(uwb):
+    # uwb_result: 20 ints, 1 int64, 5 doubles, 256 ints of logs, 160 doubles
+    assert uwb.RESULT_BYTES == 20 * 4 + 8 + 5 * 8 + 256 * 4 + 5 * 32 * 8
+    assert ctypes.sizeof(uwb.UwbGrid) == 4 + 12 + 48
+    assert ctypes.sizeof(uwb.UwbRule) == 4 + 4 + 8 + 4 * 4 + 4 + 4
+
+
+def test_default_rule(uwb):
+    r = uwb.uwb_default_rule()
+    assert (r.mode, r.metric, r.min_segment, r.frame_num, r.frame_den, r.max_iters) == \
+        (uwb.UWB_DECIM_AUTO, uwb.UWB_METRIC_HYBRID, 4, 1, 4, 0)
+    assert r.min_tumor_diameter == pytest.approx(0.01)
+
+
+def test_automatic_decimation_worked_example(uwb):
+    # Section IV: 1 cm tumour at 1 mm resolution -> 7
+    grid = {"dim": 2, "n": [100, 100, 1], "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    assert uwb.uwb_decimation(grid, uwb.uwb_default_rule()) == 7
+    g512 = {"dim": 2, "n": [512, 512, 1], "origin": [0, 0, 0], "pitch": [0.12 / 512] * 2 + [1.0]}
+    assert uwb.uwb_decimation(g512, uwb.uwb_default_rule()) == 30
+    manual = uwb.uwb_default_rule(mode=uwb.UWB_DECIM_MANUAL, decimation=5)
+    assert uwb.uwb_decimation(grid, manual) == 5
+
+
+def test_workspace_grows_with_the_batch(uwb):
+    g = {"dim": 2, "n": [512, 512, 1], "origin": [0, 0, 0], "pitch": [0.12 / 512] * 2 + [1.0]}
+    r = uwb.uwb_default_rule()
+    one = uwb.uwb_localize_workspace(1, 32, 2048, g, uwb.UWB_DMAS_LITERAL, r)
+    many = uwb.uwb_localize_workspace(64, 32, 2048, g, uwb.UWB_DMAS_LITERAL, r)
+    assert 0 < one < many
+    assert many >= 64 * 18 * 18 * 4      # the decimated profiles
+
+
+@pytest.mark.parametrize("kw,code", [
+    ({"M": 0}, -1), ({"N": 0}, -1), ({"window": 0}, -1), ({"v": 0.0}, -1),
+    ({"fs": float("nan")}, -1), ({"dim": 4}, -1), ({"n2": 3}, -1), ({"pitch": 0.0}, -1),
+    ({"null_traces": True}, -1),
+])
+def test_bad_arguments_are_rejected_on_the_host(uwb, kw, code):
+    L = uwb.lib()
+    g = uwb.make_grid({"dim": kw.get("dim", 2), "n": [8, 8, kw.get("n2", 1)],
+                       "origin": [0, 0, 0], "pitch": [kw.get("pitch", 1e-3)] * 2 + [1.0]})
+    fake = ctypes.c_void_p(0x1000)           # never dereferenced: checks come first
+    tr = None if kw.get("null_traces") else fake
+    st = L.uwb_das_image(tr, kw.get("M", 4), kw.get("N", 64), fake, ctypes.byref(g),
+                         kw.get("v", 1e8), kw.get("fs", 5e10), kw.get("window", 4), fake, None,
+                         None)
+    assert st == code
+    assert uwb.uwb_last_error() != ""
+
+
+def test_bad_rule_and_workspace_are_rejected(uwb):
+    L = uwb.lib()
+    g = uwb.make_grid({"dim": 2, "n": [8, 8, 1], "origin": [0, 0, 0], "pitch": [1e-3] * 2 + [1.0]})
+    fake = ctypes.c_void_p(0x1000)
+    bad = uwb.uwb_default_rule(metric=9)
+    assert L.uwb_localize(fake, 4, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, uwb.UWB_DAS,
+                          ctypes.byref(bad), fake, 1 << 20, fake, None, None) == -1
+    ok = uwb.uwb_default_rule()
+    assert L.uwb_localize(fake, 4, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, uwb.UWB_DAS,
+                          ctypes.byref(ok), None, 0, fake, None, None) == -6
+    assert L.uwb_localize(fake, 4, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, uwb.UWB_DAS,
+                          ctypes.byref(ok), ctypes.c_void_p(0x1008), 1 << 20, fake, None,
+                          None) == -6
+    assert L.uwb_localize(fake, 4, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 7,
+                          ctypes.byref(ok), fake, 1 << 20, fake, None, None) == -1
+    # literal pairs are built for up to 64 antennas
+    assert L.uwb_dmas_image(fake, 65, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 1, fake, None,
+                            None) == -5

@@ -1,0 +1,269 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300)."""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import phantom
+from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, dev,
+                    gpu_image_batch, gpu_localize_batch, rule_pair)
+
+pytestmark = pytest.mark.gpu
+
+BFS = [0, 1, 2]  # UWB_DAS, UWB_DMAS, UWB_DMAS_LITERAL
+
+
+@pytest.fixture(scope="module")
+def gpu(uwb):
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    uwb.uwb_device_status(clear=True)
+    yield uwb
+    assert uwb.uwb_device_status(clear=True) == 0
+
+
+def ring(M, radius, z=0.0, seed=0):
+    rng = np.random.default_rng(seed)
+    ang = np.sort(rng.uniform(0, 2 * np.pi, M))
+    return np.stack([radius * np.cos(ang), radius * np.sin(ang), np.full(M, z)], 1) \
+        .astype(np.float32)
+
+
+def random_case(M, N, n, extent, W, seed, dim=2, radius=0.07):
+    rng = np.random.default_rng(seed)
+    tr = rng.standard_normal((M, N)).astype(np.float32)
+    if dim == 2:
+        ants = ring(M, radius, seed=seed)
+    else:
+        ants = ring(M, radius, z=0.01, seed=seed)
+        ants[:, 2] = rng.uniform(-0.03, 0.03, M)
+    pitch = [extent / n[a] if a < dim else 1.0 for a in range(3)]
+    origin = [-extent / 2 + pitch[a] / 2 if a < dim else 0.0 for a in range(3)]
+    grid = {"dim": dim, "n": list(n), "origin": origin, "pitch": pitch}
+    return tr, ants, grid, 1.0e8, 50.0e9, W
+
+
+CASES = {
+    # name: (M, N, grid points, extent [m], W, dim)
+    "c1_like": (16, 1024, (64, 64, 1), 0.10, 20, 2),
+    "ragged_plain_staging": (5, 1023, (37, 29, 1), 0.09, 7, 2),      # N % 4 != 0
+    "window_chunks": (6, 512, (33, 17, 1), 0.08, 33, 2),             # W > 32
+    "single_sample_one_antenna": (1, 256, (9, 7, 1), 0.05, 1, 2),
+    "literal_register_block_64": (33, 640, (19, 21, 1), 0.08, 5, 2),
+    "three_d": (12, 1024, (20, 18, 14), 0.08, 20, 3),
+    "window_beyond_shared_memory": (8, 4096, (16, 12, 1), 0.60, 20, 2),  # global-load path
+}
+
+
+@pytest.mark.parametrize("bf", BFS)
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_image_matches_oracle(gpu, case, bf):
+    M, N, n, extent, W, dim = CASES[case]
+    tr, ants, grid, v, fs, W = random_case(M, N, n, extent, W, seed=zlib.crc32(case.encode()) % 1000, dim=dim)
+    img, peak = gpu_image_batch(gpu, bf, tr, ants, grid, v, fs, W)
+    ref = oracle.image(tr, ants, grid, v, fs, W, BF_ORACLE[bf])
+    assert_image_close(img[0], ref, what=case)
+    k = int(np.argmax(ref))
+    flat = ref.ravel()
+    assert abs(flat[int(peak[0])] - flat[k]) <= IMG_TOL * flat[k]
+
+
+@pytest.mark.parametrize("bf", BFS)
+def test_single_scan_entry_points(gpu, bf):
+    M, N, n, extent, W, dim = CASES["c1_like"]
+    tr, ants, grid, v, fs, W = random_case(M, N, n, extent, W, seed=5)
+    img = torch.zeros(int(np.prod(n)), device="cuda")
+    peak = torch.zeros(1, dtype=torch.int64, device="cuda")
+    if bf == 0:
+        gpu.uwb_das_image(dev(tr), dev(ants), grid, v, fs, W, img, peak)
+    else:
+        gpu.uwb_dmas_image(dev(tr), dev(ants), grid, v, fs, W, bf == 2, img, peak)
+    torch.cuda.synchronize()
+    ref = oracle.image(tr, ants, grid, v, fs, W, BF_ORACLE[bf])
+    assert_image_close(img.cpu().numpy().reshape(ref.shape), ref)
+
+
+def test_batched_images_with_per_scan_antennas(gpu):
+    M, N, n, extent, W = 10, 512, (21, 23, 1), 0.09, 12
+    traces, ants = [], []
+    for s in range(3):
+        tr, a, grid, v, fs, W = random_case(M, N, n, extent, W, seed=40 + s)
+        traces.append(tr)
+        ants.append(a)
+    traces = np.stack(traces)
+    ants = np.stack(ants)
+    for bf in BFS:
+        img, peak = gpu_image_batch(gpu, bf, traces, ants, grid, v, fs, W)
+        for s in range(3):
+            ref = oracle.image(traces[s], ants[s], grid, v, fs, W, BF_ORACLE[bf])
+            assert_image_close(img[s], ref, what=f"scan {s}")
+
+
+def test_ragged_trace_with_tma_disabled_by_alignment(gpu):
+    # a trace array starting 4 bytes past a 16-byte boundary cannot use TMA
+    M, N, n, extent, W = 6, 256, (13, 11, 1), 0.08, 9
+    tr, ants, grid, v, fs, W = random_case(M, N, n, extent, W, seed=77)
+    buf = torch.zeros(M * N + 1, device="cuda")
+    buf[1:] = dev(tr).ravel()
+    view = buf[1:].view(M, N)
+    img = torch.zeros(int(np.prod(n)), device="cuda")
+    gpu.uwb_das_image(view, dev(ants), grid, v, fs, W, img)
+    torch.cuda.synchronize()
+    ref = oracle.image(tr, ants, grid, v, fs, W, oracle.DAS)
+    assert_image_close(img.cpu().numpy().reshape(ref.shape), ref)
+
+
+# ------------------------------------------------------------------ localisation
+
+def _energy_at(tr, ants, grid, v, fs, W, bf):
+    def f(idx):
+        return float(oracle.image(tr, ants, grid, v, fs, W, BF_ORACLE[bf], lo=idx,
+                                  cnt=[1, 1, 1])[0, 0, 0])
+    return f
+
+
+def _check_batch(gpu, cfg, bf, seeds, rule_kw=None, ants=None):
+    rule_kw = rule_kw or {}
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in seeds]
+    traces = np.stack([sc["traces"] for sc in scans])
+    ants = scans[0]["antennas"] if ants is None else ants
+    grid = cfg.grid()
+    g_rule, o_rule = rule_pair(gpu, **rule_kw)
+    res = gpu_localize_batch(gpu, bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, g_rule)
+    ties = 0
+    for s, sc in enumerate(scans):
+        o = oracle.localize(sc["traces"], ants, grid, cfg.v, cfg.fs, cfg.window, BF_ORACLE[bf],
+                            o_rule)
+        summary = compare_localize(res[s], o, _energy_at(sc["traces"], ants, grid, cfg.v, cfg.fs,
+                                                          cfg.window, bf))
+        ties += summary["tie"]
+    assert ties <= max(1, len(seeds) // 4), f"{ties} near-ties in {len(seeds)} scans"
+    return res
+
+
+@pytest.mark.parametrize("bf", BFS)
+def test_localize_small_scans(gpu, bf):
+    _check_batch(gpu, phantom.CONFIGS["das2d_64"], bf, range(12))
+
+
+@pytest.mark.parametrize("metric", [1, 2, 3])
+def test_localize_other_metrics(gpu, metric):
+    _check_batch(gpu, phantom.CONFIGS["das2d_64"], 0, range(6), {"metric": metric})
+
+
+def test_localize_manual_decimation_and_framing(gpu):
+    _check_batch(gpu, phantom.CONFIGS["das2d_64"], 1, range(6),
+                 {"mode": 0, "decimation": 3, "frame_num": 1, "frame_den": 3, "min_segment": 2})
+
+
+@pytest.mark.parametrize("bf", [1, 2])
+def test_localize_512_grid_with_clutter(gpu, bf):
+    # full-size 512 x 512, 32 antennas, 2048 samples, clutter: the launch
+    # configuration the benchmark times
+    res = _check_batch(gpu, phantom.CONFIGS["dmas2d_512"], bf, range(4))
+    for r in res:
+        assert r["points_evaluated"] < 512 * 512 / 4
+
+
+def test_localize_writes_the_mixed_resolution_image(gpu):
+    cfg = phantom.CONFIGS["das2d_64"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 2)
+    g_rule, o_rule = rule_pair(gpu)
+    grid = cfg.grid()
+    res, img = gpu_localize_batch(gpu, 0, sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs,
+                                  cfg.window, g_rule, image=True)
+    r = res[0]
+    full = oracle.image(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, oracle.DAS)
+    img = img[0]
+    written = img >= 0
+    # the decimated lattice and the final region are written, nothing else
+    D, off = r["decim"], r["offset"]
+    expect = np.zeros_like(written)
+    expect[0, off[1]::D, off[0]::D] = True
+    expect[0, r["roi_lo"][1]:r["roi_hi"][1], r["roi_lo"][0]:r["roi_hi"][0]] = True
+    assert np.array_equal(written, expect)
+    assert np.max(np.abs(img[written] - full[written])) <= IMG_TOL * full.max()
+
+
+def test_localize_three_d_small(gpu):
+    cfg = phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(40, 40, 40),
+                               n_antennas=24, n_samples=1024, n_clutter=10)
+    for bf in BFS:
+        _check_batch(gpu, cfg, bf, range(3), {"min_segment": 2})
+
+
+def test_localize_edge_cases(gpu):
+    cfg = phantom.CONFIGS["das2d_64"]
+    grid = cfg.grid()
+    good = phantom.make_scan(cfg, phantom.BASE_SEED)
+    zero = np.zeros_like(good["traces"])
+    nan = good["traces"].copy()
+    nan[3, 100] = np.nan
+    traces = np.stack([good["traces"], zero, nan, good["traces"]])
+    g_rule, o_rule = rule_pair(gpu)
+    res = gpu_localize_batch(gpu, 0, traces, good["antennas"], grid, cfg.v, cfg.fs, cfg.window,
+                             g_rule)
+    for s in range(4):
+        o = oracle.localize(traces[s], good["antennas"], grid, cfg.v, cfg.fs, cfg.window,
+                            oracle.DAS, o_rule)
+        compare_localize(res[s], o)
+    assert res[1]["stop_reason"] == oracle.STOP_NO_TARGET
+    assert res[2]["status"] == -4
+    assert res[0]["loc_idx"] == res[3]["loc_idx"]
+
+
+def test_localize_degenerate_grids(gpu):
+    tr, ants, _, v, fs, W = random_case(4, 256, (1, 1, 1), 0.05, 6, seed=3)
+    for n in [(1, 1, 1), (2, 1, 1), (5, 3, 1)]:
+        grid = {"dim": 2, "n": list(n), "origin": [0.001, -0.002, 0.0],
+                "pitch": [1e-3, 1e-3, 1.0]}
+        g_rule, o_rule = rule_pair(gpu, mode=0, decimation=1, min_segment=1)
+        res = gpu_localize_batch(gpu, 0, tr, ants, grid, v, fs, W, g_rule)
+        o = oracle.localize(tr, ants, grid, v, fs, W, oracle.DAS, o_rule)
+        compare_localize(res[0], o, _energy_at(tr, ants, grid, v, fs, W, 0))
+
+
+# ------------------------------------------------------------------ full size
+
+def test_full_resolution_512_literal_dmas(gpu):
+    cfg = phantom.CONFIGS["dmas2d_512"]
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in range(2)]
+    traces = np.stack([s["traces"] for s in scans])
+    ants = scans[0]["antennas"]
+    grid = cfg.grid()
+    img, peak = gpu_image_batch(gpu, 2, traces, ants, grid, cfg.v, cfg.fs, cfg.window)
+    ref = oracle.image(traces[0], ants, grid, cfg.v, cfg.fs, cfg.window, oracle.DMAS)
+    assert_image_close(img[0], ref)
+    flat = ref.ravel()
+    assert abs(flat[int(peak[0])] - flat.max()) <= IMG_TOL * flat.max()
+    # second scan: sampled focal points, each computed alone by the oracle
+    rng = np.random.default_rng(2)
+    pts = rng.integers(0, 512, size=(64, 2))
+    ref1 = np.array([oracle.image(traces[1], ants, grid, cfg.v, cfg.fs, cfg.window, oracle.DMAS,
+                                  lo=[x, y, 0], cnt=[1, 1, 1])[0, 0, 0] for x, y in pts])
+    got1 = np.array([img[1, 0, y, x] for x, y in pts])
+    scale = float(img[1].max())
+    assert np.max(np.abs(got1 - ref1)) <= IMG_TOL * scale
+
+
+def test_full_resolution_256_cube_sampled(gpu):
+    cfg = phantom.CONFIGS["hemi3d_256"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED)
+    grid = cfg.grid()
+    for bf in (0, 1):
+        img, peak = gpu_image_batch(gpu, bf, sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs,
+                                    cfg.window)
+        rng = np.random.default_rng(3 + bf)
+        pts = rng.integers(0, 256, size=(48, 3))
+        pk = int(peak[0])
+        pts = np.vstack([pts, [[pk % 256, (pk // 256) % 256, pk // 65536]]])
+        ref = np.array([oracle.image(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs,
+                                     cfg.window, BF_ORACLE[bf], lo=list(p), cnt=[1, 1, 1])[0, 0, 0]
+                        for p in pts])
+        got = np.array([img[0, z, y, x] for x, y, z in pts])
+        assert np.max(np.abs(got - ref)) <= IMG_TOL * float(img[0].max())
+
+
+def test_localize_256_cube_das(gpu):
+    _check_batch(gpu, phantom.CONFIGS["hemi3d_256"], 0, range(1))
