@@ -192,6 +192,35 @@ int uwb_localize_batch(int batch, const float* traces, int M, int N,
                        int beamformer, const uwb_rule* rule, void* workspace,
                        size_t ws_bytes, uwb_result* out, float* image, void* stream);
 
+/* uwb_localize_batch for callers that may not allocate device memory.
+ *
+ * Some callers cannot call cudaMalloc once they are running: acquisition
+ * loops that must keep a fixed device-memory footprint and predictable
+ * latency for the whole session, and plug-ins hosted by a framework that
+ * owns every device allocation through its own pool. They cannot provide
+ * the workspace uwb_localize_batch asks for, so this entry point takes none:
+ * its scratch is a fixed array of UWB_NOALLOC_SCRATCH_BYTES (16 MiB) inside
+ * the library, which every GPU that loads the library keeps until the
+ * process exits. The paper has no counterpart to this; it is a deployment
+ * convenience. Arguments and results are those of uwb_localize_batch.
+ *  - It allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ *    library call); inputs and outputs still come from the caller.
+ *  - Calls whose scratch need (uwb_localize_workspace for the same
+ *    arguments) exceeds UWB_NOALLOC_SCRATCH_BYTES are rejected with
+ *    UWB_ERR_WORKSPACE before any launch; split the batch instead.
+ *  - The first call on a device looks up the address of that device's copy
+ *    of the array; make that first call before any stream capture.
+ *  - Every call on a device uses the same array, and the array keeps the
+ *    last call's contents (each call clears what it needs zeroed). Calls
+ *    that overlap on the GPU (other streams, other host threads) race on
+ *    it: serialise them, for example on one stream. */
+#define UWB_NOALLOC_SCRATCH_BYTES (16u << 20)
+int uwb_localize_batch_noalloc(int batch, const float* traces, int M, int N,
+                               const float* antennas, long long antenna_stride,
+                               const uwb_grid* grid, double v, double fs, int window,
+                               int beamformer, const uwb_rule* rule, uwb_result* out,
+                               float* image, void* stream);
+
 /* Optional phase timing of uwb_localize / uwb_localize_batch (profiling aid).
  * While enabled, each call records CUDA events on its own stream around its
  * phases: 0 = decimated energy profile, 1 = segment selection and work

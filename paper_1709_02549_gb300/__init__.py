@@ -18,7 +18,7 @@ __all__ = [
     "RESULT_DTYPE", "lib", "make_grid", "uwb_default_rule", "uwb_decimation", "uwb_das_image",
     "uwb_dmas_image", "uwb_image_batch", "uwb_localize_workspace", "uwb_localize",
     "uwb_localize_batch", "uwb_device_status", "uwb_last_error", "results_from_device",
-    "uwb_phase_timing", "uwb_phase_times",
+    "uwb_phase_timing", "uwb_phase_times", "uwb_localize_batch_noalloc",
     "UwbError",
 ]
 
@@ -96,6 +96,8 @@ def lib() -> ctypes.CDLL:
             "uwb_localize": (i, [vp, i, i, vp, gp, d, d, i, i, rp, vp, sz, vp, vp, vp]),
             "uwb_localize_batch": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, sz, vp, vp,
                                        vp]),
+            "uwb_localize_batch_noalloc": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, vp,
+                                               vp]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -230,6 +232,24 @@ def uwb_localize_batch(traces, antennas, grid, v, fs, window, beamformer, rule: 
                                     workspace.numel() * workspace.element_size(),
                                     _ptr(out, "out"), _f32(image, "image", True),
                                     _stream(stream)), "uwb_localize_batch")
+
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def uwb_localize_batch_noalloc(traces, antennas, grid, v, fs, window, beamformer,
+                               rule: UwbRule, out, image=None, stream=None):
+    """uwb_localize_batch without a workspace: the library's built-in scratch
+    (NOALLOC_SCRATCH_BYTES per device) is used instead, for callers that may not
+    allocate device memory. Calls on one device must not overlap on the GPU."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_localize_batch_noalloc(B, _f32(traces, "traces"), M, N,
+                                            _f32(antennas, "antennas"), stride,
+                                            ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                            int(window), int(beamformer), ctypes.byref(rule),
+                                            _ptr(out, "out"), _f32(image, "image", True),
+                                            _stream(stream)), "uwb_localize_batch_noalloc")
 
 
 def uwb_phase_timing(enable: bool) -> None:

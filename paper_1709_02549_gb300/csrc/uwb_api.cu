@@ -649,6 +649,61 @@ int uwb_localize_batch(int batch, const float* traces, int M, int N, const float
                        beamformer, rule, workspace, ws_bytes, out, image, stream);
 }
 
+}  // extern "C"
+
+// Scratch of uwb_localize_batch_noalloc: a fixed array in the library image,
+// one copy per device, so callers that may not allocate still get a
+// workspace. In host code `g_noalloc_scratch` only names the symbol; the
+// device address comes from cudaGetSymbolAddress, looked up once per device
+// with that device current.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[UWB_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};
+
+int noalloc_scratch(void** out) {
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (d < 0 || d >= 64) return fail(UWB_ERR_UNSUPPORTED, "device ordinal %d", d);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[d]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[d] = p;
+  }
+  *out = g_noalloc_ptr[d];
+  return UWB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int uwb_localize_batch_noalloc(int batch, const float* traces, int M, int N,
+                               const float* antennas, long long antenna_stride,
+                               const uwb_grid* grid, double v, double fs, int window,
+                               int beamformer, const uwb_rule* rule, uwb_result* out,
+                               float* image, void* stream) {
+  const size_t need = uwb_localize_workspace(batch, M, N, grid, beamformer, rule);
+  if (need == 0) {
+    // invalid arguments: let the regular checks name the problem
+    return localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                         beamformer, rule, nullptr, 0, out, image, stream);
+  }
+  if (need > UWB_NOALLOC_SCRATCH_BYTES)
+    return fail(UWB_ERR_WORKSPACE,
+                "this call needs %zu bytes of scratch but the built-in scratch holds %u; "
+                "use a smaller batch or uwb_localize_batch with a workspace",
+                need, UWB_NOALLOC_SCRATCH_BYTES);
+  void* scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st) return st;
+  return localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                       beamformer, rule, scratch, UWB_NOALLOC_SCRATCH_BYTES, out, image, stream);
+}
+
 int uwb_phase_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);
   drop_records();
