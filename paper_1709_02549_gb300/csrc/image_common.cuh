@@ -32,15 +32,11 @@ namespace uwb {
 // Bounded waits: a staging wait gives up after this many try_wait probes.
 constexpr long kWaitProbes = 1L << 24;
 
-template <int BF>
+template <int BF, int V>
 struct KernelShape {
   static constexpr int threads = (BF == BF_DMAS_LIT) ? 128 : 256;
-};
-
-// Window chunk of the literal-DMAS kernel for a given antenna register block.
-template <int MMAX>
-struct LitChunk {
-  static constexpr int KC = MMAX <= 16 ? 4 : (MMAX <= 32 ? 2 : 1);
+  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas
+  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : 1;
 };
 
 // -------------------------------------------------------------- DAS / DMAS-identity
@@ -117,23 +113,27 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
 }
 
 // ------------------------------------------------------------------ literal DMAS
-// sum_{i<j} x_i x_j with every product formed explicitly (M(M-1)/2 FMAs),
-// spread over eight accumulators for instruction-level parallelism.
+// Two window samples (k, k+1) travel together as a float2, so every antenna
+// pair costs one paired FMA for both samples: sum_{i<j} x_i x_j with every
+// product formed explicitly (MMAX(MMAX-1)/2 paired FMAs), over eight
+// accumulators for instruction-level parallelism. Antenna slots beyond M hold
+// zeros and add nothing.
 template <int MMAX>
-__device__ __forceinline__ float pair_sum(const float (&x)[MMAX], int M) {
-  float acc[8];
+__device__ __forceinline__ float2 pair_sum2(const float2 (&x)[MMAX]) {
+  float2 acc[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) acc[a] = 0.f;
+  for (int a = 0; a < 8; ++a) acc[a] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int j = 1; j < MMAX; ++j) {
-    if (j < M) {
 #pragma unroll
-      for (int i = 0; i < j; ++i) acc[(i + j) & 7] = fmaf(x[i], x[j], acc[(i + j) & 7]);
-    }
+    for (int i = 0; i < j; ++i) acc[(i + j) & 7] = __ffma2_rn(x[i], x[j], acc[(i + j) & 7]);
   }
-  return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+  const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
+  const float2 s45 = __fadd2_rn(acc[4], acc[5]), s67 = __fadd2_rn(acc[6], acc[7]);
+  return __fadd2_rn(__fadd2_rn(s01, s23), __fadd2_rn(s45, s67));
 }
 
+// sTr holds MMAX rows; rows M..MMAX-1 are zero (written at kernel start).
 template <int MMAX, bool STAGED>
 __device__ __forceinline__ float energy_literal(const ImgParams& P, const float* __restrict__ sTr,
                                                 const float* __restrict__ sAnt,
@@ -141,58 +141,59 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
                                                 const float* __restrict__ gTr, int nlo,
                                                 int cl_lo, int cl_hi, float px, float py,
                                                 float pz) {
-  constexpr int KC = LitChunk<MMAX>::KC;
   const int T = blockDim.x, tid = threadIdx.x;
   const int M = P.M;
   const float hf = static_cast<float>(P.h);
   // delays of every antenna for this focal point: (sample offset, fraction)
-  for (int i = 0; i < M; ++i) {
-    const float dx = px - sAnt[3 * i + 0];
-    const float dy = py - sAnt[3 * i + 1];
-    const float dz = pz - sAnt[3 * i + 2];
-    const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    const float t = fmaf(d, P.kscale, -hf);
-    const float fl = floorf(t);
-    int n0 = static_cast<int>(fl);
-    if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo;
-    sNF[i * T + tid] = make_float2(__int_as_float(n0), t - fl);
+  for (int i = 0; i < MMAX; ++i) {
+    int n0 = 0;
+    float f = 0.f;
+    if (i < M) {
+      const float dx = px - sAnt[3 * i + 0];
+      const float dy = py - sAnt[3 * i + 1];
+      const float dz = pz - sAnt[3 * i + 2];
+      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float t = fmaf(d, P.kscale, -hf);
+      const float fl = floorf(t);
+      f = t - fl;
+      n0 = static_cast<int>(fl);
+      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo;
+    }
+    sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
   }
   float energy = 0.f;
-  for (int k0 = 0; k0 < P.W; k0 += KC) {
-    float x[KC][MMAX];
+  for (int k0 = 0; k0 < P.W; k0 += 2) {
+    float2 x[MMAX];
 #pragma unroll
     for (int i = 0; i < MMAX; ++i) {
-      if (i < M) {
-        const float2 nf = sNF[i * T + tid];
-        const int off = __float_as_int(nf.x) + k0;
-        const float f = nf.y;
-        float y[KC + 1];
-        if (STAGED) {
-          const float* row = sTr + i * P.span + off;
-#pragma unroll
-          for (int c = 0; c <= KC; ++c) y[c] = row[c];
-        } else {
-          const float* row = gTr + static_cast<size_t>(i) * P.N;
-#pragma unroll
-          for (int c = 0; c <= KC; ++c) {
-            const int n = off + c;
-            y[c] = (n >= 0 && n < P.N) ? __ldg(row + n) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < KC; ++c) x[c][i] = fmaf(f, y[c + 1] - y[c], y[c]);
+      const float2 nf = sNF[i * T + tid];
+      const int off = __float_as_int(nf.x) + k0;
+      const float f = nf.y;
+      float y0, y1, y2;
+      if (STAGED) {
+        const float* row = sTr + i * P.span + off;
+        y0 = row[0];
+        y1 = row[1];
+        y2 = row[2];
+      } else if (i < M) {
+        const float* row = gTr + static_cast<size_t>(i) * P.N;
+        y0 = (off >= 0 && off < P.N) ? __ldg(row + off) : 0.f;
+        y1 = (off + 1 >= 0 && off + 1 < P.N) ? __ldg(row + off + 1) : 0.f;
+        y2 = (off + 2 >= 0 && off + 2 < P.N) ? __ldg(row + off + 2) : 0.f;
       } else {
-#pragma unroll
-        for (int c = 0; c < KC; ++c) x[c][i] = 0.f;
+        y0 = y1 = y2 = 0.f;
       }
+      // x(k) = (1 - f) y[n0+k] + f y[n0+k+1] for k = k0 and k0 + 1
+      const float2 lo = make_float2(y0, y1);
+      const float2 t = __ffma2_rn(make_float2(-f, -f), lo, lo);
+      x[i] = __ffma2_rn(make_float2(f, f), make_float2(y1, y2), t);
+      // issue the loads eight antennas at a time: hoisting all of them ahead
+      // of the interpolation would not fit the register budget
+      if ((i & 7) == 7) asm volatile("" ::: "memory");
     }
-#pragma unroll
-    for (int c = 0; c < KC; ++c) {
-      if (k0 + c < P.W) {
-        const float p = pair_sum<MMAX>(x[c], M);
-        energy = fmaf(p, p, energy);
-      }
-    }
+    const float2 p = pair_sum2<MMAX>(x);
+    energy = fmaf(p.x, p.x, energy);
+    if (k0 + 1 < P.W) energy = fmaf(p.y, p.y, energy);
   }
   return energy;
 }
@@ -202,16 +203,18 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
 // (literal DMAS). Dynamic shared memory: [M][span] traces | [M*3] antennas |
 // (literal) [M][T] delays | mbarrier and reduction slots.
 template <int BF, int V>
-__global__ void __launch_bounds__(KernelShape<BF>::threads)
+__global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V>::min_blocks)
     k_image(const __grid_constant__ CUtensorMap tmap, const ImgParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
   const int M = P.M;
+  // literal DMAS keeps V (>= M) trace rows; rows M..V-1 stay zero
+  const int rows = (BF == BF_DMAS_LIT) ? V : M;
   float* sTr = reinterpret_cast<float*>(smem_raw);
-  float* sAnt = sTr + static_cast<size_t>(M) * P.span;
+  float* sAnt = sTr + static_cast<size_t>(rows) * P.span;
   const int ant_words = (3 * M + 3) & ~3;
   float2* sNF = reinterpret_cast<float2*>(sAnt + ant_words);
-  const size_t nf_words = (BF == BF_DMAS_LIT) ? static_cast<size_t>(M) * T * 2 : 0;
+  const size_t nf_words = (BF == BF_DMAS_LIT) ? static_cast<size_t>(V) * T * 2 : 0;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sAnt + ant_words + nf_words);
   unsigned long long* sKey = reinterpret_cast<unsigned long long*>(bar + 1);  // [32]
   int* sInt = reinterpret_cast<int*>(sKey + 32);                              // [4]
@@ -225,6 +228,8 @@ __global__ void __launch_bounds__(KernelShape<BF>::threads)
 
   const bool tma_ok = P.use_tma && ((smem_u32(sTr) & 127u) == 0);
   if (tid == 0) mbar_init(bar, 1);
+  if (BF == BF_DMAS_LIT)
+    for (int j = tid; j < (rows - M) * P.span; j += T) sTr[M * P.span + j] = 0.f;
   __syncthreads();
   uint32_t phase = 0;
 

@@ -175,6 +175,8 @@ struct Variant {
   int bf, v, threads;
   int tdim[3];
   int wpad;
+  int rows;           // trace rows in shared memory
+  size_t smem_budget; // shared memory per CTA the span is sized for
 };
 
 int pick_variant(int bf, int M, int W, int dim, Variant* out) {
@@ -183,9 +185,10 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out) {
   if (bf == BF_DMAS_LIT) {
     if (M > 64) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 64 (M=%d)", M);
     var.v = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
-    const int kc = var.v <= 16 ? 4 : (var.v <= 32 ? 2 : 1);
-    var.wpad = (W + kc - 1) / kc * kc;
+    var.wpad = (W + 1) / 2 * 2;  // window samples go in pairs
     var.threads = 128;
+    var.rows = var.v;
+    var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
     if (dim == 2) {
       var.tdim[0] = 16; var.tdim[1] = 8; var.tdim[2] = 1;
     } else {
@@ -195,6 +198,8 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out) {
     var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : 32;
     var.wpad = (W + var.v - 1) / var.v * var.v;
     var.threads = 256;
+    var.rows = M;
+    var.smem_budget = 56 * 1024;
     if (dim == 2) {
       var.tdim[0] = 32; var.tdim[1] = 8; var.tdim[2] = 1;
     } else {
@@ -222,15 +227,17 @@ void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
     }
 }
 
-// Samples staged per antenna: what a shared-memory budget allows, at most
-// one TMA box width (256).
-int pick_span(int bf, int M, int threads) {
-  const size_t budget = bf == BF_DMAS_LIT ? 100 * 1024 : 56 * 1024;
-  const size_t fixed = image_smem_bytes(bf, M, 0, threads);
-  long long span = fixed >= budget ? 4 : static_cast<long long>((budget - fixed) / (4 * M));
+// Samples staged per antenna: what the variant's shared-memory budget allows,
+// at most one TMA box width (256), at least the window plus a margin.
+int pick_span(const Variant& var, int M) {
+  const size_t fixed = image_smem_bytes(var.bf, M, var.rows, 0, var.threads);
+  long long span = fixed >= var.smem_budget
+                       ? 0
+                       : static_cast<long long>((var.smem_budget - fixed) / (4 * var.rows));
   span &= ~3LL;
   if (span > 256) span = 256;
-  if (span < 4) span = 4;
+  const long long floor_span = (var.wpad + 8 + 3) & ~3LL;
+  if (span < floor_span) span = floor_span;
   return static_cast<int>(span);
 }
 
@@ -310,7 +317,7 @@ int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const 
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
   if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
   pick_warp(var.tdim, delta, p.wdim);
-  const size_t smem = image_smem_bytes(var.bf, p.M, p.span, var.threads);
+  const size_t smem = image_smem_bytes(var.bf, p.M, var.rows, p.span, var.threads);
   const int occ = occupancy(var, smem);
   if (occ < 1) return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
   long long ctas = static_cast<long long>(dev.sms) * occ;
@@ -345,7 +352,7 @@ int image_impl(int batch, int beamformer, const float* traces, int M, int N, con
   Device* dev;
   if ((st = device(&dev))) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  const int span = pick_span(bf, M, var.threads);
+  const int span = pick_span(var, M);
   CUtensorMap map;
   const int use_tma = encode_traces(geo, traces, span, &map);
   ImgParams p = base_params(geo, traces, ant, ant_stride, var, span, use_tma, dev->status);
@@ -491,7 +498,7 @@ int localize_impl(int batch, const float* traces, int M, int N, const float* ant
   cudaError_t e = cudaMemsetAsync(ws + wl.keys, 0, wl.status + 4 - wl.keys, cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
-  const int span = pick_span(bf, M, var.threads);
+  const int span = pick_span(var, M);
   CUtensorMap map;
   const int use_tma = encode_traces(geo, traces, span, &map);
   PhaseTimer timer(cs);
