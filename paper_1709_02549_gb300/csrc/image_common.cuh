@@ -114,23 +114,48 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
 
 // ------------------------------------------------------------------ literal DMAS
 // Two window samples (k, k+1) travel together as a float2, so every antenna
-// pair costs one paired FMA for both samples: sum_{i<j} x_i x_j with every
-// product formed explicitly (MMAX(MMAX-1)/2 paired FMAs), over eight
-// accumulators for instruction-level parallelism. Antenna slots beyond M hold
-// zeros and add nothing.
-template <int MMAX>
-__device__ __forceinline__ float2 pair_sum2(const float2 (&x)[MMAX]) {
-  float2 acc[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) acc[a] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int j = 1; j < MMAX; ++j) {
-#pragma unroll
-    for (int i = 0; i < j; ++i) acc[(i + j) & 7] = __ffma2_rn(x[i], x[j], acc[(i + j) & 7]);
+// pair costs one paired FMA for both samples. The pair sum
+// sum_{i<j} x_i x_j forms every product explicitly (MMAX(MMAX-1)/2 paired
+// FMAs over eight accumulators), streaming over j: antenna j is interpolated
+// and immediately multiplied with antennas 0..j-1, while the samples of
+// antenna j+1 are already being loaded. Antenna slots beyond M read zero rows
+// of shared memory (or zeros on the global path) and add nothing.
+
+// Raw inputs of one antenna's interpolation for one window pair.
+struct LitRaw {
+  float f, y0, y1, y2;
+};
+
+template <bool STAGED>
+__device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const float* __restrict__ sTr,
+                                           const float2* __restrict__ sNF,
+                                           const float* __restrict__ gTr, int i, int T, int tid,
+                                           int k0) {
+  const float2 nf = sNF[i * T + tid];
+  const int off = __float_as_int(nf.x) + k0;
+  LitRaw r;
+  r.f = nf.y;
+  if (STAGED) {
+    const float* row = sTr + i * P.span + off;
+    r.y0 = row[0];
+    r.y1 = row[1];
+    r.y2 = row[2];
+  } else if (i < P.M) {
+    const float* row = gTr + static_cast<size_t>(i) * P.N;
+    r.y0 = (off >= 0 && off < P.N) ? __ldg(row + off) : 0.f;
+    r.y1 = (off + 1 >= 0 && off + 1 < P.N) ? __ldg(row + off + 1) : 0.f;
+    r.y2 = (off + 2 >= 0 && off + 2 < P.N) ? __ldg(row + off + 2) : 0.f;
+  } else {
+    r.y0 = r.y1 = r.y2 = 0.f;
   }
-  const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
-  const float2 s45 = __fadd2_rn(acc[4], acc[5]), s67 = __fadd2_rn(acc[6], acc[7]);
-  return __fadd2_rn(__fadd2_rn(s01, s23), __fadd2_rn(s45, s67));
+  return r;
+}
+
+// x(k) = (1 - f) y[n0+k] + f y[n0+k+1] for the two samples of the pair
+__device__ __forceinline__ float2 lit_interp(const LitRaw& r) {
+  const float2 lo = make_float2(r.y0, r.y1);
+  const float2 t = __ffma2_rn(make_float2(-r.f, -r.f), lo, lo);
+  return __ffma2_rn(make_float2(r.f, r.f), make_float2(r.y1, r.y2), t);
 }
 
 // sTr holds MMAX rows; rows M..MMAX-1 are zero (written at kernel start).
@@ -164,34 +189,23 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
   float energy = 0.f;
   for (int k0 = 0; k0 < P.W; k0 += 2) {
     float2 x[MMAX];
+    float2 acc[8];
 #pragma unroll
-    for (int i = 0; i < MMAX; ++i) {
-      const float2 nf = sNF[i * T + tid];
-      const int off = __float_as_int(nf.x) + k0;
-      const float f = nf.y;
-      float y0, y1, y2;
-      if (STAGED) {
-        const float* row = sTr + i * P.span + off;
-        y0 = row[0];
-        y1 = row[1];
-        y2 = row[2];
-      } else if (i < M) {
-        const float* row = gTr + static_cast<size_t>(i) * P.N;
-        y0 = (off >= 0 && off < P.N) ? __ldg(row + off) : 0.f;
-        y1 = (off + 1 >= 0 && off + 1 < P.N) ? __ldg(row + off + 1) : 0.f;
-        y2 = (off + 2 >= 0 && off + 2 < P.N) ? __ldg(row + off + 2) : 0.f;
-      } else {
-        y0 = y1 = y2 = 0.f;
-      }
-      // x(k) = (1 - f) y[n0+k] + f y[n0+k+1] for k = k0 and k0 + 1
-      const float2 lo = make_float2(y0, y1);
-      const float2 t = __ffma2_rn(make_float2(-f, -f), lo, lo);
-      x[i] = __ffma2_rn(make_float2(f, f), make_float2(y1, y2), t);
-      // issue the loads eight antennas at a time: hoisting all of them ahead
-      // of the interpolation would not fit the register budget
-      if ((i & 7) == 7) asm volatile("" ::: "memory");
+    for (int a = 0; a < 8; ++a) acc[a] = make_float2(0.f, 0.f);
+    LitRaw next = lit_load<STAGED>(P, sTr, sNF, gTr, 0, T, tid, k0);
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+      const LitRaw cur = next;
+      if (j + 1 < MMAX) next = lit_load<STAGED>(P, sTr, sNF, gTr, j + 1, T, tid, k0);
+      x[j] = lit_interp(cur);
+#pragma unroll
+      for (int i = 0; i < j; ++i) acc[(i + j) & 7] = __ffma2_rn(x[i], x[j], acc[(i + j) & 7]);
+      // keep later loads from being hoisted above these products
+      asm volatile("" ::: "memory");
     }
-    const float2 p = pair_sum2<MMAX>(x);
+    const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
+    const float2 s45 = __fadd2_rn(acc[4], acc[5]), s67 = __fadd2_rn(acc[6], acc[7]);
+    const float2 p = __fadd2_rn(__fadd2_rn(s01, s23), __fadd2_rn(s45, s67));
     energy = fmaf(p.x, p.x, energy);
     if (k0 + 1 < P.W) energy = fmaf(p.y, p.y, energy);
   }
