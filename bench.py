@@ -131,6 +131,16 @@ def shard_first_scan(rank: int, batch: int) -> int:
     return rank * batch
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """Slowest rank's time (timing only; the data path has no collective)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_name(cfg, bf_name, batch):
     g = cfg.grid_n
     return (f"{cfg.name}: {g[0]}x{g[1]}" + (f"x{g[2]}" if cfg.dim == 3 else "") +
@@ -278,11 +288,7 @@ def main():
     calls, phase_ms = uwb.uwb_phase_times()
     uwb.uwb_phase_timing(False)
     clock_info = clocks.stop()
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dist, "cuda")
     ms_per_step = total_ms / args.steps
     value = world * B * args.steps / (total_ms / 1e3)
 
@@ -356,11 +362,7 @@ def main():
         out_host.copy_(out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     e2e = {"value": world * B * args.steps / (e2e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(traces.numel() * 4),
            "d2h_bytes_per_step": int(out.numel())}
