@@ -36,13 +36,13 @@ template <int BF, int V>
 struct KernelShape {
   static constexpr int threads = (BF == BF_DMAS_LIT) ? 128 : 256;
   // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas
-  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : 1;
+  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : (BF == BF_DAS ? (V <= 20 ? 4 : 3) : (V <= 20 ? 3 : 2));
 };
 
 // -------------------------------------------------------------- DAS / DMAS-identity
 template <int BF, int WT, bool STAGED>
 __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __restrict__ sTr,
-                                            const float* __restrict__ sAnt,
+                                            const float4* __restrict__ sAnt,
                                             const float* __restrict__ gTr, int nlo, int cl_lo,
                                             int cl_hi, float px, float py, float pz) {
   float energy = 0.f;
@@ -56,9 +56,10 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
     }
     const float hoff = static_cast<float>(P.h - k0);
     for (int i = 0; i < M; ++i) {
-      const float dx = px - sAnt[3 * i + 0];
-      const float dy = py - sAnt[3 * i + 1];
-      const float dz = pz - sAnt[3 * i + 2];
+      const float4 a = sAnt[i];
+      const float dx = px - a.x;
+      const float dy = py - a.y;
+      const float dz = pz - a.z;
       const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       const float t = fmaf(d, P.kscale, -hoff);  // u_i - h + k0
       const float fl = floorf(t);
@@ -161,7 +162,7 @@ __device__ __forceinline__ float2 lit_interp(const LitRaw& r) {
 // sTr holds MMAX rows; rows M..MMAX-1 are zero (written at kernel start).
 template <int MMAX, bool STAGED>
 __device__ __forceinline__ float energy_literal(const ImgParams& P, const float* __restrict__ sTr,
-                                                const float* __restrict__ sAnt,
+                                                const float4* __restrict__ sAnt,
                                                 float2* __restrict__ sNF,
                                                 const float* __restrict__ gTr, int nlo,
                                                 int cl_lo, int cl_hi, float px, float py,
@@ -174,9 +175,10 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
     int n0 = 0;
     float f = 0.f;
     if (i < M) {
-      const float dx = px - sAnt[3 * i + 0];
-      const float dy = py - sAnt[3 * i + 1];
-      const float dz = pz - sAnt[3 * i + 2];
+      const float4 a = sAnt[i];
+      const float dx = px - a.x;
+      const float dy = py - a.y;
+      const float dz = pz - a.z;
       const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       const float t = fmaf(d, P.kscale, -hf);
       const float fl = floorf(t);
@@ -225,11 +227,11 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   // literal DMAS keeps V (>= M) trace rows; rows M..V-1 stay zero
   const int rows = (BF == BF_DMAS_LIT) ? V : M;
   float* sTr = reinterpret_cast<float*>(smem_raw);
-  float* sAnt = sTr + static_cast<size_t>(rows) * P.span;
-  const int ant_words = (3 * M + 3) & ~3;
-  float2* sNF = reinterpret_cast<float2*>(sAnt + ant_words);
+  // antennas as (x, y, z, 0): one broadcast 16-byte load per antenna
+  float4* sAnt = reinterpret_cast<float4*>(sTr + static_cast<size_t>(rows) * P.span);
+  float2* sNF = reinterpret_cast<float2*>(sAnt + M);
   const size_t nf_words = (BF == BF_DMAS_LIT) ? static_cast<size_t>(V) * T * 2 : 0;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sAnt + ant_words + nf_words);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(sNF) + nf_words);
   unsigned long long* sKey = reinterpret_cast<unsigned long long*>(bar + 1);  // [32]
   int* sInt = reinterpret_cast<int*>(sKey + 32);                              // [4]
 
@@ -283,7 +285,8 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
       // ---- stage scan `scan`: antennas, reachable sample window ----
       __syncthreads();  // every read of the previous window is complete
       const float* ga = P.ant + static_cast<long long>(scan) * P.ant_stride;
-      for (int j = tid; j < 3 * M; j += T) sAnt[j] = ga[j];
+      for (int j = tid; j < M; j += T)
+        sAnt[j] = make_float4(ga[3 * j + 0], ga[3 * j + 1], ga[3 * j + 2], 0.f);
       if (tid == 0) {
         sInt[0] = INT_MAX;
         sInt[1] = INT_MIN;
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
         float dn2 = 0.f, df2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const float av = sAnt[3 * i + a];
+          const float av = a == 0 ? sAnt[i].x : (a == 1 ? sAnt[i].y : sAnt[i].z);
           const float dn = av - fminf(fmaxf(av, bmin[a]), bmax[a]);
           const float df = fmaxf(fabsf(av - bmin[a]), fabsf(av - bmax[a]));
           dn2 = fmaf(dn, dn, dn2);

@@ -19,18 +19,10 @@
 //  * children without a decimated point or with a side below min_segment are
 //    not candidates; ties go to the lowest child index (bit 0 = high x half,
 //    bit 1 = high y, bit 2 = high z).
-#include <float.h>
-
 #include "uwb_internal.cuh"
 
 namespace uwb {
 namespace {
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
-}
 
 // Decimated-lattice index range [klo, khi) per axis of the points inside a
 // full-resolution box [lo, hi).
@@ -60,39 +52,49 @@ __device__ KBox lattice_in_box(const SelParams& P, const int lo[3], const int hi
 
 struct Stats {
   long long n;
-  double sum, mean, scatter;  // scatter = sum of squared deviations from the mean
+  double sum, mean, scatter;  // of the normalised energies; scatter = sum of squared deviations
 };
 
-// Two-pass statistics of the normalised energies inside a box (warp-wide).
-__device__ Stats box_stats(const SelParams& P, const float* prof, double pmax, const KBox& b) {
+// Lane-partial sum and sum of squares of the raw energies of the decimated
+// points inside a box (one pass, float64).
+__device__ __forceinline__ void lane_sums(const SelParams& P, const float* prof, const KBox& b,
+                                          double& s1, double& s2) {
   const int lane = threadIdx.x & 31;
+  const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
+  s1 = 0.0;
+  s2 = 0.0;
+  for (long long j = lane; j < b.n; j += 32) {
+    const int kx = b.klo[0] + static_cast<int>(j % nx);
+    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
+    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
+    const double v = static_cast<double>(
+        prof[kx + static_cast<long long>(P.cnt[0]) * (ky + static_cast<long long>(P.cnt[1]) * kz)]);
+    s1 += v;
+    s2 = fma(v, v, s2);
+  }
+}
+
+// Statistics of the normalised energies e = I / pmax inside a box: count, sum,
+// mean and scatter (sum of squared deviations, as sum e^2 - (sum e)^2 / n; the
+// energies are non-negative and bounded, so float64 keeps ~14 digits even for
+// nearly flat segments). float64 is this GPU's slow path, so one pass.
+__device__ Stats box_stats(const SelParams& P, const float* prof, double pmax, const KBox& b) {
   Stats st;
   st.n = b.n;
   st.sum = st.mean = st.scatter = 0.0;
   if (b.n == 0) return st;
-  const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
-  double s = 0.0;
-  for (long long j = lane; j < b.n; j += 32) {
-    const int kx = b.klo[0] + static_cast<int>(j % nx);
-    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
-    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
-    s += static_cast<double>(prof[kx + static_cast<long long>(P.cnt[0]) *
-                                           (ky + static_cast<long long>(P.cnt[1]) * kz)]) /
-         pmax;
+  double s1, s2;
+  lane_sums(P, prof, b, s1, s2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
   }
-  st.sum = warp_sum(s);
-  st.mean = st.sum / static_cast<double>(b.n);
-  double q = 0.0;
-  for (long long j = lane; j < b.n; j += 32) {
-    const int kx = b.klo[0] + static_cast<int>(j % nx);
-    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
-    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
-    const double e = static_cast<double>(prof[kx + static_cast<long long>(P.cnt[0]) *
-                                                   (ky + static_cast<long long>(P.cnt[1]) * kz)]) /
-                     pmax;
-    q += (e - st.mean) * (e - st.mean);
-  }
-  st.scatter = warp_sum(q);
+  const double n = static_cast<double>(b.n);
+  const double inv = 1.0 / pmax;
+  st.sum = s1 * inv;
+  st.mean = st.sum / n;
+  st.scatter = fmax(s2 * inv * inv - st.sum * st.sum / n, 0.0);
   return st;
 }
 

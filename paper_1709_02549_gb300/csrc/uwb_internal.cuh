@@ -50,11 +50,11 @@ struct ImgParams {
 };
 
 // Bytes of dynamic shared memory of the image kernel: [rows][span] traces
-// (rows = M, or the antenna register block for literal DMAS), [M*3] antennas
-// (padded to 4 words), the literal kernel's [rows][threads] (offset, fraction)
-// pairs, then an mbarrier, 32 reduction keys, 4 ints.
+// (rows = M, or the antenna register block for literal DMAS), [M] antennas as
+// float4, the literal kernel's [rows][threads] (offset, fraction) pairs, then
+// an mbarrier, 32 reduction keys, 4 ints.
 inline size_t image_smem_bytes(int bf, int M, int rows, int span, int threads) {
-  const size_t ant_words = (3 * static_cast<size_t>(M) + 3) & ~static_cast<size_t>(3);
+  const size_t ant_words = 4 * static_cast<size_t>(M);
   size_t b = (static_cast<size_t>(rows) * span + ant_words) * 4;
   if (bf == BF_DMAS_LIT) b += static_cast<size_t>(rows) * threads * 8;
   b = (b + 7) & ~static_cast<size_t>(7);
