@@ -192,6 +192,28 @@ int uwb_localize_batch(int batch, const float* traces, int M, int N,
                        int beamformer, const uwb_rule* rule, void* workspace,
                        size_t ws_bytes, uwb_result* out, float* image, void* stream);
 
+/* End-to-end localisation from HOST memory. traces_host [batch][M][N] and
+ * antennas_host ([M][3], or [batch][...] with antenna_stride) live in host
+ * memory (pinned memory lets the copies run asynchronously); out_host
+ * receives `batch` uwb_result records in host memory. Only the window of
+ * samples that some focal point of the grid can reach (round-trip delays over
+ * the grid's bounding box, plus the window and a margin) is copied to the
+ * device, with one strided copy; the localisation then runs as in
+ * uwb_localize_batch, and the results are copied back. Everything is queued
+ * on `stream`: host buffers must stay valid until it completes.
+ * workspace: device memory of uwb_localize_host_workspace(...) bytes (it holds
+ * the trace window, the antennas, the results and the search's scratch).
+ * h2d_bytes (optional, host) receives the bytes copied to the device. */
+size_t uwb_localize_host_workspace(int batch, const float* traces_host, int M, int N,
+                                   const float* antennas_host, long long antenna_stride,
+                                   const uwb_grid* grid, double v, double fs, int window,
+                                   int beamformer, const uwb_rule* rule);
+int uwb_localize_host(int batch, const float* traces_host, int M, int N,
+                      const float* antennas_host, long long antenna_stride, const uwb_grid* grid,
+                      double v, double fs, int window, int beamformer, const uwb_rule* rule,
+                      void* workspace, size_t ws_bytes, uwb_result* out_host,
+                      long long* h2d_bytes, void* stream);
+
 /* uwb_localize_batch for callers that may not allocate device memory.
  *
  * Some callers cannot call cudaMalloc once they are running: acquisition

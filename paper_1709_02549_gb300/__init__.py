@@ -19,6 +19,7 @@ __all__ = [
     "uwb_dmas_image", "uwb_image_batch", "uwb_localize_workspace", "uwb_localize",
     "uwb_localize_batch", "uwb_device_status", "uwb_last_error", "results_from_device",
     "uwb_phase_timing", "uwb_phase_times", "uwb_localize_batch_noalloc",
+    "uwb_localize_host_workspace", "uwb_localize_host",
     "UwbError",
 ]
 
@@ -98,6 +99,9 @@ def lib() -> ctypes.CDLL:
                                        vp]),
             "uwb_localize_batch_noalloc": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, vp,
                                                vp]),
+            "uwb_localize_host_workspace": (sz, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp]),
+            "uwb_localize_host": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, sz, vp,
+                                      ctypes.POINTER(ctypes.c_longlong), vp]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -232,6 +236,46 @@ def uwb_localize_batch(traces, antennas, grid, v, fs, window, beamformer, rule: 
                                     workspace.numel() * workspace.element_size(),
                                     _ptr(out, "out"), _f32(image, "image", True),
                                     _stream(stream)), "uwb_localize_batch")
+
+
+def _host_f32(a, name):
+    import torch
+    if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 host tensor")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def uwb_localize_host_workspace(traces_host, antennas_host, grid, v, fs, window, beamformer,
+                                rule: UwbRule) -> int:
+    B, M, N = traces_host.shape
+    stride = 0 if antennas_host.dim() == 2 else M * 3
+    n = lib().uwb_localize_host_workspace(B, _host_f32(traces_host, "traces"), M, N,
+                                          _host_f32(antennas_host, "antennas"), stride,
+                                          ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                          int(window), int(beamformer), ctypes.byref(rule))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_localize_host_workspace")
+    return n
+
+
+def uwb_localize_host(traces_host, antennas_host, grid, v, fs, window, beamformer, rule: UwbRule,
+                      workspace, out_host, stream=None) -> int:
+    """Host-memory localisation (traces [B, M, N] and antennas on the host, ideally
+    pinned; out_host a host uint8 tensor of B * RESULT_BYTES). Returns the bytes
+    copied host-to-device. Queued on the stream; synchronise before reading."""
+    B, M, N = traces_host.shape
+    stride = 0 if antennas_host.dim() == 2 else M * 3
+    if out_host.is_cuda or out_host.numel() * out_host.element_size() < B * RESULT_BYTES:
+        raise ValueError("out_host must be a host buffer of B * RESULT_BYTES bytes")
+    moved = ctypes.c_longlong(0)
+    _check(lib().uwb_localize_host(B, _host_f32(traces_host, "traces"), M, N,
+                                   _host_f32(antennas_host, "antennas"), stride,
+                                   ctypes.byref(make_grid(grid)), float(v), float(fs), int(window),
+                                   int(beamformer), ctypes.byref(rule), _ptr(workspace, "workspace"),
+                                   workspace.numel() * workspace.element_size(),
+                                   ctypes.c_void_p(out_host.data_ptr()), ctypes.byref(moved),
+                                   _stream(stream)), "uwb_localize_host")
+    return int(moved.value)
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -72,10 +72,10 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
 #pragma unroll
         for (int k = 0; k <= WT; ++k) y[k] = row[k];
       } else {
-        const float* row = gTr + static_cast<size_t>(i) * P.N;
+        const float* row = gTr + static_cast<size_t>(i) * P.pitch;
 #pragma unroll
         for (int k = 0; k <= WT; ++k) {
-          const int n = n0 + k;
+          const int n = n0 + k - P.n_begin;
           y[k] = (n >= 0 && n < P.N) ? __ldg(row + n) : 0.f;
         }
       }
@@ -142,10 +142,11 @@ __device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const float* __re
     r.y1 = row[1];
     r.y2 = row[2];
   } else if (i < P.M) {
-    const float* row = gTr + static_cast<size_t>(i) * P.N;
-    r.y0 = (off >= 0 && off < P.N) ? __ldg(row + off) : 0.f;
-    r.y1 = (off + 1 >= 0 && off + 1 < P.N) ? __ldg(row + off + 1) : 0.f;
-    r.y2 = (off + 2 >= 0 && off + 2 < P.N) ? __ldg(row + off + 2) : 0.f;
+    const float* row = gTr + static_cast<size_t>(i) * P.pitch;
+    const int o = off - P.n_begin;
+    r.y0 = (o >= 0 && o < P.N) ? __ldg(row + o) : 0.f;
+    r.y1 = (o + 1 >= 0 && o + 1 < P.N) ? __ldg(row + o + 1) : 0.f;
+    r.y2 = (o + 2 >= 0 && o + 2 < P.N) ? __ldg(row + o + 2) : 0.f;
   } else {
     r.y0 = r.y1 = r.y2 = 0.f;
   }
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
           if (tid == 0) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, static_cast<uint32_t>(M) * P.span * 4u);
-            tma_load_3d(sTr, &tmap, nlo, 0, scan, bar);
+            tma_load_3d(sTr, &tmap, nlo - P.n_begin, 0, scan, bar);
           }
           uint32_t ok = 0;
           for (long it = 0; it < kWaitProbes && !ok; ++it) ok = mbar_try_wait(bar, phase);
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
           const int total_s = M * P.span;
           for (int j = tid; j < total_s; j += T) {
             const int i = j / P.span;
-            const int n = nlo + (j - i * P.span);
-            sTr[j] = (n >= 0 && n < P.N) ? gTr[static_cast<size_t>(i) * P.N + n] : 0.f;
+            const int n = nlo + (j - i * P.span) - P.n_begin;
+            sTr[j] = (n >= 0 && n < P.N) ? gTr[static_cast<size_t>(i) * P.pitch + n] : 0.f;
           }
           __syncthreads();
         }

@@ -129,6 +129,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 // Scans of one call: shared sizes and geometry.
 struct Geo {
   int B, M, N, W, h;
+  int pitch;    // floats between antenna rows of the trace array
+  int n_begin;  // sample index of the first stored sample
   double v, fs;
   float kscale;
   uwb_grid g;
@@ -160,6 +162,8 @@ int check_common(int batch, const float* traces, int M, int N, const float* ant,
   geo->B = batch;
   geo->M = M;
   geo->N = N;
+  geo->pitch = N;
+  geo->n_begin = 0;
   geo->W = window;
   geo->h = window / 2;
   geo->v = v;
@@ -244,12 +248,13 @@ int pick_span(const Variant& var, int M) {
 int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* map) {
   memset(map, 0, sizeof *map);
   if (!g_encode) return 0;
-  if ((reinterpret_cast<uintptr_t>(traces) & 15) || (geo.N & 3) || geo.M > 256 || span > 256)
+  if ((reinterpret_cast<uintptr_t>(traces) & 15) || (geo.pitch & 3) || (geo.n_begin & 3) ||
+      geo.N < 1 || geo.M > 256 || span > 256)
     return 0;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(geo.N), static_cast<cuuint64_t>(geo.M),
                         static_cast<cuuint64_t>(geo.B)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(geo.N) * 4,
-                           static_cast<cuuint64_t>(geo.N) * geo.M * 4};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(geo.pitch) * 4,
+                           static_cast<cuuint64_t>(geo.pitch) * geo.M * 4};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(geo.M), 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(traces),
@@ -288,7 +293,9 @@ ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
   ImgParams p;
   memset(&p, 0, sizeof p);
   p.traces = traces;
-  p.trace_stride = static_cast<long long>(geo.M) * geo.N;
+  p.trace_stride = static_cast<long long>(geo.M) * geo.pitch;
+  p.pitch = geo.pitch;
+  p.n_begin = geo.n_begin;
   p.ant = ant;
   p.ant_stride = ant_stride;
   p.B = geo.B;
@@ -464,6 +471,10 @@ WsLayout ws_layout(int B, long long Pd) {
   return w;
 }
 
+int localize_core(const Geo& geo, const float* traces, const float* ant, long long ant_stride,
+                  int beamformer, const uwb_rule* rule, void* workspace, size_t ws_bytes,
+                  uwb_result* out, float* image, void* stream);
+
 int localize_impl(int batch, const float* traces, int M, int N, const float* ant,
                   long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
                   int beamformer, const uwb_rule* rule, void* workspace, size_t ws_bytes,
@@ -474,10 +485,21 @@ int localize_impl(int batch, const float* traces, int M, int N, const float* ant
   if ((st = check_rule(rule))) return st;
   if (!out) return fail(UWB_ERR_ARG, "null result array");
   if (ant_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  if (bf_of(beamformer) < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  return localize_core(geo, traces, ant, ant_stride, beamformer, rule, workspace, ws_bytes, out,
+                       image, stream);
+}
+
+// The device-resident search on validated arguments (traces as described by
+// geo's N / pitch / n_begin).
+int localize_core(const Geo& geo, const float* traces, const float* ant, long long ant_stride,
+                  int beamformer, const uwb_rule* rule, void* workspace, size_t ws_bytes,
+                  uwb_result* out, float* image, void* stream) {
+  int st;
+  const int batch = geo.B, M = geo.M, window = geo.W;
   const int bf = bf_of(beamformer);
-  if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
   Variant var;
-  if ((st = pick_variant(bf, M, window, grid->dim, &var))) return st;
+  if ((st = pick_variant(bf, M, window, geo.g.dim, &var))) return st;
   const Decim dc = decimate(geo.g, *rule);
   const WsLayout wl = ws_layout(batch, dc.Pd);
   if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
@@ -581,6 +603,88 @@ int localize_impl(int batch, const float* traces, int M, int N, const float* ant
   return UWB_OK;
 }
 
+// ---- host-buffer localisation: only the reachable sample window travels
+
+// Samples [w0, w0 + len) of every trace that any focal point of the grid can
+// read (round-trip delays over the grid's bounding box, the centred window,
+// its padding, and a margin), clipped to the recorded trace and aligned for
+// the tensor copies.
+struct HostWindow {
+  int w0, len, pitch;
+};
+
+HostWindow reachable_window(const Geo& geo, const float* ant_host, long long ant_stride) {
+  double bmin[3], bmax[3];
+  for (int a = 0; a < 3; ++a) {
+    const double p0 = geo.g.origin[a];
+    const double p1 = geo.g.origin[a] + (geo.g.n[a] - 1) * geo.g.pitch[a];
+    bmin[a] = std::fmin(p0, p1);
+    bmax[a] = std::fmax(p0, p1);
+  }
+  const double ks = 2.0 * geo.fs / geo.v;
+  const long long scans = ant_stride ? geo.B : 1;
+  double umin = 1e300, umax = -1e300;
+  for (long long s = 0; s < scans; ++s)
+    for (int i = 0; i < geo.M; ++i) {
+      const float* a = ant_host + s * ant_stride + 3 * i;
+      double dn2 = 0.0, df2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double av = a[k];
+        const double dn = av - std::fmin(std::fmax(av, bmin[k]), bmax[k]);
+        const double df = std::fmax(std::fabs(av - bmin[k]), std::fabs(av - bmax[k]));
+        dn2 += dn * dn;
+        df2 += df * df;
+      }
+      umin = std::fmin(umin, std::sqrt(dn2) * ks);
+      umax = std::fmax(umax, std::sqrt(df2) * ks);
+    }
+  // every kernel variant reads at most W + 32 samples past floor(u - h)
+  const double lo = std::floor(umin - geo.h) - 8.0;
+  const double hi = std::floor(umax - geo.h) + geo.W + 32 + 8.0;
+  long long w0 = lo < 0 ? 0 : static_cast<long long>(lo);
+  long long w1 = hi > geo.N ? geo.N : static_cast<long long>(hi);
+  w0 &= ~3LL;
+  if (w1 < w0) w1 = w0;
+  HostWindow w;
+  w.w0 = static_cast<int>(w0);
+  w.len = static_cast<int>(w1 - w0);
+  w.pitch = (w.len + 3) & ~3;
+  if (w.pitch < 4) w.pitch = 4;
+  return w;
+}
+
+struct HostLayout {
+  size_t traces, ants, results, local, total;
+};
+
+HostLayout host_layout(const Geo& geo, const HostWindow& w, long long ant_stride,
+                       const uwb_rule& rule) {
+  HostLayout h;
+  size_t off = 0;
+  h.traces = off;
+  off += align256(static_cast<size_t>(geo.B) * geo.M * w.pitch * 4);
+  h.ants = off;
+  off += align256(static_cast<size_t>(ant_stride ? geo.B : 1) * geo.M * 3 * 4);
+  h.results = off;
+  off += align256(static_cast<size_t>(geo.B) * sizeof(uwb_result));
+  h.local = off;
+  off += ws_layout(geo.B, decimate(geo.g, rule).Pd).total;
+  h.total = off;
+  return h;
+}
+
+int host_checks(int batch, const float* traces, int M, int N, const float* ant,
+                long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
+                int beamformer, const uwb_rule* rule, Geo* geo) {
+  int st = check_common(batch, traces, M, N, ant, grid, v, fs, window, geo);
+  if (st) return st;
+  if ((st = check_rule(rule))) return st;
+  if (ant_stride < 0 || (ant_stride != 0 && ant_stride < 3LL * M))
+    return fail(UWB_ERR_ARG, "antenna stride must be 0 or >= 3 M");
+  if (bf_of(beamformer) < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  return UWB_OK;
+}
+
 }  // namespace
 }  // namespace uwb
 
@@ -639,6 +743,74 @@ size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid, int
   if (check_common(batch, &dummy, M, N, &dummy, grid, 1.0, 1.0, 1, &geo)) return 0;
   if (check_rule(rule) || bf_of(beamformer) < 0) return 0;
   return ws_layout(batch, decimate(geo.g, *rule).Pd).total;
+}
+
+size_t uwb_localize_host_workspace(int batch, const float* traces_host, int M, int N,
+                                   const float* antennas_host, long long antenna_stride,
+                                   const uwb_grid* grid, double v, double fs, int window,
+                                   int beamformer, const uwb_rule* rule) {
+  Geo geo;
+  if (host_checks(batch, traces_host, M, N, antennas_host, antenna_stride, grid, v, fs, window,
+                  beamformer, rule, &geo))
+    return 0;
+  const HostWindow w = reachable_window(geo, antennas_host, antenna_stride);
+  return host_layout(geo, w, antenna_stride, *rule).total;
+}
+
+int uwb_localize_host(int batch, const float* traces_host, int M, int N,
+                      const float* antennas_host, long long antenna_stride, const uwb_grid* grid,
+                      double v, double fs, int window, int beamformer, const uwb_rule* rule,
+                      void* workspace, size_t ws_bytes, uwb_result* out_host,
+                      long long* h2d_bytes, void* stream) {
+  Geo geo;
+  int st = host_checks(batch, traces_host, M, N, antennas_host, antenna_stride, grid, v, fs,
+                       window, beamformer, rule, &geo);
+  if (st) return st;
+  if (!out_host) return fail(UWB_ERR_ARG, "null result array");
+  const HostWindow w = reachable_window(geo, antennas_host, antenna_stride);
+  const HostLayout hl = host_layout(geo, w, antenna_stride, *rule);
+  if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255)
+    return fail(UWB_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < hl.total)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, hl.total);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  float* dtr = reinterpret_cast<float*>(ws + hl.traces);
+  float* dant = reinterpret_cast<float*>(ws + hl.ants);
+  uwb_result* dres = reinterpret_cast<uwb_result*>(ws + hl.results);
+  const size_t ant_bytes = static_cast<size_t>(antenna_stride ? batch : 1) * M * 3 * 4;
+  long long moved = 0;
+  cudaError_t e;
+  if (w.len > 0) {
+    e = cudaMemcpy2DAsync(dtr, static_cast<size_t>(w.pitch) * 4, traces_host + w.w0,
+                          static_cast<size_t>(N) * 4, static_cast<size_t>(w.len) * 4,
+                          static_cast<size_t>(batch) * M, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "trace window copy");
+    moved += static_cast<long long>(batch) * M * w.len * 4;
+  }
+  if (antenna_stride) {
+    // pack the per-scan arrays densely on the device
+    e = cudaMemcpy2DAsync(dant, static_cast<size_t>(M) * 12, antennas_host,
+                          static_cast<size_t>(antenna_stride) * 4, static_cast<size_t>(M) * 12,
+                          static_cast<size_t>(batch), cudaMemcpyHostToDevice, cs);
+  } else {
+    e = cudaMemcpyAsync(dant, antennas_host, ant_bytes, cudaMemcpyHostToDevice, cs);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "antenna copy");
+  moved += static_cast<long long>(ant_bytes);
+  Geo dgeo = geo;
+  dgeo.N = w.len;
+  dgeo.pitch = w.pitch;
+  dgeo.n_begin = w.w0;
+  st = localize_core(dgeo, dtr, dant, antenna_stride ? 3LL * M : 0, beamformer, rule,
+                     ws + hl.local, hl.total - hl.local, dres, nullptr, stream);
+  if (st) return st;
+  e = cudaMemcpyAsync(out_host, dres, static_cast<size_t>(batch) * sizeof(uwb_result),
+                      cudaMemcpyDeviceToHost, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "result copy");
+  if (h2d_bytes) *h2d_bytes = moved;
+  return UWB_OK;
 }
 
 int uwb_localize(const float* traces, int M, int N, const float* antennas, const uwb_grid* grid,

@@ -25,8 +25,12 @@ struct LatBox {
 // and the lattice shape (uniform lattice) or each has its own box (per-scan
 // lattices with a tile prefix sum, used for the final regions).
 struct ImgParams {
-  const float* traces;       // [B][M][N]
+  // Sample n of antenna i of scan s is traces[s * trace_stride + i * pitch +
+  // (n - n_begin)] for n_begin <= n < n_begin + N, and 0 outside.
+  const float* traces;
   long long trace_stride;    // floats between scans
+  int pitch;                 // floats between antenna rows
+  int n_begin;               // sample index of the first stored sample
   const float* ant;          // [M][3] per scan
   long long ant_stride;      // floats between scans' antenna arrays (0 = shared)
   int B, M, N, W, h;

@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import phantom
-from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, dev,
+from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, dev, record_to_dict,
                     gpu_image_batch, gpu_localize_batch, rule_pair)
 
 pytestmark = pytest.mark.gpu
@@ -267,3 +267,39 @@ def test_full_resolution_256_cube_sampled(gpu):
 
 def test_localize_256_cube_das(gpu):
     _check_batch(gpu, phantom.CONFIGS["hemi3d_256"], 0, range(1))
+
+
+# ------------------------------------------------------------------ host-buffer entry point
+
+@pytest.mark.parametrize("name,bf,N,per_scan", [("dmas2d_512", 2, 2048, False),
+                                                 ("das2d_64", 1, 1021, False),
+                                                 ("das2d_64", 0, 1024, True)])
+def test_host_entry_point_matches_device_entry_point(gpu, name, bf, N, per_scan):
+    cfg = phantom.with_changes(phantom.CONFIGS[name], n_samples=N)
+    batch = phantom.make_batch(cfg, 5)
+    grid = cfg.grid()
+    ants = batch["antennas"]
+    if per_scan:
+        rng = np.random.default_rng(9)
+        ants = np.stack([ants + rng.normal(0, 1e-3, ants.shape).astype(np.float32)
+                         for _ in range(5)])
+    g_rule, _ = rule_pair(gpu)
+    want = gpu_localize_batch(gpu, bf, batch["traces"], ants, grid, cfg.v, cfg.fs, cfg.window,
+                              g_rule)
+    tr_h = torch.from_numpy(batch["traces"]).pin_memory()
+    an_h = torch.from_numpy(np.ascontiguousarray(ants))
+    ws = torch.empty(gpu.uwb_localize_host_workspace(tr_h, an_h, grid, cfg.v, cfg.fs, cfg.window,
+                                                     bf, g_rule), dtype=torch.uint8,
+                     device="cuda")
+    out_h = torch.empty(5 * gpu.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    moved = gpu.uwb_localize_host(tr_h, an_h, grid, cfg.v, cfg.fs, cfg.window, bf, g_rule, ws,
+                                  out_h)
+    torch.cuda.synchronize()
+    got = [record_to_dict(r) for r in out_h.numpy().view(gpu.RESULT_DTYPE)]
+    # only the reachable window of the traces crossed the bus
+    assert moved < tr_h.numel() * 4
+    for g, w in zip(got, want):
+        for key in ("status", "iters", "stop_reason", "roi_lo", "roi_hi", "loc_idx", "child",
+                    "points_evaluated"):
+            assert g[key] == w[key], key
+        assert g["peak"] == w["peak"]
