@@ -211,6 +211,58 @@ def cpu_baseline(cfg, bf, seconds):
                       f"({busy:.1f} s of oracle time)"}
 
 
+def run_presence(args, cfg, bf, uwb, torch):
+    """Device time of the tumour-presence test (two localisations + verdict) on a
+    batch of tumour scenes, and its verdicts on tumour and clutter-only scenes."""
+    B = args.batch
+    grid = cfg.grid()
+    rule = uwb.uwb_default_rule()
+    D1 = uwb.uwb_decimation(grid, rule)
+    D2 = args.decimation2 or max(1, round(2 * D1 / 3))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rates = {}
+    value = ms = None
+    for label, c in (("tumour", cfg), ("clutter_only", phantom.with_changes(cfg, n_tumors=(0, 0)))):
+        nb = B if label == "tumour" else max(B // 4, 1)
+        b = phantom.make_batch(c, nb, first_scan=0)
+        traces = torch.from_numpy(b["traces"]).to("cuda")
+        ants = torch.from_numpy(b["antennas"]).to("cuda")
+        ws = torch.empty(uwb.uwb_presence_workspace(nb, c.n_antennas, c.n_samples, grid, bf, rule,
+                                                    D2), dtype=torch.uint8, device="cuda")
+        o1 = torch.empty(nb * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        o2 = torch.empty_like(o1)
+        present = torch.empty(nb, dtype=torch.int32, device="cuda")
+
+        def step():
+            uwb.uwb_presence_batch(traces, ants, grid, c.v, c.fs, c.window, bf, rule, D2, ws, o1,
+                                   o2, present, stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if label == "tumour":
+            tot = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / args.steps
+            value = nb / (ms / 1e3)
+        rates[label] = float(present.float().mean().item())
+    return {"metric": "tumour-presence tests/s (two decimation factors, Section IV)",
+            "value": value, "unit": "scans/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, args.beamformer, B), "decimation": [D1, D2]},
+            "confirmed_rate": rates, "gpu_launches": 11 * args.steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,6 +276,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-scans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="localize", choices=["localize", "presence"],
+                    help="presence: time the two-decimation tumour-presence test instead")
+    ap.add_argument("--decimation2", type=int, default=0,
+                    help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     cfg = phantom.CONFIGS[args.config]
@@ -245,6 +301,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     B = args.batch
+    if args.mode == "presence":
+        print(json.dumps(run_presence(args, cfg, bf, uwb, torch)), flush=True)
+        return
     batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
     grid = cfg.grid()
     M, N = cfg.n_antennas, cfg.n_samples

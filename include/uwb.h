@@ -192,6 +192,22 @@ int uwb_localize_batch(int batch, const float* traces, int M, int N,
                        int beamformer, const uwb_rule* rule, void* workspace,
                        size_t ws_bytes, uwb_result* out, float* image, void* stream);
 
+/* Tumour-presence test (Section IV, last paragraph): localise every scan
+ * twice, with the rule's decimation factor and with the manual factor
+ * `decimation2`; a scan whose two runs locate the same focal point has its
+ * tumour confirmed (present[b] = 1), otherwise it is declared tumour-free
+ * (present[b] = 0, also when a run located nothing or failed). out1, out2:
+ * [batch] uwb_result (device) of the two runs; present: [batch] int
+ * (device). The runs reuse one workspace of uwb_presence_workspace(...)
+ * bytes, one after the other on `stream`. */
+size_t uwb_presence_workspace(int batch, int M, int N, const uwb_grid* grid, int beamformer,
+                              const uwb_rule* rule, int decimation2);
+int uwb_presence_batch(int batch, const float* traces, int M, int N, const float* antennas,
+                       long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                       int window, int beamformer, const uwb_rule* rule, int decimation2,
+                       void* workspace, size_t ws_bytes, uwb_result* out1, uwb_result* out2,
+                       int* present, void* stream);
+
 /* End-to-end localisation from HOST memory. traces_host [batch][M][N] and
  * antennas_host ([M][3], or [batch][...] with antenna_stride) live in host
  * memory (pinned memory lets the copies run asynchronously); out_host

@@ -127,6 +127,11 @@ def lib():
         L.orc_hybrid_metric_unclipped.restype = ctypes.c_double
         L.orc_scatter.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, dp, dp]
         L.orc_scatter.restype = None
+        L.orc_presence.argtypes = [fp, ctypes.c_int, ctypes.c_int, fp, ctypes.POINTER(Grid),
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(Rule), ctypes.c_int, ctypes.POINTER(Result),
+                                   ctypes.POINTER(Result)]
+        L.orc_presence.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -203,6 +208,23 @@ def localize(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
     lib().orc_localize(trp, M, N, anp, ctypes.byref(g), float(v), float(fs), int(window),
                        int(beamformer), ctypes.byref(rule), ctypes.byref(res))
     return res.to_dict()
+
+
+def presence(traces, antennas, grid: dict, v, fs, window, beamformer=DAS, rule: Rule | None = None,
+             decimation2: int = 1):
+    """Two-decimation tumour-presence test: (present, result1, result2)."""
+    tr, trp = _f32(traces)
+    an, anp = _f32(antennas)
+    M, N = tr.shape
+    rule = make_rule() if rule is None else rule
+    g = make_grid(grid)
+    r1, r2 = Result(), Result()
+    st = lib().orc_presence(trp, M, N, anp, ctypes.byref(g), float(v), float(fs), int(window),
+                            int(beamformer), ctypes.byref(rule), int(decimation2), ctypes.byref(r1),
+                            ctypes.byref(r2))
+    if st < 0:
+        raise ValueError(f"orc_presence failed: {st}")
+    return bool(st), r1.to_dict(), r2.to_dict()
 
 
 def hybrid_metric(mean_i: float, var_i: float, var_prev: float) -> float:

@@ -480,3 +480,20 @@ int orc_localize(const float* traces, int M, int N, const float* antennas,
   free(img);
   return ORC_OK;
 }
+
+int orc_presence(const float* traces, int M, int N, const float* antennas, const orc_grid* g,
+                 double v, double fs, int window, int beamformer, const orc_rule* r,
+                 int decimation2, orc_result* res1, orc_result* res2) {
+  if (decimation2 < 1) return ORC_ERR_ARG;
+  int st = orc_localize(traces, M, N, antennas, g, v, fs, window, beamformer, r, res1);
+  if (st != ORC_OK) return st;
+  orc_rule r2 = *r;
+  r2.mode = ORC_DECIM_MANUAL;
+  r2.decimation = decimation2;
+  st = orc_localize(traces, M, N, antennas, g, v, fs, window, beamformer, &r2, res2);
+  if (st != ORC_OK) return st;
+  if (res1->loc_idx[0] < 0 || res2->loc_idx[0] < 0) return 0; /* nothing located */
+  for (int a = 0; a < 3; ++a)
+    if (res1->loc_idx[a] != res2->loc_idx[a]) return 0;
+  return 1;
+}

@@ -117,6 +117,15 @@ int orc_localize(const float* traces, int M, int N, const float* antennas,
                  const orc_grid* g, double v, double fs, int window, int beamformer,
                  const orc_rule* r, orc_result* res);
 
+/* Tumour-presence test (Section IV, last paragraph): localise with the rule's
+ * decimation factor and again with the manual factor `decimation2`; a tumour
+ * is confirmed (returns 1) when both runs locate the same focal point, and
+ * the scan is declared tumour-free (returns 0) when they disagree. res1 and
+ * res2 receive the two runs. Negative on error. */
+int orc_presence(const float* traces, int M, int N, const float* antennas, const orc_grid* g,
+                 double v, double fs, int window, int beamformer, const orc_rule* r,
+                 int decimation2, orc_result* res1, orc_result* res2);
+
 /* Eq. 5 hybrid metric for one candidate, weight clipped to [0, 1], and the
  * printed formula without the clip (exposed for the tests). */
 double orc_hybrid_metric(double mean_i, double var_i, double var_prev);

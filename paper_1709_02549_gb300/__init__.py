@@ -19,7 +19,8 @@ __all__ = [
     "uwb_dmas_image", "uwb_image_batch", "uwb_localize_workspace", "uwb_localize",
     "uwb_localize_batch", "uwb_device_status", "uwb_last_error", "results_from_device",
     "uwb_phase_timing", "uwb_phase_times", "uwb_localize_batch_noalloc",
-    "uwb_localize_host_workspace", "uwb_localize_host",
+    "uwb_localize_host_workspace", "uwb_localize_host", "uwb_presence_workspace",
+    "uwb_presence_batch",
     "UwbError",
 ]
 
@@ -102,6 +103,9 @@ def lib() -> ctypes.CDLL:
             "uwb_localize_host_workspace": (sz, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp]),
             "uwb_localize_host": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, sz, vp,
                                       ctypes.POINTER(ctypes.c_longlong), vp]),
+            "uwb_presence_workspace": (sz, [i, i, i, gp, i, rp, i]),
+            "uwb_presence_batch": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, i, vp, sz, vp, vp,
+                                       vp, vp]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -276,6 +280,29 @@ def uwb_localize_host(traces_host, antennas_host, grid, v, fs, window, beamforme
                                    ctypes.c_void_p(out_host.data_ptr()), ctypes.byref(moved),
                                    _stream(stream)), "uwb_localize_host")
     return int(moved.value)
+
+
+def uwb_presence_workspace(batch, M, N, grid, beamformer, rule: UwbRule, decimation2) -> int:
+    n = lib().uwb_presence_workspace(int(batch), int(M), int(N), ctypes.byref(make_grid(grid)),
+                                     int(beamformer), ctypes.byref(rule), int(decimation2))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_presence_workspace")
+    return n
+
+
+def uwb_presence_batch(traces, antennas, grid, v, fs, window, beamformer, rule: UwbRule,
+                       decimation2, workspace, out1, out2, present, stream=None):
+    """Two-decimation tumour-presence test; present: int32 CUDA tensor [B]."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_presence_batch(B, _f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                                    stride, ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                    int(window), int(beamformer), ctypes.byref(rule),
+                                    int(decimation2), _ptr(workspace, "workspace"),
+                                    workspace.numel() * workspace.element_size(),
+                                    _ptr(out1, "out1"), _ptr(out2, "out2"),
+                                    _ptr(present, "present"), _stream(stream)),
+           "uwb_presence_batch")
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -367,6 +367,17 @@ __global__ void k_finish(const FinishParams P, const int* status) {
   }
 }
 
+// Tumour-presence verdict per scan: both runs located the same focal point.
+__global__ void k_presence(const uwb_result* a, const uwb_result* b, int* present, int B) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const uwb_result& x = a[s];
+  const uwb_result& y = b[s];
+  int same = x.status == UWB_OK && y.status == UWB_OK && x.loc_idx[0] >= 0 && y.loc_idx[0] >= 0;
+  for (int k = 0; k < 3; ++k) same = same && x.loc_idx[k] == y.loc_idx[k];
+  present[s] = same;
+}
+
 // argmax keys -> linear index (or -1), in place.
 __global__ void k_keys_to_index(unsigned long long* keys, int B) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,6 +403,12 @@ cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st
 
 cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t st) {
   k_finish<<<(p.B + 127) / 128, 128, 0, st>>>(p, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_presence(const uwb_result* a, const uwb_result* b, int* present, int B,
+                            cudaStream_t st) {
+  k_presence<<<(B + 127) / 128, 128, 0, st>>>(a, b, present, B);
   return cudaGetLastError();
 }
 

@@ -745,6 +745,39 @@ size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid, int
   return ws_layout(batch, decimate(geo.g, *rule).Pd).total;
 }
 
+size_t uwb_presence_workspace(int batch, int M, int N, const uwb_grid* grid, int beamformer,
+                              const uwb_rule* rule, int decimation2) {
+  if (decimation2 < 1 || !rule) return 0;
+  uwb_rule r2 = *rule;
+  r2.mode = UWB_DECIM_MANUAL;
+  r2.decimation = decimation2;
+  const size_t a = uwb_localize_workspace(batch, M, N, grid, beamformer, rule);
+  const size_t b = uwb_localize_workspace(batch, M, N, grid, beamformer, &r2);
+  if (!a || !b) return 0;
+  return a > b ? a : b;
+}
+
+int uwb_presence_batch(int batch, const float* traces, int M, int N, const float* antennas,
+                       long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                       int window, int beamformer, const uwb_rule* rule, int decimation2,
+                       void* workspace, size_t ws_bytes, uwb_result* out1, uwb_result* out2,
+                       int* present, void* stream) {
+  if (decimation2 < 1) return fail(UWB_ERR_ARG, "second decimation factor %d < 1", decimation2);
+  if (!out2 || !present) return fail(UWB_ERR_ARG, "null second result array or verdicts");
+  int st = localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                         beamformer, rule, workspace, ws_bytes, out1, nullptr, stream);
+  if (st) return st;
+  uwb_rule r2 = *rule;
+  r2.mode = UWB_DECIM_MANUAL;
+  r2.decimation = decimation2;
+  st = localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                     beamformer, &r2, workspace, ws_bytes, out2, nullptr, stream);
+  if (st) return st;
+  cudaError_t e = launch_presence(out1, out2, present, batch, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "presence launch");
+  return UWB_OK;
+}
+
 size_t uwb_localize_host_workspace(int batch, const float* traces_host, int M, int N,
                                    const float* antennas_host, long long antenna_stride,
                                    const uwb_grid* grid, double v, double fs, int window,

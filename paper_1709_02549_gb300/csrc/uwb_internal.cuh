@@ -109,5 +109,7 @@ cudaError_t launch_select(const SelParams& p, cudaStream_t st);
 cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t st);
 cudaError_t launch_keys_to_index(unsigned long long* keys, int B, cudaStream_t st);
+cudaError_t launch_presence(const uwb_result* a, const uwb_result* b, int* present, int B,
+                            cudaStream_t st);
 
 }  // namespace uwb

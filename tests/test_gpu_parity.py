@@ -303,3 +303,40 @@ def test_host_entry_point_matches_device_entry_point(gpu, name, bf, N, per_scan)
                     "points_evaluated"):
             assert g[key] == w[key], key
         assert g["peak"] == w["peak"]
+
+
+# ------------------------------------------------------------------ tumour-presence test
+
+@pytest.mark.parametrize("name,bf,D2", [("das2d_64", 0, 3), ("dmas2d_512", 2, 20)])
+def test_presence_matches_oracle(gpu, name, bf, D2):
+    base = phantom.CONFIGS[name]
+    scans, truth = [], []
+    for tumor in (True, False):
+        cfg = base if tumor else phantom.with_changes(base, n_tumors=(0, 0))
+        for s in range(3):
+            scans.append(phantom.make_scan(cfg, phantom.BASE_SEED + 700 + s))
+    traces = np.stack([sc["traces"] for sc in scans])
+    ants = scans[0]["antennas"]
+    grid = base.grid()
+    g_rule, o_rule = rule_pair(gpu)
+    B = len(scans)
+    ws = torch.empty(gpu.uwb_presence_workspace(B, base.n_antennas, base.n_samples, grid, bf,
+                                                g_rule, D2), dtype=torch.uint8, device="cuda")
+    o1 = torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    o2 = torch.empty_like(o1)
+    present = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+    gpu.uwb_presence_batch(dev(traces), dev(ants), grid, base.v, base.fs, base.window, bf, g_rule,
+                           D2, ws, o1, o2, present)
+    torch.cuda.synchronize()
+    r1 = [record_to_dict(r) for r in gpu.results_from_device(o1)]
+    r2 = [record_to_dict(r) for r in gpu.results_from_device(o2)]
+    got = present.cpu().numpy()
+    for s, sc in enumerate(scans):
+        want, w1, w2 = oracle.presence(sc["traces"], ants, grid, base.v, base.fs, base.window,
+                                       BF_ORACLE[bf], o_rule, D2)
+        e = _energy_at(sc["traces"], ants, grid, base.v, base.fs, base.window, bf)
+        t1 = compare_localize(r1[s], w1, e)
+        t2 = compare_localize(r2[s], w2, e)
+        if not (t1["tie"] or t2["tie"]):
+            assert bool(got[s]) == want, s
+        assert r2[s]["decim"] == D2

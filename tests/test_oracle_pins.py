@@ -375,3 +375,36 @@ def test_three_d_localisation_runs_on_a_small_cube():
                         oracle.make_rule(min_segment=2))
     assert r["loc_idx"] == [k % 24, (k // 24) % 24, k // 576]
     assert all(0 <= c < 8 for c in r["child"])
+
+
+# ------------------------------------------------------------- tumour-presence test (Section IV)
+
+def test_presence_with_the_same_factor_twice_confirms_any_located_target():
+    cfg = phantom.CONFIGS["das2d_64"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 7)
+    rule = oracle.make_rule()
+    D = oracle.decimation(rule, cfg.grid())
+    present, r1, r2 = oracle.presence(sc["traces"], sc["antennas"], cfg.grid(), cfg.v, cfg.fs,
+                                      cfg.window, oracle.DAS, rule, D)
+    assert present and r1["loc_idx"] == r2["loc_idx"] and r2["decim"] == D
+
+
+def test_presence_is_declined_without_any_echo():
+    cfg = phantom.CONFIGS["das2d_64"]
+    tr = np.zeros((cfg.n_antennas, cfg.n_samples), np.float32)
+    present, r1, _ = oracle.presence(tr, phantom.antenna_positions(cfg), cfg.grid(), cfg.v,
+                                     cfg.fs, cfg.window, oracle.DAS, oracle.make_rule(), 3)
+    assert not present and r1["stop_reason"] == oracle.STOP_NO_TARGET
+
+
+def test_presence_reports_disagreeing_runs():
+    # two point scatterers of equal strength far apart: decimation factors that
+    # sample them differently may send the search to different ones; whenever
+    # the two runs' locations differ the verdict must be "absent"
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], snr_db=None)
+    g = cfg.grid()
+    for D2 in (2, 3, 5):
+        tr = phantom.point_scatterer_traces(cfg, [[-0.02, -0.01, 0], [0.021, 0.012, 0]], [1, 1])
+        present, r1, r2 = oracle.presence(tr, phantom.antenna_positions(cfg), g, cfg.v, cfg.fs,
+                                          cfg.window, oracle.DAS, oracle.make_rule(), D2)
+        assert present == (r1["loc_idx"] == r2["loc_idx"])
