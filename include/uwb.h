@@ -164,6 +164,32 @@ int uwb_image_batch(int batch, int beamformer, const float* traces, int M, int N
                     const uwb_grid* grid, double v, double fs, int window,
                     float* image, long long* peak_index, void* stream);
 
+/* Multistatic images (Section II.A: Eq. 2 delays; Eq. 4 DAS, DMAS over pairs
+ * of channels): channel c is the echo sent by antenna channels[2c] and
+ * received by antenna channels[2c+1] (int32 [C][2], device), its trace is
+ * traces[b][c][0..N) and its delay in samples (|r - a_tx| + |r - a_rx|) fs / v.
+ * Eq. 4 sums over every (i, j) pair; any subset may be given. antennas:
+ * [M][3]. beamformer: UWB_DAS or UWB_DMAS (the literal pair form is built for
+ * monostatic data only: UWB_ERR_UNSUPPORTED). A channel index outside
+ * [0, M) is recorded as UWB_ERR_ARG in the device status word and clamped.
+ * Otherwise as uwb_image_batch. */
+int uwb_image_multistatic_batch(int batch, int beamformer, const float* traces, int C, int N,
+                                const int* channels, const float* antennas, int M,
+                                long long antenna_stride, const uwb_grid* grid, double v,
+                                double fs, int window, float* image, long long* peak_index,
+                                void* stream);
+
+/* The segment-search framework (Section III) on multistatic scans; arguments
+ * as uwb_image_multistatic_batch and uwb_localize_batch. */
+size_t uwb_localize_multistatic_workspace(int batch, int C, int N, const uwb_grid* grid,
+                                          int beamformer, const uwb_rule* rule);
+int uwb_localize_multistatic_batch(int batch, const float* traces, int C, int N,
+                                   const int* channels, const float* antennas, int M,
+                                   long long antenna_stride, const uwb_grid* grid, double v,
+                                   double fs, int window, int beamformer, const uwb_rule* rule,
+                                   void* workspace, size_t ws_bytes, uwb_result* out,
+                                   float* image, void* stream);
+
 /* Bytes of device workspace uwb_localize_batch needs for these sizes
  * (0 on invalid arguments). The workspace must be 256-byte aligned. */
 size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid,

@@ -109,6 +109,11 @@ def lib():
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                 ip, ip, ip, dp]
         L.orc_image.restype = ctypes.c_int
+        L.orc_image_multistatic.argtypes = [fp, ctypes.c_int, ctypes.c_int, ip, fp, ctypes.c_int,
+                                            ctypes.POINTER(Grid), ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ip,
+                                            ip, dp]
+        L.orc_image_multistatic.restype = ctypes.c_int
         L.orc_decimation.argtypes = [ctypes.POINTER(Rule), ctypes.POINTER(Grid)]
         L.orc_decimation.restype = ctypes.c_int
         L.orc_lattice_offset.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -127,6 +132,12 @@ def lib():
         L.orc_hybrid_metric_unclipped.restype = ctypes.c_double
         L.orc_scatter.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, dp, dp]
         L.orc_scatter.restype = None
+        L.orc_localize_multistatic.argtypes = [fp, ctypes.c_int, ctypes.c_int, ip, fp,
+                                               ctypes.c_int, ctypes.POINTER(Grid),
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, ctypes.POINTER(Rule),
+                                               ctypes.POINTER(Result)]
+        L.orc_localize_multistatic.restype = ctypes.c_int
         L.orc_presence.argtypes = [fp, ctypes.c_int, ctypes.c_int, fp, ctypes.POINTER(Grid),
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(Rule), ctypes.c_int, ctypes.POINTER(Result),
@@ -174,6 +185,29 @@ def image(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if st != 0:
         raise ValueError(f"orc_image failed: {st}")
+    return out.reshape(cnt[2], cnt[1], cnt[0])
+
+
+def image_multistatic(traces, channels, antennas, grid: dict, v, fs, window, beamformer=DAS,
+                      lo=None, step=None, cnt=None) -> np.ndarray:
+    """Multistatic energy image; traces [C, N], channels [C, 2] (tx, rx)."""
+    tr, trp = _f32(traces)
+    an, anp = _f32(antennas)
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    C, N = tr.shape
+    M = an.shape[0]
+    n = list(grid["n"]) + [1] * (3 - len(grid["n"]))
+    lo = [0, 0, 0] if lo is None else list(lo)
+    step = [1, 1, 1] if step is None else list(step)
+    cnt = n if cnt is None else list(cnt)
+    out = np.zeros(int(np.prod(cnt)), dtype=np.float64)
+    g = make_grid(grid)
+    st = lib().orc_image_multistatic(trp, C, N, ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     anp, M, ctypes.byref(g), float(v), float(fs), int(window),
+                                     int(beamformer), I3(*lo), I3(*step), I3(*cnt),
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != 0:
+        raise ValueError(f"orc_image_multistatic failed: {st}")
     return out.reshape(cnt[2], cnt[1], cnt[0])
 
 
@@ -225,6 +259,21 @@ def presence(traces, antennas, grid: dict, v, fs, window, beamformer=DAS, rule: 
     if st < 0:
         raise ValueError(f"orc_presence failed: {st}")
     return bool(st), r1.to_dict(), r2.to_dict()
+
+
+def localize_multistatic(traces, channels, antennas, grid: dict, v, fs, window, beamformer=DAS,
+                         rule: Rule | None = None) -> dict:
+    tr, trp = _f32(traces)
+    an, anp = _f32(antennas)
+    ch = np.ascontiguousarray(channels, dtype=np.int32)
+    C, N = tr.shape
+    rule = make_rule() if rule is None else rule
+    g = make_grid(grid)
+    res = Result()
+    lib().orc_localize_multistatic(trp, C, N, ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), anp,
+                                   an.shape[0], ctypes.byref(g), float(v), float(fs), int(window),
+                                   int(beamformer), ctypes.byref(rule), ctypes.byref(res))
+    return res.to_dict()
 
 
 def hybrid_metric(mean_i: float, var_i: float, var_prev: float) -> float:

@@ -132,6 +132,80 @@ int orc_image(const float* traces, int M, int N, const float* antennas,
   return bad ? ORC_ERR_ARG : ORC_OK;
 }
 
+/* Multistatic energy of one focal point (Eq. 2 + Eq. 4, or Eq. 2 + DMAS over
+ * channel pairs). u and x are caller scratch of C doubles each. */
+static double focal_energy_ms(const float* traces, int C, int N, const int* chan,
+                              const float* ant, const double r[3], double v, double fs, int W,
+                              int bf, double* u, double* x) {
+  const int h = W / 2;
+  for (int c = 0; c < C; ++c) {
+    double path = 0.0;
+    for (int e = 0; e < 2; ++e) {
+      const int i = chan[2 * c + e];
+      double dx = r[0] - (double)ant[3 * i + 0];
+      double dy = r[1] - (double)ant[3 * i + 1];
+      double dz = r[2] - (double)ant[3 * i + 2];
+      path += sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    u[c] = path / v * fs; /* transmitter -> focal point -> receiver, in samples */
+  }
+  double energy = 0.0;
+  for (int k = 0; k < W; ++k) {
+    for (int c = 0; c < C; ++c) {
+      double t = u[c] - (double)h + (double)k;
+      double n0 = floor(t);
+      double f = t - n0;
+      const float* row = traces + (size_t)c * (size_t)N;
+      x[c] = (1.0 - f) * trace_sample(row, N, (long)n0) +
+             f * trace_sample(row, N, (long)n0 + 1);
+    }
+    double s = 0.0;
+    if (bf == ORC_DAS) {
+      for (int c = 0; c < C; ++c) s += x[c];
+    } else {
+      for (int c = 0; c < C; ++c)
+        for (int d = c + 1; d < C; ++d) s += x[c] * x[d];
+    }
+    energy += s * s;
+  }
+  return energy;
+}
+
+int orc_image_multistatic(const float* traces, int C, int N, const int* chan,
+                          const float* antennas, int M, const orc_grid* g, double v, double fs,
+                          int window, int beamformer, const int lo[3], const int step[3],
+                          const int cnt[3], double* out) {
+  if (!traces || !chan || !antennas || !g || !out || C < 1 || N < 1 || M < 1 || window < 1 ||
+      !(v > 0) || !(fs > 0) || (beamformer != ORC_DAS && beamformer != ORC_DMAS))
+    return ORC_ERR_ARG;
+  for (int c = 0; c < 2 * C; ++c)
+    if (chan[c] < 0 || chan[c] >= M) return ORC_ERR_ARG;
+  const long long total = (long long)cnt[0] * cnt[1] * cnt[2];
+  int bad = 0;
+#pragma omp parallel
+  {
+    double* u = (double*)malloc(sizeof(double) * (size_t)C);
+    double* x = (double*)malloc(sizeof(double) * (size_t)C);
+    if (!u || !x) {
+#pragma omp atomic write
+      bad = 1;
+    } else {
+#pragma omp for schedule(dynamic, 16)
+      for (long long p = 0; p < total; ++p) {
+        long long kk[3] = {p % cnt[0], (p / cnt[0]) % cnt[1], p / ((long long)cnt[0] * cnt[1])};
+        double r[3];
+        for (int a = 0; a < 3; ++a)
+          r[a] = g->origin[a] + (double)(lo[a] + step[a] * kk[a]) * g->pitch[a];
+        out[p] = focal_energy_ms(traces, C, N, chan, antennas, r, v, fs, window, beamformer, u,
+                                 x);
+      }
+    }
+    free(u);
+    free(x);
+  }
+  return bad ? ORC_ERR_ARG : ORC_OK;
+}
+
 /* Section III: manual mode takes D as given; automatic mode spaces samples
  * by the side of the square inscribed in the smallest tumour to be detected
  * (d / sqrt 2), in units of the final resolution (Section IV: 1 cm and 1 mm
@@ -393,9 +467,47 @@ int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
   return ORC_OK;
 }
 
+/* The data a localisation images: monostatic (chan == NULL, rows = antennas)
+ * or multistatic (rows = channels). */
+typedef struct {
+  const float* traces;
+  int rows, N;
+  const int* chan;
+  const float* antennas;
+  int M;
+  double v, fs;
+  int window, beamformer;
+} scan_data;
+
+static int scan_image(const scan_data* d, const orc_grid* g, const int lo[3], const int step[3],
+                      const int cnt[3], double* out) {
+  if (d->chan)
+    return orc_image_multistatic(d->traces, d->rows, d->N, d->chan, d->antennas, d->M, g, d->v,
+                                 d->fs, d->window, d->beamformer, lo, step, cnt, out);
+  return orc_image(d->traces, d->rows, d->N, d->antennas, g, d->v, d->fs, d->window,
+                   d->beamformer, lo, step, cnt, out);
+}
+
+static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* r,
+                         orc_result* res);
+
 int orc_localize(const float* traces, int M, int N, const float* antennas,
                  const orc_grid* g, double v, double fs, int window, int beamformer,
                  const orc_rule* r, orc_result* res) {
+  scan_data d = {traces, M, N, NULL, antennas, M, v, fs, window, beamformer};
+  return localize_data(&d, g, r, res);
+}
+
+int orc_localize_multistatic(const float* traces, int C, int N, const int* chan,
+                             const float* antennas, int M, const orc_grid* g, double v,
+                             double fs, int window, int beamformer, const orc_rule* r,
+                             orc_result* res) {
+  scan_data d = {traces, C, N, chan, antennas, M, v, fs, window, beamformer};
+  return localize_data(&d, g, r, res);
+}
+
+static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* r,
+                         orc_result* res) {
   memset(res, 0, sizeof *res);
   for (int a = 0; a < 3; ++a) res->loc_idx[a] = -1;
   if (!g || !r || g->dim < 2 || g->dim > 3 || (g->dim == 2 && g->n[2] != 1) ||
@@ -417,8 +529,7 @@ int orc_localize(const float* traces, int M, int N, const float* antennas,
     res->status = ORC_ERR_ARG;
     return ORC_ERR_ARG;
   }
-  int st = orc_image(traces, M, N, antennas, g, v, fs, window, beamformer, L.off,
-                     L.step, L.cnt, prof);
+  int st = scan_image(d, g, L.off, L.step, L.cnt, prof);
   if (st != ORC_OK) {
     free(prof);
     res->status = st;
@@ -457,8 +568,7 @@ int orc_localize(const float* traces, int M, int N, const float* antennas,
     res->status = ORC_ERR_ARG;
     return ORC_ERR_ARG;
   }
-  st = orc_image(traces, M, N, antennas, g, v, fs, window, beamformer, res->roi_lo,
-                 step1, cnt, img);
+  st = scan_image(d, g, res->roi_lo, step1, cnt, img);
   if (st != ORC_OK) {
     free(img);
     res->status = st;

@@ -98,6 +98,16 @@ int orc_image(const float* traces, int M, int N, const float* antennas,
               const orc_grid* g, double v, double fs, int window, int beamformer,
               const int lo[3], const int step[3], const int cnt[3], double* out);
 
+/* Multistatic image (Section II.A, Eq. 2 delays, Eq. 4 for DAS; DMAS over
+ * pairs of channels): channel c is the echo sent by antenna chan[2c] and
+ * received by antenna chan[2c+1], stored in traces[c][N]; its delay in
+ * samples is (|r - a_tx| + |r - a_rx|) fs / v. Same lattice and output as
+ * orc_image. */
+int orc_image_multistatic(const float* traces, int C, int N, const int* chan,
+                          const float* antennas, int M, const orc_grid* g, double v, double fs,
+                          int window, int beamformer, const int lo[3], const int step[3],
+                          const int cnt[3], double* out);
+
 /* Spatial decimation factor, Section III (manual / automatic modes) and the
  * worked example of Section IV. */
 int orc_decimation(const orc_rule* r, const orc_grid* g);
@@ -125,6 +135,12 @@ int orc_localize(const float* traces, int M, int N, const float* antennas,
 int orc_presence(const float* traces, int M, int N, const float* antennas, const orc_grid* g,
                  double v, double fs, int window, int beamformer, const orc_rule* r,
                  int decimation2, orc_result* res1, orc_result* res2);
+
+/* The framework on a multistatic scan (channels as in orc_image_multistatic). */
+int orc_localize_multistatic(const float* traces, int C, int N, const int* chan,
+                             const float* antennas, int M, const orc_grid* g, double v,
+                             double fs, int window, int beamformer, const orc_rule* r,
+                             orc_result* res);
 
 /* Eq. 5 hybrid metric for one candidate, weight clipped to [0, 1], and the
  * printed formula without the clip (exposed for the tests). */

@@ -20,7 +20,8 @@ __all__ = [
     "uwb_localize_batch", "uwb_device_status", "uwb_last_error", "results_from_device",
     "uwb_phase_timing", "uwb_phase_times", "uwb_localize_batch_noalloc",
     "uwb_localize_host_workspace", "uwb_localize_host", "uwb_presence_workspace",
-    "uwb_presence_batch",
+    "uwb_presence_batch", "uwb_image_multistatic_batch", "uwb_localize_multistatic_workspace",
+    "uwb_localize_multistatic_batch",
     "UwbError",
 ]
 
@@ -106,6 +107,11 @@ def lib() -> ctypes.CDLL:
             "uwb_presence_workspace": (sz, [i, i, i, gp, i, rp, i]),
             "uwb_presence_batch": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, i, vp, sz, vp, vp,
                                        vp, vp]),
+            "uwb_image_multistatic_batch": (i, [i, i, vp, i, i, vp, vp, i, ll, gp, d, d, i, vp, vp,
+                                                vp]),
+            "uwb_localize_multistatic_workspace": (sz, [i, i, i, gp, i, rp]),
+            "uwb_localize_multistatic_batch": (i, [i, vp, i, i, vp, vp, i, ll, gp, d, d, i, i, rp,
+                                                   vp, sz, vp, vp, vp]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -303,6 +309,54 @@ def uwb_presence_batch(traces, antennas, grid, v, fs, window, beamformer, rule: 
                                     _ptr(out1, "out1"), _ptr(out2, "out2"),
                                     _ptr(present, "present"), _stream(stream)),
            "uwb_presence_batch")
+
+
+def _i32(t, name):
+    import torch
+    if t.dtype != torch.int32:
+        raise ValueError(f"{name} must be int32")
+    return _ptr(t, name)
+
+
+def uwb_image_multistatic_batch(beamformer, traces, channels, antennas, grid, v, fs, window,
+                                image, peak_index=None, stream=None):
+    """traces [B, C, N]; channels int32 [C, 2] (transmitter, receiver); antennas [M, 3]
+    or [B, M, 3]; image [B, P]."""
+    B, C, N = traces.shape
+    M = antennas.shape[-2]
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_image_multistatic_batch(B, int(beamformer), _f32(traces, "traces"), C, N,
+                                             _i32(channels, "channels"),
+                                             _f32(antennas, "antennas"), M, stride,
+                                             ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                             int(window), _f32(image, "image"),
+                                             _ptr(peak_index, "peak_index", True),
+                                             _stream(stream)), "uwb_image_multistatic_batch")
+
+
+def uwb_localize_multistatic_workspace(batch, C, N, grid, beamformer, rule: UwbRule) -> int:
+    n = lib().uwb_localize_multistatic_workspace(int(batch), int(C), int(N),
+                                                 ctypes.byref(make_grid(grid)), int(beamformer),
+                                                 ctypes.byref(rule))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_localize_multistatic_workspace")
+    return n
+
+
+def uwb_localize_multistatic_batch(traces, channels, antennas, grid, v, fs, window, beamformer,
+                                   rule: UwbRule, workspace, out, image=None, stream=None):
+    B, C, N = traces.shape
+    M = antennas.shape[-2]
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_localize_multistatic_batch(B, _f32(traces, "traces"), C, N,
+                                                _i32(channels, "channels"),
+                                                _f32(antennas, "antennas"), M, stride,
+                                                ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                                int(window), int(beamformer), ctypes.byref(rule),
+                                                _ptr(workspace, "workspace"),
+                                                workspace.numel() * workspace.element_size(),
+                                                _ptr(out, "out"), _f32(image, "image", True),
+                                                _stream(stream)), "uwb_localize_multistatic_batch")
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20

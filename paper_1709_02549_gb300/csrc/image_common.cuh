@@ -40,13 +40,27 @@ struct KernelShape {
 };
 
 // -------------------------------------------------------------- DAS / DMAS-identity
-template <int BF, int WT, bool STAGED>
+// Rows are the M antennas (monostatic: delay 2|r - a_i| fs / v) or, with MS,
+// the R channels (transmitter, receiver) of a multistatic recording (Eq. 2:
+// delay (|r - a_tx| + |r - a_rx|) fs / v); for MS each thread first puts its
+// focal point's distance to every antenna in sD[antenna][thread].
+template <int BF, int WT, bool STAGED, bool MS>
 __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __restrict__ sTr,
                                             const float4* __restrict__ sAnt,
+                                            const int2* __restrict__ sCh, float* __restrict__ sD,
                                             const float* __restrict__ gTr, int nlo, int cl_lo,
                                             int cl_hi, float px, float py, float pz) {
   float energy = 0.f;
-  const int M = P.M;
+  const int R = P.R;
+  const int T = blockDim.x, tid = threadIdx.x;
+  if (MS) {
+    for (int i = 0; i < P.M; ++i) {
+      const float4 a = sAnt[i];
+      const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
+      sD[i * T + tid] = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    }
+  }
+  const float half_k = 0.5f * P.kscale;
   for (int k0 = 0; k0 < P.W; k0 += WT) {
     float s1[WT], s2[WT];
 #pragma unroll
@@ -55,13 +69,19 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
       s2[k] = 0.f;
     }
     const float hoff = static_cast<float>(P.h - k0);
-    for (int i = 0; i < M; ++i) {
-      const float4 a = sAnt[i];
-      const float dx = px - a.x;
-      const float dy = py - a.y;
-      const float dz = pz - a.z;
-      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-      const float t = fmaf(d, P.kscale, -hoff);  // u_i - h + k0
+    for (int i = 0; i < R; ++i) {
+      float t;  // u_i - h + k0
+      if (MS) {
+        const int2 c = sCh[i];
+        t = fmaf(sD[c.x * T + tid] + sD[c.y * T + tid], half_k, -hoff);
+      } else {
+        const float4 a = sAnt[i];
+        const float dx = px - a.x;
+        const float dy = py - a.y;
+        const float dz = pz - a.z;
+        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        t = fmaf(d, P.kscale, -hoff);
+      }
       const float fl = floorf(t);
       const float f = t - fl;
       int n0 = static_cast<int>(fl);
@@ -217,22 +237,28 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
 
 // ------------------------------------------------------------------ the kernel
 // V = window chunk WT (DAS, DMAS identity) or antenna register block MMAX
-// (literal DMAS). Dynamic shared memory: [M][span] traces | [M*3] antennas |
-// (literal) [M][T] delays | mbarrier and reduction slots.
-template <int BF, int V>
+// (literal DMAS); MS = multistatic rows. Dynamic shared memory (see
+// image_smem_bytes): [rows][span] traces | [M] antennas (float4) | (MS) [R]
+// channels | (literal) [V][T] delays | (MS) [M][T] distances | mbarrier and
+// reduction slots.
+template <int BF, int V, bool MS>
 __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V>::min_blocks)
     k_image(const __grid_constant__ CUtensorMap tmap, const ImgParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
   const int M = P.M;
+  const int R = P.R;  // trace rows per scan: M antennas, or R channels
   // literal DMAS keeps V (>= M) trace rows; rows M..V-1 stay zero
-  const int rows = (BF == BF_DMAS_LIT) ? V : M;
+  const int rows = (BF == BF_DMAS_LIT) ? V : R;
   float* sTr = reinterpret_cast<float*>(smem_raw);
   // antennas as (x, y, z, 0): one broadcast 16-byte load per antenna
   float4* sAnt = reinterpret_cast<float4*>(sTr + static_cast<size_t>(rows) * P.span);
-  float2* sNF = reinterpret_cast<float2*>(sAnt + M);
+  int2* sCh = reinterpret_cast<int2*>(sAnt + M);
+  float2* sNF = reinterpret_cast<float2*>(sCh + (MS ? R : 0));
   const size_t nf_words = (BF == BF_DMAS_LIT) ? static_cast<size_t>(V) * T * 2 : 0;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(sNF) + nf_words);
+  float* sD = reinterpret_cast<float*>(sNF) + nf_words;
+  const size_t d_words = MS ? static_cast<size_t>(M) * T : 0;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sD + d_words);
   unsigned long long* sKey = reinterpret_cast<unsigned long long*>(bar + 1);  // [32]
   int* sInt = reinterpret_cast<int*>(sKey + 32);                              // [4]
 
@@ -247,6 +273,17 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   if (tid == 0) mbar_init(bar, 1);
   if (BF == BF_DMAS_LIT)
     for (int j = tid; j < (rows - M) * P.span; j += T) sTr[M * P.span + j] = 0.f;
+  if (MS) {
+    // channel table (shared by every scan); indices outside the array are
+    // recorded as an argument error and clamped so that no access leaves it
+    for (int r = tid; r < R; r += T) {
+      int2 c = P.chan[r];
+      if (c.x < 0 || c.x >= M || c.y < 0 || c.y >= M) atomicExch(P.status, UWB_ERR_ARG);
+      c.x = min(max(c.x, 0), M - 1);
+      c.y = min(max(c.y, 0), M - 1);
+      sCh[r] = c;
+    }
+  }
   __syncthreads();
   uint32_t phase = 0;
 
@@ -302,6 +339,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
         bmin[a] = fminf(p0, p1);
         bmax[a] = fmaxf(p0, p1);
       }
+      // nearest and farthest distance from each antenna to the lattice's box
       for (int i = tid; i < M; i += T) {
         float dn2 = 0.f, df2 = 0.f;
 #pragma unroll
@@ -312,10 +350,27 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
           dn2 = fmaf(dn, dn, dn2);
           df2 = fmaf(df, df, df2);
         }
-        const float umin = fminf(fmaxf(sqrtf(dn2) * P.kscale - P.h, -1e8f), 1e8f);
-        const float umax = fminf(fmaxf(sqrtf(df2) * P.kscale - P.h, -1e8f), 1e8f);
-        atomicMin(&sInt[0], static_cast<int>(floorf(umin)) - 2);
-        atomicMax(&sInt[1], static_cast<int>(floorf(umax)) + P.wpad + 3);
+        if (MS) {
+          sD[i] = sqrtf(dn2);  // scratch until the tile computation starts
+          sD[M + i] = sqrtf(df2);
+        } else {
+          const float umin = fminf(fmaxf(sqrtf(dn2) * P.kscale - P.h, -1e8f), 1e8f);
+          const float umax = fminf(fmaxf(sqrtf(df2) * P.kscale - P.h, -1e8f), 1e8f);
+          atomicMin(&sInt[0], static_cast<int>(floorf(umin)) - 2);
+          atomicMax(&sInt[1], static_cast<int>(floorf(umax)) + P.wpad + 3);
+        }
+      }
+      if (MS) {
+        __syncthreads();
+        const float half_k = 0.5f * P.kscale;
+        for (int r = tid; r < R; r += T) {
+          const int2 c = sCh[r];
+          const float umin = fminf(fmaxf((sD[c.x] + sD[c.y]) * half_k - P.h, -1e8f), 1e8f);
+          const float umax =
+              fminf(fmaxf((sD[M + c.x] + sD[M + c.y]) * half_k - P.h, -1e8f), 1e8f);
+          atomicMin(&sInt[0], static_cast<int>(floorf(umin)) - 2);
+          atomicMax(&sInt[1], static_cast<int>(floorf(umax)) + P.wpad + 3);
+        }
       }
       __syncthreads();
       nlo = sInt[0] & ~3;  // TMA needs a 16-byte aligned sample coordinate
@@ -328,7 +383,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
         if (tma_ok) {
           if (tid == 0) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(M) * P.span * 4u);
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(R) * P.span * 4u);
             tma_load_3d(sTr, &tmap, nlo - P.n_begin, 0, scan, bar);
           }
           uint32_t ok = 0;
@@ -344,7 +399,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
           }
           phase ^= 1u;
         } else {
-          const int total_s = M * P.span;
+          const int total_s = R * P.span;
           for (int j = tid; j < total_s; j += T) {
             const int i = j / P.span;
             const int n = nlo + (j - i * P.span) - P.n_begin;
@@ -380,10 +435,10 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
                       : energy_literal<V, false>(P, sTr, sAnt, sNF, gTr, nlo, cl_lo, cl_hi,
                                                  px, py, pz);
       } else {
-        energy = fits ? energy_sum<BF, V, true>(P, sTr, sAnt, gTr, nlo, cl_lo, cl_hi, px, py,
-                                                pz)
-                      : energy_sum<BF, V, false>(P, sTr, sAnt, gTr, nlo, cl_lo, cl_hi, px, py,
-                                                 pz);
+        energy = fits ? energy_sum<BF, V, true, MS>(P, sTr, sAnt, sCh, sD, gTr, nlo, cl_lo,
+                                                    cl_hi, px, py, pz)
+                      : energy_sum<BF, V, false, MS>(P, sTr, sAnt, sCh, sD, gTr, nlo, cl_lo,
+                                                     cl_hi, px, py, pz);
       }
       if (P.image) P.image[static_cast<long long>(scan) * P.gP + lin] = energy;
       if (P.compact)
@@ -414,21 +469,21 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   }
 }
 
-template <int BF, int V>
+template <int BF, int V, bool MS>
 cudaError_t launch_variant(const ImgParams& p, const CUtensorMap* tmap, int ctas, int threads,
                            size_t smem, cudaStream_t st) {
-  k_image<BF, V><<<ctas, threads, smem, st>>>(*tmap, p);
+  k_image<BF, V, MS><<<ctas, threads, smem, st>>>(*tmap, p);
   return cudaGetLastError();
 }
 
-template <int BF, int V>
+template <int BF, int V, bool MS>
 int occupancy_variant(int threads, size_t smem) {
-  if (cudaFuncSetAttribute(k_image<BF, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_image<BF, V, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(smem)) != cudaSuccess)
     return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_image<BF, V>, threads, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_image<BF, V, MS>, threads,
+                                                    smem) != cudaSuccess)
     return 0;
   return blocks;
 }

@@ -1,39 +1,49 @@
-// Delay-and-sum energy image (Eq. 1 + Eq. 3).
-// Instantiations of the image kernel for DAS, one instance per window chunk WT.
+// Delay-and-sum energy image (Eq. 1 + Eq. 3; multistatic: Eq. 2 + Eq. 4).
+// Instantiations of the image kernel for DAS, one instance per window chunk WT, monostatic and multistatic.
 #include "image_common.cuh"
 
 namespace uwb {
 
-cudaError_t launch_image_das(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
-                               int threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_image_das(int v, bool ms, const ImgParams& p, const CUtensorMap* tmap,
+                               int ctas, int threads, size_t smem, cudaStream_t st) {
   switch (v) {
     case 4:
-      return launch_variant<BF_DAS, 4>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DAS, 4, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DAS, 4, false>(p, tmap, ctas, threads, smem, st);
     case 8:
-      return launch_variant<BF_DAS, 8>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DAS, 8, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DAS, 8, false>(p, tmap, ctas, threads, smem, st);
     case 16:
-      return launch_variant<BF_DAS, 16>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DAS, 16, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DAS, 16, false>(p, tmap, ctas, threads, smem, st);
     case 20:
-      return launch_variant<BF_DAS, 20>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DAS, 20, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DAS, 20, false>(p, tmap, ctas, threads, smem, st);
     case 32:
-      return launch_variant<BF_DAS, 32>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DAS, 32, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DAS, 32, false>(p, tmap, ctas, threads, smem, st);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
-int occupancy_image_das(int v, int threads, size_t smem) {
+int occupancy_image_das(int v, bool ms, int threads, size_t smem) {
   switch (v) {
     case 4:
-      return occupancy_variant<BF_DAS, 4>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 4, true>(threads, smem)
+                : occupancy_variant<BF_DAS, 4, false>(threads, smem);
     case 8:
-      return occupancy_variant<BF_DAS, 8>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 8, true>(threads, smem)
+                : occupancy_variant<BF_DAS, 8, false>(threads, smem);
     case 16:
-      return occupancy_variant<BF_DAS, 16>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 16, true>(threads, smem)
+                : occupancy_variant<BF_DAS, 16, false>(threads, smem);
     case 20:
-      return occupancy_variant<BF_DAS, 20>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 20, true>(threads, smem)
+                : occupancy_variant<BF_DAS, 20, false>(threads, smem);
     case 32:
-      return occupancy_variant<BF_DAS, 32>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 32, true>(threads, smem)
+                : occupancy_variant<BF_DAS, 32, false>(threads, smem);
     default:
       return 0;
   }

@@ -1,40 +1,51 @@
 // Delay-multiply-and-sum energy image (Section II.B), pair sum through the
 // identity sum_{i<j} x_i x_j = ((sum x)^2 - sum x^2) / 2.
-// Instantiations of the image kernel for DMAS (identity form), one instance per window chunk WT.
+// Instantiations of the image kernel for DMAS (identity form), one instance per window chunk WT, monostatic and
+// multistatic.
 #include "image_common.cuh"
 
 namespace uwb {
 
-cudaError_t launch_image_dmas(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
-                               int threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_image_dmas(int v, bool ms, const ImgParams& p, const CUtensorMap* tmap,
+                               int ctas, int threads, size_t smem, cudaStream_t st) {
   switch (v) {
     case 4:
-      return launch_variant<BF_DMAS_ID, 4>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DMAS_ID, 4, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DMAS_ID, 4, false>(p, tmap, ctas, threads, smem, st);
     case 8:
-      return launch_variant<BF_DMAS_ID, 8>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DMAS_ID, 8, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DMAS_ID, 8, false>(p, tmap, ctas, threads, smem, st);
     case 16:
-      return launch_variant<BF_DMAS_ID, 16>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DMAS_ID, 16, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DMAS_ID, 16, false>(p, tmap, ctas, threads, smem, st);
     case 20:
-      return launch_variant<BF_DMAS_ID, 20>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DMAS_ID, 20, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DMAS_ID, 20, false>(p, tmap, ctas, threads, smem, st);
     case 32:
-      return launch_variant<BF_DMAS_ID, 32>(p, tmap, ctas, threads, smem, st);
+      return ms ? launch_variant<BF_DMAS_ID, 32, true>(p, tmap, ctas, threads, smem, st)
+                : launch_variant<BF_DMAS_ID, 32, false>(p, tmap, ctas, threads, smem, st);
     default:
       return cudaErrorInvalidValue;
   }
 }
 
-int occupancy_image_dmas(int v, int threads, size_t smem) {
+int occupancy_image_dmas(int v, bool ms, int threads, size_t smem) {
   switch (v) {
     case 4:
-      return occupancy_variant<BF_DMAS_ID, 4>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 4, true>(threads, smem)
+                : occupancy_variant<BF_DMAS_ID, 4, false>(threads, smem);
     case 8:
-      return occupancy_variant<BF_DMAS_ID, 8>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 8, true>(threads, smem)
+                : occupancy_variant<BF_DMAS_ID, 8, false>(threads, smem);
     case 16:
-      return occupancy_variant<BF_DMAS_ID, 16>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 16, true>(threads, smem)
+                : occupancy_variant<BF_DMAS_ID, 16, false>(threads, smem);
     case 20:
-      return occupancy_variant<BF_DMAS_ID, 20>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 20, true>(threads, smem)
+                : occupancy_variant<BF_DMAS_ID, 20, false>(threads, smem);
     case 32:
-      return occupancy_variant<BF_DMAS_ID, 32>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 32, true>(threads, smem)
+                : occupancy_variant<BF_DMAS_ID, 32, false>(threads, smem);
     default:
       return 0;
   }

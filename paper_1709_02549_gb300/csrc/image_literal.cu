@@ -5,15 +5,15 @@
 
 namespace uwb {
 
-cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
-                               int threads, size_t smem, cudaStream_t st) {
+cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* tmap,
+                               int ctas, int threads, size_t smem, cudaStream_t st) {
   switch (v) {
     case 16:
-      return launch_variant<BF_DMAS_LIT, 16>(p, tmap, ctas, threads, smem, st);
+      return launch_variant<BF_DMAS_LIT, 16, false>(p, tmap, ctas, threads, smem, st);
     case 32:
-      return launch_variant<BF_DMAS_LIT, 32>(p, tmap, ctas, threads, smem, st);
+      return launch_variant<BF_DMAS_LIT, 32, false>(p, tmap, ctas, threads, smem, st);
     case 64:
-      return launch_variant<BF_DMAS_LIT, 64>(p, tmap, ctas, threads, smem, st);
+      return launch_variant<BF_DMAS_LIT, 64, false>(p, tmap, ctas, threads, smem, st);
     default:
       return cudaErrorInvalidValue;
   }
@@ -22,11 +22,11 @@ cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* t
 int occupancy_image_literal(int v, int threads, size_t smem) {
   switch (v) {
     case 16:
-      return occupancy_variant<BF_DMAS_LIT, 16>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 16, false>(threads, smem);
     case 32:
-      return occupancy_variant<BF_DMAS_LIT, 32>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 32, false>(threads, smem);
     case 64:
-      return occupancy_variant<BF_DMAS_LIT, 64>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 64, false>(threads, smem);
     default:
       return 0;
   }

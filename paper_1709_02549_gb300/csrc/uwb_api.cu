@@ -129,6 +129,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 // Scans of one call: shared sizes and geometry.
 struct Geo {
   int B, M, N, W, h;
+  int R;              // trace rows per scan: M, or the multistatic channel count
+  const int2* chan;   // multistatic channel table (device) or nullptr
   int pitch;    // floats between antenna rows of the trace array
   int n_begin;  // sample index of the first stored sample
   double v, fs;
@@ -162,6 +164,8 @@ int check_common(int batch, const float* traces, int M, int N, const float* ant,
   geo->B = batch;
   geo->M = M;
   geo->N = N;
+  geo->R = M;
+  geo->chan = nullptr;
   geo->pitch = N;
   geo->n_begin = 0;
   geo->W = window;
@@ -181,11 +185,18 @@ struct Variant {
   int wpad;
   int rows;           // trace rows in shared memory
   size_t smem_budget; // shared memory per CTA the span is sized for
+  bool ms;            // multistatic rows (channels)
+  int M, R;           // antennas, trace rows per scan
 };
 
-int pick_variant(int bf, int M, int W, int dim, Variant* out) {
+int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   Variant var;
   var.bf = bf;
+  var.ms = R >= 0;
+  var.M = M;
+  var.R = R >= 0 ? R : M;
+  if (var.ms && bf == BF_DMAS_LIT)
+    return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS is built for monostatic data only");
   if (bf == BF_DMAS_LIT) {
     if (M > 64) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 64 (M=%d)", M);
     var.v = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
@@ -202,8 +213,9 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out) {
     var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : 32;
     var.wpad = (W + var.v - 1) / var.v * var.v;
     var.threads = 256;
-    var.rows = M;
-    var.smem_budget = 56 * 1024;
+    var.rows = var.R;
+    // multistatic rows are M^2 channels: a larger window budget per CTA
+    var.smem_budget = var.ms ? 120 * 1024 : 56 * 1024;
     if (dim == 2) {
       var.tdim[0] = 32; var.tdim[1] = 8; var.tdim[2] = 1;
     } else {
@@ -234,7 +246,7 @@ void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
 // Samples staged per antenna: what the variant's shared-memory budget allows,
 // at most one TMA box width (256), at least the window plus a margin.
 int pick_span(const Variant& var, int M) {
-  const size_t fixed = image_smem_bytes(var.bf, M, var.rows, 0, var.threads);
+  const size_t fixed = image_smem_bytes(var.bf, M, var.rows, 0, var.threads, var.R, var.ms);
   long long span = fixed >= var.smem_budget
                        ? 0
                        : static_cast<long long>((var.smem_budget - fixed) / (4 * var.rows));
@@ -249,13 +261,13 @@ int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* ma
   memset(map, 0, sizeof *map);
   if (!g_encode) return 0;
   if ((reinterpret_cast<uintptr_t>(traces) & 15) || (geo.pitch & 3) || (geo.n_begin & 3) ||
-      geo.N < 1 || geo.M > 256 || span > 256)
+      geo.N < 1 || geo.R > 256 || span > 256)
     return 0;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(geo.N), static_cast<cuuint64_t>(geo.M),
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(geo.N), static_cast<cuuint64_t>(geo.R),
                         static_cast<cuuint64_t>(geo.B)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(geo.pitch) * 4,
-                           static_cast<cuuint64_t>(geo.pitch) * geo.M * 4};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(geo.M), 1};
+                           static_cast<cuuint64_t>(geo.pitch) * geo.R * 4};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(geo.R), 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(traces),
                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -266,8 +278,8 @@ int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* ma
 
 int occupancy(const Variant& var, size_t smem) {
   switch (var.bf) {
-    case BF_DAS: return occupancy_image_das(var.v, var.threads, smem);
-    case BF_DMAS_ID: return occupancy_image_dmas(var.v, var.threads, smem);
+    case BF_DAS: return occupancy_image_das(var.v, var.ms, var.threads, smem);
+    case BF_DMAS_ID: return occupancy_image_dmas(var.v, var.ms, var.threads, smem);
     default: return occupancy_image_literal(var.v, var.threads, smem);
   }
 }
@@ -275,8 +287,9 @@ int occupancy(const Variant& var, size_t smem) {
 cudaError_t launch(const Variant& var, const ImgParams& p, const CUtensorMap* map, int ctas,
                    size_t smem, cudaStream_t st) {
   switch (var.bf) {
-    case BF_DAS: return launch_image_das(var.v, p, map, ctas, var.threads, smem, st);
-    case BF_DMAS_ID: return launch_image_dmas(var.v, p, map, ctas, var.threads, smem, st);
+    case BF_DAS: return launch_image_das(var.v, var.ms, p, map, ctas, var.threads, smem, st);
+    case BF_DMAS_ID:
+      return launch_image_dmas(var.v, var.ms, p, map, ctas, var.threads, smem, st);
     default: return launch_image_literal(var.v, p, map, ctas, var.threads, smem, st);
   }
 }
@@ -293,7 +306,9 @@ ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
   ImgParams p;
   memset(&p, 0, sizeof p);
   p.traces = traces;
-  p.trace_stride = static_cast<long long>(geo.M) * geo.pitch;
+  p.trace_stride = static_cast<long long>(geo.R) * geo.pitch;
+  p.R = geo.R;
+  p.chan = geo.chan;
   p.pitch = geo.pitch;
   p.n_begin = geo.n_begin;
   p.ant = ant;
@@ -324,7 +339,7 @@ int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const 
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
   if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
   pick_warp(var.tdim, delta, p.wdim);
-  const size_t smem = image_smem_bytes(var.bf, p.M, var.rows, p.span, var.threads);
+  const size_t smem = image_smem_bytes(var.bf, p.M, var.rows, p.span, var.threads, var.R, var.ms);
   const int occ = occupancy(var, smem);
   if (occ < 1) return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
   long long ctas = static_cast<long long>(dev.sms) * occ;
@@ -346,16 +361,22 @@ int bf_of(int beamformer) {
 
 int image_impl(int batch, int beamformer, const float* traces, int M, int N, const float* ant,
                long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
-               float* image, long long* peak_index, void* stream) {
+               float* image, long long* peak_index, void* stream, int R = -1,
+               const int* channels = nullptr) {
   Geo geo;
   int st = check_common(batch, traces, M, N, ant, grid, v, fs, window, &geo);
   if (st) return st;
+  if (R >= 0) {
+    if (R < 1 || R > 4096 || !channels) return fail(UWB_ERR_ARG, "multistatic needs 1..4096 channels");
+    geo.R = R;
+    geo.chan = reinterpret_cast<const int2*>(channels);
+  }
   if (!image) return fail(UWB_ERR_ARG, "null image");
   if (ant_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
   const int bf = bf_of(beamformer);
   if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
   Variant var;
-  if ((st = pick_variant(bf, M, window, grid->dim, &var))) return st;
+  if ((st = pick_variant(bf, M, window, grid->dim, &var, geo.chan ? geo.R : -1))) return st;
   Device* dev;
   if ((st = device(&dev))) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -478,10 +499,16 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
 int localize_impl(int batch, const float* traces, int M, int N, const float* ant,
                   long long ant_stride, const uwb_grid* grid, double v, double fs, int window,
                   int beamformer, const uwb_rule* rule, void* workspace, size_t ws_bytes,
-                  uwb_result* out, float* image, void* stream) {
+                  uwb_result* out, float* image, void* stream, int R = -1,
+                  const int* channels = nullptr) {
   Geo geo;
   int st = check_common(batch, traces, M, N, ant, grid, v, fs, window, &geo);
   if (st) return st;
+  if (R >= 0) {
+    if (R < 1 || R > 4096 || !channels) return fail(UWB_ERR_ARG, "multistatic needs 1..4096 channels");
+    geo.R = R;
+    geo.chan = reinterpret_cast<const int2*>(channels);
+  }
   if ((st = check_rule(rule))) return st;
   if (!out) return fail(UWB_ERR_ARG, "null result array");
   if (ant_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
@@ -499,7 +526,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
   const int batch = geo.B, M = geo.M, window = geo.W;
   const int bf = bf_of(beamformer);
   Variant var;
-  if ((st = pick_variant(bf, M, window, geo.g.dim, &var))) return st;
+  if ((st = pick_variant(bf, M, window, geo.g.dim, &var, geo.chan ? geo.R : -1))) return st;
   const Decim dc = decimate(geo.g, *rule);
   const WsLayout wl = ws_layout(batch, dc.Pd);
   if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
@@ -734,6 +761,31 @@ int uwb_image_batch(int batch, int beamformer, const float* traces, int M, int N
                     void* stream) {
   return image_impl(batch, beamformer, traces, M, N, antennas, antenna_stride, grid, v, fs,
                     window, image, peak_index, stream);
+}
+
+int uwb_image_multistatic_batch(int batch, int beamformer, const float* traces, int C, int N,
+                                const int* channels, const float* antennas, int M,
+                                long long antenna_stride, const uwb_grid* grid, double v,
+                                double fs, int window, float* image, long long* peak_index,
+                                void* stream) {
+  return image_impl(batch, beamformer, traces, M, N, antennas, antenna_stride, grid, v, fs,
+                    window, image, peak_index, stream, C, channels);
+}
+
+size_t uwb_localize_multistatic_workspace(int batch, int C, int N, const uwb_grid* grid,
+                                          int beamformer, const uwb_rule* rule) {
+  if (C < 1) return 0;
+  return uwb_localize_workspace(batch, 1, N, grid, beamformer, rule);
+}
+
+int uwb_localize_multistatic_batch(int batch, const float* traces, int C, int N,
+                                   const int* channels, const float* antennas, int M,
+                                   long long antenna_stride, const uwb_grid* grid, double v,
+                                   double fs, int window, int beamformer, const uwb_rule* rule,
+                                   void* workspace, size_t ws_bytes, uwb_result* out,
+                                   float* image, void* stream) {
+  return localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
+                       beamformer, rule, workspace, ws_bytes, out, image, stream, C, channels);
 }
 
 size_t uwb_localize_workspace(int batch, int M, int N, const uwb_grid* grid, int beamformer,

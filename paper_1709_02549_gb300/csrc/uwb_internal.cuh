@@ -33,6 +33,8 @@ struct ImgParams {
   int n_begin;               // sample index of the first stored sample
   const float* ant;          // [M][3] per scan
   long long ant_stride;      // floats between scans' antenna arrays (0 = shared)
+  const int2* chan;          // multistatic: [R] (transmitter, receiver); else nullptr
+  int R;                     // trace rows per scan: M (monostatic) or channels
   int B, M, N, W, h;
   float kscale;              // 2 fs / v: samples per metre of one-way path
   float org[3], pit[3];      // grid origin and pitch (float32)
@@ -57,9 +59,11 @@ struct ImgParams {
 // (rows = M, or the antenna register block for literal DMAS), [M] antennas as
 // float4, the literal kernel's [rows][threads] (offset, fraction) pairs, then
 // an mbarrier, 32 reduction keys, 4 ints.
-inline size_t image_smem_bytes(int bf, int M, int rows, int span, int threads) {
+inline size_t image_smem_bytes(int bf, int M, int rows, int span, int threads, int R = 0,
+                               bool ms = false) {
   const size_t ant_words = 4 * static_cast<size_t>(M);
   size_t b = (static_cast<size_t>(rows) * span + ant_words) * 4;
+  if (ms) b += static_cast<size_t>(R) * 8 + static_cast<size_t>(M) * threads * 4;
   if (bf == BF_DMAS_LIT) b += static_cast<size_t>(rows) * threads * 8;
   b = (b + 7) & ~static_cast<size_t>(7);
   return b + 8 + 32 * 8 + 4 * 4;
@@ -93,16 +97,17 @@ struct FinishParams {
 // Image-kernel launchers, one per beamformer; `v` selects the instance (window
 // chunk WT for DAS / DMAS, antenna register block MMAX for literal DMAS).
 // Each returns cudaGetLastError() after the launch.
-cudaError_t launch_image_das(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
-                             int threads, size_t smem, cudaStream_t st);
-cudaError_t launch_image_dmas(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
-                              int threads, size_t smem, cudaStream_t st);
+// ms selects the multistatic instance (rows are channels).
+cudaError_t launch_image_das(int v, bool ms, const ImgParams& p, const CUtensorMap* tmap,
+                             int ctas, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_image_dmas(int v, bool ms, const ImgParams& p, const CUtensorMap* tmap,
+                              int ctas, int threads, size_t smem, cudaStream_t st);
 cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* tmap, int ctas,
                                  int threads, size_t smem, cudaStream_t st);
 // Sets the dynamic shared-memory limit of the instance and returns its
 // resident CTAs per SM (0 on error).
-int occupancy_image_das(int v, int threads, size_t smem);
-int occupancy_image_dmas(int v, int threads, size_t smem);
+int occupancy_image_das(int v, bool ms, int threads, size_t smem);
+int occupancy_image_dmas(int v, bool ms, int threads, size_t smem);
 int occupancy_image_literal(int v, int threads, size_t smem);
 
 cudaError_t launch_select(const SelParams& p, cudaStream_t st);

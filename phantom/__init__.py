@@ -95,6 +95,20 @@ CONFIGS = {
 }
 
 
+# Multistatic ring of 12 antennas (the paper's experiments use a ring of 12),
+# every transmitter/receiver pair recorded (Eq. 4 sums over all of them).
+CONFIGS["ms2d_12"] = ScanConfig(
+    name="ms2d_12", dim=2, n_antennas=12, array="ring", radius=0.07, grid_n=(256, 256, 1),
+    extent=0.12, n_samples=2048, snr_db=20.0, tumor_half=0.05, n_clutter=20,
+    clutter_amp=(0.05, 0.2), eps_jitter=0.10)
+
+
+def all_channels(m: int) -> np.ndarray:
+    """[m*m, 2] (transmitter, receiver) pairs, transmitter-major."""
+    tx, rx = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    return np.stack([tx.ravel(), rx.ravel()], 1).astype(np.int32)
+
+
 def with_changes(cfg: ScanConfig, **kw) -> ScanConfig:
     return dataclasses.replace(cfg, **kw)
 
@@ -181,9 +195,12 @@ def echo_span(cfg: ScanConfig) -> int:
     return min(cfg.n_samples, int(math.ceil(2.0 * dmax / vmin * cfg.fs)) + cfg.window + 2)
 
 
-def synthesize(cfg: ScanConfig, pos, amp, eps, ants) -> np.ndarray:
-    """Clean traces [M, N] (float64) for a list of point scatterers."""
-    m, n = cfg.n_antennas, cfg.n_samples
+def synthesize(cfg: ScanConfig, pos, amp, eps, ants, channels=None) -> np.ndarray:
+    """Clean traces (float64) for a list of point scatterers: [M, N] monostatic
+    echoes, or [C, N] for channels [C, 2] = (transmitter, receiver) pairs, whose
+    round trip is |r_s - a_tx| + |r_s - a_rx| at the scatterer's speed."""
+    n = cfg.n_samples
+    m = cfg.n_antennas if channels is None else len(channels)
     sigma = 1.0 / (2.0 * np.pi * cfg.f_center)
     half = int(math.ceil(_PULSE_HALF_WIDTH_SIGMAS * sigma * cfg.fs)) + 1
     out = np.zeros(m * n)
@@ -191,7 +208,12 @@ def synthesize(cfg: ScanConfig, pos, amp, eps, ants) -> np.ndarray:
         return out.reshape(m, n)
     vs = C0 / np.sqrt(np.asarray(eps))                                  # [S]
     dist = np.linalg.norm(pos[:, None, :] - ants[None, :, :], axis=2)   # [S, M]
-    tau = 2.0 * dist / vs[:, None]                                      # [S, M] seconds
+    if channels is None:
+        path = 2.0 * dist
+    else:
+        ch = np.asarray(channels)
+        path = dist[:, ch[:, 0]] + dist[:, ch[:, 1]]                    # [S, C]
+    tau = path / vs[:, None]                                            # seconds
     centre = np.floor(tau * cfg.fs).astype(np.int64)
     offs = np.arange(-half, half + 1)
     idx = centre[:, :, None] + offs[None, None, :]                      # [S, M, K]
@@ -203,10 +225,11 @@ def synthesize(cfg: ScanConfig, pos, amp, eps, ants) -> np.ndarray:
     return out.reshape(m, n)
 
 
-def make_scan(cfg: ScanConfig, seed: int) -> dict:
-    """One scan: float32 traces [M, N], float32 antennas [M, 3] and the truth."""
+def make_scan(cfg: ScanConfig, seed: int, channels=None) -> dict:
+    """One scan: float32 traces [M, N] (or [C, N] for multistatic channels),
+    float32 antennas [M, 3] and the truth."""
     sc = draw_scene(cfg, seed)
-    clean = synthesize(cfg, sc["pos"], sc["amp"], sc["eps"], sc["antennas"])
+    clean = synthesize(cfg, sc["pos"], sc["amp"], sc["eps"], sc["antennas"], channels)
     traces = clean
     if cfg.snr_db is not None:
         span = echo_span(cfg)
@@ -220,26 +243,29 @@ def make_scan(cfg: ScanConfig, seed: int) -> dict:
         "tumors": sc["pos"][:nt].copy(),
         "tumor_amp": sc["amp"][:nt].copy(),
         "scatterers": sc["pos"].copy(),
+        "channels": None if channels is None else np.asarray(channels, np.int32),
     }
 
 
 def make_batch(cfg: ScanConfig, n_scans: int, first_scan: int = 0,
-               base_seed: int = BASE_SEED) -> dict:
+               base_seed: int = BASE_SEED, channels=None) -> dict:
     """``n_scans`` scans with seeds ``base_seed + first_scan + s``.
 
-    Returns traces float32 [B, M, N], antennas float32 [M, 3] (one array
-    geometry per workload) and per-scan tumour lists.
+    Returns traces float32 [B, M, N] ([B, C, N] with channels), antennas
+    float32 [M, 3] (one array geometry per workload) and per-scan tumour lists.
     """
-    tr = np.empty((n_scans, cfg.n_antennas, cfg.n_samples), dtype=np.float32)
+    rows = cfg.n_antennas if channels is None else len(channels)
+    tr = np.empty((n_scans, rows, cfg.n_samples), dtype=np.float32)
     tumors = []
     ants = None
     for s in range(n_scans):
-        sc = make_scan(cfg, base_seed + first_scan + s)
+        sc = make_scan(cfg, base_seed + first_scan + s, channels)
         tr[s] = sc["traces"]
         ants = sc["antennas"]
         tumors.append(sc["tumors"])
     return {"traces": tr, "antennas": ants, "tumors": tumors, "grid": cfg.grid(),
-            "v": cfg.v, "fs": cfg.fs, "window": cfg.window}
+            "v": cfg.v, "fs": cfg.fs, "window": cfg.window,
+            "channels": None if channels is None else np.asarray(channels, np.int32)}
 
 
 def point_scatterer_traces(cfg: ScanConfig, points: Sequence, amps: Sequence,

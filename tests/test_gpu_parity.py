@@ -30,9 +30,22 @@ def ring(M, radius, z=0.0, seed=0):
         .astype(np.float32)
 
 
+def bandlimited(rng, rows, N):
+    """Random traces with the UWB pulse's spectrum: white noise filtered by the
+    differentiated-Gaussian pulse (6 GHz at 50 GS/s). The float32 delay error
+    grows with the delay, and its effect on the image with the trace's slope
+    per sample, so stress inputs keep the bandwidth of real echoes."""
+    sigma = 50e9 / (2 * np.pi * 6e9)            # pulse sigma in samples
+    k = np.arange(-12, 13)
+    kern = -(k / sigma) * np.exp(0.5 - 0.5 * (k / sigma) ** 2)
+    noise = rng.standard_normal((rows, N + len(k) - 1))
+    out = np.stack([np.convolve(r, kern, mode="valid") for r in noise])
+    return (out / out.std()).astype(np.float32)
+
+
 def random_case(M, N, n, extent, W, seed, dim=2, radius=0.07):
     rng = np.random.default_rng(seed)
-    tr = rng.standard_normal((M, N)).astype(np.float32)
+    tr = bandlimited(rng, M, N)
     if dim == 2:
         ants = ring(M, radius, seed=seed)
     else:
@@ -340,3 +353,84 @@ def test_presence_matches_oracle(gpu, name, bf, D2):
         if not (t1["tie"] or t2["tie"]):
             assert bool(got[s]) == want, s
         assert r2[s]["decim"] == D2
+
+
+# ------------------------------------------------------------------ multistatic
+
+def _ms_gpu_image(gpu, bf, traces, channels, ants, grid, v, fs, W):
+    traces = np.asarray(traces, np.float32)
+    if traces.ndim == 2:
+        traces = traces[None]
+    B = traces.shape[0]
+    n = list(grid["n"])
+    img = torch.full((B, int(np.prod(n))), -1.0, device="cuda")
+    peak = torch.zeros(B, dtype=torch.int64, device="cuda")
+    gpu.uwb_image_multistatic_batch(bf, dev(traces),
+                                    torch.from_numpy(np.ascontiguousarray(channels, np.int32))
+                                    .cuda(), dev(ants), grid, v, fs, W, img, peak)
+    torch.cuda.synchronize()
+    return img.cpu().numpy().reshape(B, n[2], n[1], n[0]), peak.cpu().numpy()
+
+
+@pytest.mark.parametrize("bf", [0, 1])
+def test_multistatic_image_matches_oracle_full_size(gpu, bf):
+    cfg = phantom.CONFIGS["ms2d_12"]
+    ch = phantom.all_channels(cfg.n_antennas)
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED, ch)
+    img, peak = _ms_gpu_image(gpu, bf, sc["traces"], ch, sc["antennas"], cfg.grid(), cfg.v,
+                              cfg.fs, cfg.window)
+    ref = oracle.image_multistatic(sc["traces"], ch, sc["antennas"], cfg.grid(), cfg.v, cfg.fs,
+                                   cfg.window, BF_ORACLE[bf])
+    assert_image_close(img[0], ref)
+    flat = ref.ravel()
+    assert abs(flat[int(peak[0])] - flat.max()) <= IMG_TOL * flat.max()
+
+
+@pytest.mark.parametrize("bf", [0, 1])
+@pytest.mark.parametrize("case", ["ragged", "global_path"])
+def test_multistatic_image_small_cases(gpu, bf, case):
+    M, N, n, extent, W = (5, 1023, (37, 29, 1), 0.09, 7) if case == "ragged" else \
+        (4, 4096, (16, 12, 1), 0.60, 20)
+    tr, ants, grid, v, fs, W = random_case(M, N, n, extent, W, seed=31)
+    rng = np.random.default_rng(32)
+    ch = rng.integers(0, M, size=(7, 2)).astype(np.int32)
+    trc = bandlimited(rng, 7, N)
+    img, _ = _ms_gpu_image(gpu, bf, trc, ch, ants, grid, v, fs, W)
+    ref = oracle.image_multistatic(trc, ch, ants, grid, v, fs, W, BF_ORACLE[bf])
+    assert_image_close(img[0], ref, what=case)
+
+
+def test_multistatic_channel_index_out_of_range_is_reported(gpu):
+    tr, ants, grid, v, fs, W = random_case(3, 256, (8, 8, 1), 0.05, 4, seed=33)
+    ch = np.array([[0, 1], [2, 7]], np.int32)         # antenna 7 does not exist
+    gpu.uwb_device_status(clear=True)
+    _ms_gpu_image(gpu, 0, tr[:2], ch, ants, grid, v, fs, W)
+    assert gpu.uwb_device_status(clear=True) == -1
+
+
+@pytest.mark.parametrize("bf", [0, 1])
+def test_multistatic_localize_matches_oracle(gpu, bf):
+    cfg = phantom.CONFIGS["ms2d_12"]
+    ch = phantom.all_channels(cfg.n_antennas)
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s, ch) for s in range(3)]
+    traces = np.stack([sc["traces"] for sc in scans])
+    ants = scans[0]["antennas"]
+    grid = cfg.grid()
+    g_rule, o_rule = rule_pair(gpu)
+    B = len(scans)
+    ws = torch.empty(gpu.uwb_localize_multistatic_workspace(B, len(ch), cfg.n_samples, grid, bf,
+                                                            g_rule), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    gpu.uwb_localize_multistatic_batch(dev(traces), torch.from_numpy(ch).cuda(), dev(ants), grid,
+                                       cfg.v, cfg.fs, cfg.window, bf, g_rule, ws, out)
+    torch.cuda.synchronize()
+    res = [record_to_dict(r) for r in gpu.results_from_device(out)]
+    for s, sc in enumerate(scans):
+        o = oracle.localize_multistatic(sc["traces"], ch, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                        BF_ORACLE[bf], o_rule)
+
+        def energy_at(idx, t=sc["traces"]):
+            return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                                  BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
+        compare_localize(res[s], o, energy_at)

@@ -408,3 +408,69 @@ def test_presence_reports_disagreeing_runs():
         present, r1, r2 = oracle.presence(tr, phantom.antenna_positions(cfg), g, cfg.v, cfg.fs,
                                           cfg.window, oracle.DAS, oracle.make_rule(), D2)
         assert present == (r1["loc_idx"] == r2["loc_idx"])
+
+
+# ------------------------------------------------------------- multistatic (Eq. 2, Eq. 4)
+
+def test_diagonal_channels_reproduce_the_monostatic_image():
+    tr, ants, grid = _random_scene(5, seed=21)
+    diag = np.stack([np.arange(5), np.arange(5)], 1)
+    for bf in (oracle.DAS, oracle.DMAS):
+        mono = oracle.image(tr, ants, grid, V, FS, 6, bf)
+        ms = oracle.image_multistatic(tr, diag, ants, grid, V, FS, 6, bf)
+        np.testing.assert_allclose(ms, mono, rtol=1e-12)
+
+
+def test_single_channel_delay_is_transmitter_plus_receiver_path():
+    # tx at the origin, rx at (30 mm, 0): the focal point (0, 40 mm) is 40 mm
+    # from tx and 50 mm from rx, so u = 90 mm of path * 500 samples/m = 45
+    a, b = 0.5, 0.02
+    tr = (a + b * np.arange(128)).astype(np.float32)[None, :]
+    ants = np.array([[0, 0, 0], [0.03, 0, 0]], np.float32)
+    grid = {"dim": 2, "n": [1, 1, 1], "origin": [0.0, 0.04, 0.0], "pitch": [1e-3, 1e-3, 1.0]}
+    got = oracle.image_multistatic(tr, [[0, 1]], ants, grid, V, FS, 1)[0, 0, 0]
+    assert got == pytest.approx((a + b * 45.0) ** 2, rel=1e-6)
+
+
+def test_multistatic_dmas_single_sample_identity():
+    tr, ants, grid = _random_scene(4, seed=22)
+    rng = np.random.default_rng(3)
+    ch = rng.integers(0, 4, size=(6, 2))
+    trc = rng.standard_normal((6, 256)).astype(np.float32)
+    dmas = oracle.image_multistatic(trc, ch, ants, grid, V, FS, 1, oracle.DMAS)
+    das = oracle.image_multistatic(trc, ch, ants, grid, V, FS, 1, oracle.DAS)
+    each = sum(oracle.image_multistatic(trc[c:c + 1], ch[c:c + 1], ants, grid, V, FS, 1)
+               for c in range(6))
+    np.testing.assert_allclose(dmas, ((das - each) / 2) ** 2, rtol=1e-9,
+                               atol=1e-12 * dmas.max())
+
+
+def test_reciprocal_channels_have_the_same_delay():
+    tr, ants, grid = _random_scene(3, seed=23)
+    one = tr[:1]
+    a = oracle.image_multistatic(one, [[0, 2]], ants, grid, V, FS, 5)
+    b = oracle.image_multistatic(one, [[2, 0]], ants, grid, V, FS, 5)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_multistatic_localisation_with_diagonal_channels_is_monostatic():
+    cfg = phantom.CONFIGS["das2d_64"]
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 4)
+    diag = np.stack([np.arange(cfg.n_antennas)] * 2, 1)
+    g = cfg.grid()
+    mono = oracle.localize(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DAS)
+    ms = oracle.localize_multistatic(sc["traces"], diag, sc["antennas"], g, cfg.v, cfg.fs,
+                                     cfg.window, oracle.DAS)
+    for key in ("child", "box_lo", "box_hi", "roi_lo", "roi_hi", "loc_idx", "iters"):
+        assert ms[key] == mono[key]
+
+
+def test_multistatic_scene_locates_its_tumour():
+    cfg = phantom.with_changes(phantom.CONFIGS["ms2d_12"], snr_db=None, n_clutter=0,
+                               grid_n=(96, 96, 1))
+    ch = phantom.all_channels(cfg.n_antennas)
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 1, ch)
+    g = cfg.grid()
+    r = oracle.localize_multistatic(sc["traces"], ch, sc["antennas"], g, cfg.v, cfg.fs,
+                                    cfg.window, oracle.DAS)
+    assert np.linalg.norm(np.array(r["loc_xyz"]) - sc["tumors"][0]) < 2 * g["pitch"][0]
