@@ -164,6 +164,46 @@ int uwb_image_batch(int batch, int beamformer, const float* traces, int M, int N
                     const uwb_grid* grid, double v, double fs, int window,
                     float* image, long long* peak_index, void* stream);
 
+/* ---- Ragged batches -----------------------------------------------------
+ * Scans with different antenna counts, trace lengths, grids (same
+ * dimensionality) and media, in one set of launches, with traces stored as
+ * float32, float16 or bfloat16 (delays and accumulation stay float32). */
+#define UWB_F32 0
+#define UWB_F16 1
+#define UWB_BF16 2
+
+typedef struct uwb_scan {
+  const void* traces;      /* device [M][N], element type of the plan, row-major */
+  const float* antennas;   /* device [M][3] metres */
+  int M, N;
+  uwb_grid grid;
+  double v, fs;
+} uwb_scan;
+
+typedef struct uwb_plan uwb_plan;  /* opaque host object owned by the caller */
+
+/* Builds a plan for `batch` scans (host array, copied): per-scan descriptors,
+ * tensor maps, decimated lattices (the rule applies to each scan's own grid)
+ * and work offsets. Returns NULL and sets *status (if given) on error: every
+ * scan must pass the checks of uwb_localize, and all share grid.dim. */
+uwb_plan* uwb_plan_create(int batch, const uwb_scan* scans, int dtype, int window,
+                          int beamformer, const uwb_rule* rule, int* status);
+/* Device workspace the plan needs (256-byte aligned, owned by the caller). */
+size_t uwb_plan_workspace(const uwb_plan* plan);
+/* Element offset of scan `scan`'s image in the concatenated image array of
+ * uwb_plan_images (scan == batch gives the total). -1 on error. */
+long long uwb_plan_image_offset(const uwb_plan* plan, int scan);
+/* Copies the plan into the workspace (queued on stream). After it, the two
+ * calls below launch kernels only, so a sequence of them can be captured in
+ * a CUDA graph; the workspace is reused by every run of the plan. */
+int uwb_plan_upload(uwb_plan* plan, void* workspace, size_t ws_bytes, void* stream);
+/* Full-resolution images of every scan (each scan's [nz][ny][nx] image at its
+ * uwb_plan_image_offset) and optional per-scan argmax indices. */
+int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* stream);
+/* The segment-search framework on every scan; out: [batch] uwb_result. */
+int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream);
+void uwb_plan_destroy(uwb_plan* plan);
+
 /* Multistatic images (Section II.A: Eq. 2 delays; Eq. 4 DAS, DMAS over pairs
  * of channels): channel c is the echo sent by antenna channels[2c] and
  * received by antenna channels[2c+1] (int32 [C][2], device), its trace is

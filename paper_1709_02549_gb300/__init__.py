@@ -21,7 +21,7 @@ __all__ = [
     "uwb_phase_timing", "uwb_phase_times", "uwb_localize_batch_noalloc",
     "uwb_localize_host_workspace", "uwb_localize_host", "uwb_presence_workspace",
     "uwb_presence_batch", "uwb_image_multistatic_batch", "uwb_localize_multistatic_workspace",
-    "uwb_localize_multistatic_batch",
+    "uwb_localize_multistatic_batch", "UwbScan", "UwbPlan", "UWB_F32", "UWB_F16", "UWB_BF16",
     "UwbError",
 ]
 
@@ -72,6 +72,14 @@ class UwbResult(ctypes.Structure):
                 ("within", _ITD), ("stop_margin", _ITD)]
 
 
+class UwbScan(ctypes.Structure):
+    _fields_ = [("traces", ctypes.c_void_p), ("antennas", ctypes.c_void_p), ("M", ctypes.c_int),
+                ("N", ctypes.c_int), ("grid", UwbGrid), ("v", ctypes.c_double),
+                ("fs", ctypes.c_double)]
+
+
+UWB_F32, UWB_F16, UWB_BF16 = 0, 1, 2
+
 RESULT_DTYPE = np.dtype(UwbResult)
 RESULT_BYTES = ctypes.sizeof(UwbResult)
 
@@ -112,6 +120,14 @@ def lib() -> ctypes.CDLL:
             "uwb_localize_multistatic_workspace": (sz, [i, i, i, gp, i, rp]),
             "uwb_localize_multistatic_batch": (i, [i, vp, i, i, vp, vp, i, ll, gp, d, d, i, i, rp,
                                                    vp, sz, vp, vp, vp]),
+            "uwb_plan_create": (vp, [i, ctypes.POINTER(UwbScan), i, i, i, rp,
+                                     ctypes.POINTER(ctypes.c_int)]),
+            "uwb_plan_workspace": (sz, [vp]),
+            "uwb_plan_image_offset": (ll, [vp, i]),
+            "uwb_plan_upload": (i, [vp, vp, sz, vp]),
+            "uwb_plan_images": (i, [vp, vp, vp, vp]),
+            "uwb_plan_localize": (i, [vp, vp, vp]),
+            "uwb_plan_destroy": (None, [vp]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -357,6 +373,68 @@ def uwb_localize_multistatic_batch(traces, channels, antennas, grid, v, fs, wind
                                                 workspace.numel() * workspace.element_size(),
                                                 _ptr(out, "out"), _f32(image, "image", True),
                                                 _stream(stream)), "uwb_localize_multistatic_batch")
+
+
+class UwbPlan:
+    """A ragged batch (scans of different antenna counts, trace lengths, grids):
+    wraps uwb_plan_create / _upload / _images / _localize / _destroy. scans is a
+    list of dicts {traces: CUDA tensor [M, N] (float32, float16 or bfloat16),
+    antennas: CUDA float32 [M, 3], grid: dict, v, fs}; all traces share a dtype."""
+
+    _DT = {"torch.float32": UWB_F32, "torch.float16": UWB_F16, "torch.bfloat16": UWB_BF16}
+
+    def __init__(self, scans, window, beamformer, rule: UwbRule):
+        self.B = len(scans)
+        dts = {str(sc["traces"].dtype) for sc in scans}
+        if len(dts) != 1 or next(iter(dts)) not in self._DT:
+            raise ValueError("all traces must share one of float32/float16/bfloat16")
+        self.dtype = self._DT[next(iter(dts))]
+        self._keep = [(sc["traces"], sc["antennas"]) for sc in scans]
+        arr = (UwbScan * self.B)()
+        for k, sc in enumerate(scans):
+            t, a = sc["traces"], sc["antennas"]
+            if not (t.is_cuda and a.is_cuda and t.is_contiguous() and a.is_contiguous()):
+                raise ValueError("traces and antennas must be contiguous CUDA tensors")
+            arr[k] = UwbScan(t.data_ptr(), a.data_ptr(), int(t.shape[0]), int(t.shape[1]),
+                             make_grid(sc["grid"]), float(sc["v"]), float(sc["fs"]))
+        st = ctypes.c_int(0)
+        self.handle = lib().uwb_plan_create(self.B, arr, self.dtype, int(window), int(beamformer),
+                                            ctypes.byref(rule), ctypes.byref(st))
+        if not self.handle:
+            raise UwbError(st.value, "uwb_plan_create")
+        self.workspace = None
+
+    def workspace_bytes(self) -> int:
+        return lib().uwb_plan_workspace(self.handle)
+
+    def image_offset(self, scan: int) -> int:
+        return lib().uwb_plan_image_offset(self.handle, int(scan))
+
+    def upload(self, workspace, stream=None):
+        self.workspace = workspace
+        _check(lib().uwb_plan_upload(self.handle, _ptr(workspace, "workspace"),
+                                     workspace.numel() * workspace.element_size(),
+                                     _stream(stream)), "uwb_plan_upload")
+
+    def images(self, images, peak_index=None, stream=None):
+        _check(lib().uwb_plan_images(self.handle, _f32(images, "images"),
+                                     _ptr(peak_index, "peak_index", True), _stream(stream)),
+               "uwb_plan_images")
+
+    def localize(self, out, stream=None):
+        _check(lib().uwb_plan_localize(self.handle, _ptr(out, "out"), _stream(stream)),
+               "uwb_plan_localize")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().uwb_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_SCRATCH_BYTES = 16 << 20

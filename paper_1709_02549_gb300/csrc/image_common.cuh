@@ -19,10 +19,16 @@
 //  * fused epilogue: image store, compact-profile store, and a block-reduced
 //    64-bit (energy, -index) key folded into the scan's argmax with atomicMax.
 // Scans whose window does not fit the staged span fall back to bounds-checked
-// global loads (same arithmetic).
+// global loads (same arithmetic). Traces may be stored as float32, float16 or
+// bfloat16; the staged window is always float32 (16-bit traces land in a raw
+// area first and are widened once per staging), so the arithmetic is float32
+// in every case.
 #pragma once
 
 #include <climits>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ptx.cuh"
 #include "uwb_internal.cuh"
@@ -39,28 +45,74 @@ struct KernelShape {
   static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : (BF == BF_DAS ? (V <= 20 ? 4 : 3) : (V <= 20 ? 3 : 2));
 };
 
+// Per-scan quantities: ragged instances (RG) read the scan's descriptor in
+// shared memory; uniform instances read the launch parameters, which stay
+// operands of the instructions that use them rather than occupying registers.
+template <bool RG>
+__device__ __forceinline__ int scan_M(const ImgParams& P, const ScanDesc* sS) {
+  return RG ? sS->M : P.M;
+}
+template <bool RG>
+__device__ __forceinline__ int scan_R(const ImgParams& P, const ScanDesc* sS) {
+  return RG ? sS->R : P.R;
+}
+template <bool RG>
+__device__ __forceinline__ float scan_kscale(const ImgParams& P, const ScanDesc* sS) {
+  return RG ? sS->kscale : P.kscale;
+}
+template <bool RG>
+__device__ __forceinline__ float scan_org(const ImgParams& P, const ScanDesc* sS, int a) {
+  return RG ? sS->org[a] : P.org[a];
+}
+template <bool RG>
+__device__ __forceinline__ float scan_pit(const ImgParams& P, const ScanDesc* sS, int a) {
+  return RG ? sS->pit[a] : P.pit[a];
+}
+template <bool RG>
+__device__ __forceinline__ int scan_gn(const ImgParams& P, const ScanDesc* sS, int a) {
+  return RG ? sS->gn[a] : P.gn[a];
+}
+
+// One stored sample, widened to float32 (global-load path).
+__device__ __forceinline__ float ld_trace(const void* base, long long i, int dtype) {
+  if (dtype == DT_F32) return __ldg(static_cast<const float*>(base) + i);
+  const unsigned short b = __ldg(static_cast<const unsigned short*>(base) + i);
+  return dtype == DT_F16 ? __half2float(__ushort_as_half(b))
+                         : __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// Sample n (absolute index) of trace row i, zero outside the stored range.
+__device__ __forceinline__ float sample_at(const ScanDesc& S, int dtype, int i, int n) {
+  const int o = n - S.n_begin;
+  if (o < 0 || o >= S.N) return 0.f;
+  return ld_trace(S.traces, static_cast<long long>(i) * S.pitch + o, dtype);
+}
+
 // -------------------------------------------------------------- DAS / DMAS-identity
 // Rows are the M antennas (monostatic: delay 2|r - a_i| fs / v) or, with MS,
 // the R channels (transmitter, receiver) of a multistatic recording (Eq. 2:
 // delay (|r - a_tx| + |r - a_rx|) fs / v); for MS each thread first puts its
 // focal point's distance to every antenna in sD[antenna][thread].
-template <int BF, int WT, bool STAGED, bool MS>
-__device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __restrict__ sTr,
+template <int BF, int WT, bool STAGED, bool MS, bool RG>
+__device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* __restrict__ sS,
+                                            const float* __restrict__ sTr,
                                             const float4* __restrict__ sAnt,
                                             const int2* __restrict__ sCh, float* __restrict__ sD,
-                                            const float* __restrict__ gTr, int nlo, int cl_lo,
-                                            int cl_hi, float px, float py, float pz) {
+                                            int nlo, int cl_lo, int cl_hi, float px, float py,
+                                            float pz) {
   float energy = 0.f;
-  const int R = P.R;
+  const int R = scan_R<RG>(P, sS);
+  const float kscale = scan_kscale<RG>(P, sS);
   const int T = blockDim.x, tid = threadIdx.x;
   if (MS) {
-    for (int i = 0; i < P.M; ++i) {
+    const int M = scan_M<RG>(P, sS);
+    for (int i = 0; i < M; ++i) {
       const float4 a = sAnt[i];
       const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
       sD[i * T + tid] = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
     }
   }
-  const float half_k = 0.5f * P.kscale;
+  const float half_k = 0.5f * kscale;
   for (int k0 = 0; k0 < P.W; k0 += WT) {
     float s1[WT], s2[WT];
 #pragma unroll
@@ -80,7 +132,7 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
         const float dy = py - a.y;
         const float dz = pz - a.z;
         const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        t = fmaf(d, P.kscale, -hoff);
+        t = fmaf(d, kscale, -hoff);
       }
       const float fl = floorf(t);
       const float f = t - fl;
@@ -92,12 +144,9 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const float* __r
 #pragma unroll
         for (int k = 0; k <= WT; ++k) y[k] = row[k];
       } else {
-        const float* row = gTr + static_cast<size_t>(i) * P.pitch;
+        const ScanDesc S = *sS;
 #pragma unroll
-        for (int k = 0; k <= WT; ++k) {
-          const int n = n0 + k - P.n_begin;
-          y[k] = (n >= 0 && n < P.N) ? __ldg(row + n) : 0.f;
-        }
+        for (int k = 0; k <= WT; ++k) y[k] = sample_at(S, P.dtype, i, n0 + k);
       }
       if (BF == BF_DAS) {
         const float g = 1.f - f;
@@ -147,10 +196,10 @@ struct LitRaw {
   float f, y0, y1, y2;
 };
 
-template <bool STAGED>
-__device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const float* __restrict__ sTr,
-                                           const float2* __restrict__ sNF,
-                                           const float* __restrict__ gTr, int i, int T, int tid,
+template <bool STAGED, bool RG>
+__device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const ScanDesc* __restrict__ sS,
+                                           const float* __restrict__ sTr,
+                                           const float2* __restrict__ sNF, int i, int T, int tid,
                                            int k0) {
   const float2 nf = sNF[i * T + tid];
   const int off = __float_as_int(nf.x) + k0;
@@ -161,12 +210,11 @@ __device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const float* __re
     r.y0 = row[0];
     r.y1 = row[1];
     r.y2 = row[2];
-  } else if (i < P.M) {
-    const float* row = gTr + static_cast<size_t>(i) * P.pitch;
-    const int o = off - P.n_begin;
-    r.y0 = (o >= 0 && o < P.N) ? __ldg(row + o) : 0.f;
-    r.y1 = (o + 1 >= 0 && o + 1 < P.N) ? __ldg(row + o + 1) : 0.f;
-    r.y2 = (o + 2 >= 0 && o + 2 < P.N) ? __ldg(row + o + 2) : 0.f;
+  } else if (i < scan_M<RG>(P, sS)) {
+    const ScanDesc S = *sS;
+    r.y0 = sample_at(S, P.dtype, i, off);
+    r.y1 = sample_at(S, P.dtype, i, off + 1);
+    r.y2 = sample_at(S, P.dtype, i, off + 2);
   } else {
     r.y0 = r.y1 = r.y2 = 0.f;
   }
@@ -180,16 +228,17 @@ __device__ __forceinline__ float2 lit_interp(const LitRaw& r) {
   return __ffma2_rn(make_float2(r.f, r.f), make_float2(r.y1, r.y2), t);
 }
 
-// sTr holds MMAX rows; rows M..MMAX-1 are zero (written at kernel start).
-template <int MMAX, bool STAGED>
-__device__ __forceinline__ float energy_literal(const ImgParams& P, const float* __restrict__ sTr,
+// sTr holds MMAX rows; rows M..MMAX-1 are zero (written at each staging).
+template <int MMAX, bool STAGED, bool RG>
+__device__ __forceinline__ float energy_literal(const ImgParams& P,
+                                                const ScanDesc* __restrict__ sS,
+                                                const float* __restrict__ sTr,
                                                 const float4* __restrict__ sAnt,
-                                                float2* __restrict__ sNF,
-                                                const float* __restrict__ gTr, int nlo,
-                                                int cl_lo, int cl_hi, float px, float py,
-                                                float pz) {
+                                                float2* __restrict__ sNF, int nlo, int cl_lo,
+                                                int cl_hi, float px, float py, float pz) {
   const int T = blockDim.x, tid = threadIdx.x;
-  const int M = P.M;
+  const int M = scan_M<RG>(P, sS);
+  const float kscale = scan_kscale<RG>(P, sS);
   const float hf = static_cast<float>(P.h);
   // delays of every antenna for this focal point: (sample offset, fraction)
   for (int i = 0; i < MMAX; ++i) {
@@ -201,7 +250,7 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
       const float dy = py - a.y;
       const float dz = pz - a.z;
       const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-      const float t = fmaf(d, P.kscale, -hf);
+      const float t = fmaf(d, kscale, -hf);
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
@@ -215,11 +264,11 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
     float2 acc[8];
 #pragma unroll
     for (int a = 0; a < 8; ++a) acc[a] = make_float2(0.f, 0.f);
-    LitRaw next = lit_load<STAGED>(P, sTr, sNF, gTr, 0, T, tid, k0);
+    LitRaw next = lit_load<STAGED, RG>(P, sS, sTr, sNF, 0, T, tid, k0);
 #pragma unroll
     for (int j = 0; j < MMAX; ++j) {
       const LitRaw cur = next;
-      if (j + 1 < MMAX) next = lit_load<STAGED>(P, sTr, sNF, gTr, j + 1, T, tid, k0);
+      if (j + 1 < MMAX) next = lit_load<STAGED, RG>(P, sS, sTr, sNF, j + 1, T, tid, k0);
       x[j] = lit_interp(cur);
 #pragma unroll
       for (int i = 0; i < j; ++i) acc[(i + j) & 7] = __ffma2_rn(x[i], x[j], acc[(i + j) & 7]);
@@ -235,32 +284,72 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P, const float*
   return energy;
 }
 
+// The global-load fallback (a window wider than the staged span) runs as a
+// real call, so its bounds checks and type conversions do not add to the
+// register allocation of the staged hot path.
+template <int BF, int WT, bool MS>
+__device__ __noinline__ float energy_sum_global(const ImgParams& P, const ScanDesc* sS,
+                                                const float4* sAnt, const int2* sCh, float* sD,
+                                                float px, float py, float pz) {
+  return energy_sum<BF, WT, false, MS, true>(P, sS, nullptr, sAnt, sCh, sD, 0, 0, 0, px, py, pz);
+}
+
+template <int MMAX>
+__device__ __noinline__ float energy_literal_global(const ImgParams& P, const ScanDesc* sS,
+                                                    const float4* sAnt, float2* sNF, float px,
+                                                    float py, float pz) {
+  return energy_literal<MMAX, false, true>(P, sS, nullptr, sAnt, sNF, 0, 0, 0, px, py, pz);
+}
+
+// The descriptor of scan `scan`: from the per-scan array of a ragged batch, or
+// derived from the uniform batch's parameters.
+__device__ __forceinline__ void make_desc(const ImgParams& P, int scan, ScanDesc& S) {
+  if (P.descs) {
+    S = P.descs[scan];
+    return;
+  }
+  S.traces = static_cast<const char*>(P.traces) +
+             static_cast<long long>(scan) * P.trace_stride * dtype_bytes(P.dtype);
+  S.ant = P.ant + static_cast<long long>(scan) * P.ant_stride;
+  S.img_off = static_cast<long long>(scan) * P.gP;
+  S.cmp_off = static_cast<long long>(scan) * P.compact_stride;
+  S.pitch = P.pitch;
+  S.n_begin = P.n_begin;
+  S.N = P.N;
+  S.M = P.M;
+  S.R = P.R;
+  S.tma = P.use_tma ? scan : -1;  // uniform: z coordinate of the launch's tensor map
+  S.kscale = P.kscale;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    S.org[a] = P.org[a];
+    S.pit[a] = P.pit[a];
+    S.gn[a] = P.gn[a];
+  }
+}
+
 // ------------------------------------------------------------------ the kernel
 // V = window chunk WT (DAS, DMAS identity) or antenna register block MMAX
-// (literal DMAS); MS = multistatic rows. Dynamic shared memory (see
-// image_smem_bytes): [rows][span] traces | [M] antennas (float4) | (MS) [R]
-// channels | (literal) [V][T] delays | (MS) [M][T] distances | mbarrier and
-// reduction slots.
-template <int BF, int V, bool MS>
+// (literal DMAS); MS = multistatic rows. Dynamic shared memory as laid out by
+// image_smem_layout.
+template <int BF, int V, bool MS, bool RG>
 __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V>::min_blocks)
     k_image(const __grid_constant__ CUtensorMap tmap, const ImgParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
-  const int M = P.M;
-  const int R = P.R;  // trace rows per scan: M antennas, or R channels
   // literal DMAS keeps V (>= M) trace rows; rows M..V-1 stay zero
-  const int rows = (BF == BF_DMAS_LIT) ? V : R;
+  const int rows = (BF == BF_DMAS_LIT) ? V : P.Rcap;
+  const SmemLayout Lay = image_smem_layout(BF, P.Mcap, P.Rcap, rows, P.span, T, MS, P.dtype);
   float* sTr = reinterpret_cast<float*>(smem_raw);
-  // antennas as (x, y, z, 0): one broadcast 16-byte load per antenna
-  float4* sAnt = reinterpret_cast<float4*>(sTr + static_cast<size_t>(rows) * P.span);
-  int2* sCh = reinterpret_cast<int2*>(sAnt + M);
-  float2* sNF = reinterpret_cast<float2*>(sCh + (MS ? R : 0));
-  const size_t nf_words = (BF == BF_DMAS_LIT) ? static_cast<size_t>(V) * T * 2 : 0;
-  float* sD = reinterpret_cast<float*>(sNF) + nf_words;
-  const size_t d_words = MS ? static_cast<size_t>(M) * T : 0;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sD + d_words);
-  unsigned long long* sKey = reinterpret_cast<unsigned long long*>(bar + 1);  // [32]
-  int* sInt = reinterpret_cast<int*>(sKey + 32);                              // [4]
+  unsigned short* sRaw = reinterpret_cast<unsigned short*>(smem_raw + Lay.raw);
+  float4* sAnt = reinterpret_cast<float4*>(smem_raw + Lay.ant);  // (x, y, z, 0)
+  int2* sCh = reinterpret_cast<int2*>(smem_raw + Lay.ch);
+  float2* sNF = reinterpret_cast<float2*>(smem_raw + Lay.nf);
+  float* sD = reinterpret_cast<float*>(smem_raw + Lay.d);
+  ScanDesc* sS = reinterpret_cast<ScanDesc*>(smem_raw + Lay.desc);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Lay.bar);
+  unsigned long long* sKey = reinterpret_cast<unsigned long long*>(smem_raw + Lay.key);
+  int* sInt = reinterpret_cast<int*>(smem_raw + Lay.ints);
 
   // thread -> point of the tile (warp sub-blocks of wdim points)
   const int lane = tid & 31, warp = tid >> 5;
@@ -269,14 +358,16 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   const int ly = ((warp / nbx) % nby) * P.wdim[1] + (lane / P.wdim[0]) % P.wdim[1];
   const int lz = (warp / (nbx * nby)) * P.wdim[2] + lane / (P.wdim[0] * P.wdim[1]);
 
-  const bool tma_ok = P.use_tma && ((smem_u32(sTr) & 127u) == 0);
+  // where a TMA copy of the window lands: the float32 window itself, or the
+  // raw 16-bit area that is widened afterwards
+  void* tma_dst = P.dtype == DT_F32 ? static_cast<void*>(sTr) : static_cast<void*>(sRaw);
+  const bool tma_ok = (P.use_tma || P.tmaps) && ((smem_u32(tma_dst) & 127u) == 0);
   if (tid == 0) mbar_init(bar, 1);
-  if (BF == BF_DMAS_LIT)
-    for (int j = tid; j < (rows - M) * P.span; j += T) sTr[M * P.span + j] = 0.f;
   if (MS) {
     // channel table (shared by every scan); indices outside the array are
     // recorded as an argument error and clamped so that no access leaves it
-    for (int r = tid; r < R; r += T) {
+    const int M = P.M;
+    for (int r = tid; r < P.R; r += T) {
       int2 c = P.chan[r];
       if (c.x < 0 || c.x >= M || c.y < 0 || c.y >= M) atomicExch(P.status, UWB_ERR_ARG);
       c.x = min(max(c.x, 0), M - 1);
@@ -306,7 +397,6 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   int staged = -1;
   bool fits = false;
   int nlo = 0, cl_lo = 0, cl_hi = 0;
-  const float* gTr = nullptr;
 
   for (long long g = g_begin; g < g_end; ++g) {
     long long t;
@@ -320,22 +410,30 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
     const LatBox L = P.boxes ? P.boxes[scan] : P.uni;
 
     if (scan != staged) {
-      // ---- stage scan `scan`: antennas, reachable sample window ----
+      // ---- stage scan `scan`: descriptor, antennas, reachable sample window ----
       __syncthreads();  // every read of the previous window is complete
-      const float* ga = P.ant + static_cast<long long>(scan) * P.ant_stride;
-      for (int j = tid; j < M; j += T)
-        sAnt[j] = make_float4(ga[3 * j + 0], ga[3 * j + 1], ga[3 * j + 2], 0.f);
       if (tid == 0) {
+        make_desc(P, scan, *sS);
         sInt[0] = INT_MAX;
         sInt[1] = INT_MIN;
       }
       __syncthreads();
+      const int M = scan_M<RG>(P, sS), R = scan_R<RG>(P, sS);
+      const float kscale = scan_kscale<RG>(P, sS);
+      for (int j = tid; j < M; j += T) {
+        const float* ga = sS->ant;
+        sAnt[j] = make_float4(ga[3 * j + 0], ga[3 * j + 1], ga[3 * j + 2], 0.f);
+      }
+      if (BF == BF_DMAS_LIT)  // zero the padded antenna rows of this scan
+        for (int j = tid; j < (rows - R) * P.span; j += T) sTr[R * P.span + j] = 0.f;
+      __syncthreads();
       float bmin[3], bmax[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float p0 = fmaf(static_cast<float>(L.lo[a]), P.pit[a], P.org[a]);
-        const float p1 =
-            fmaf(static_cast<float>(L.lo[a] + L.step[a] * (L.cnt[a] - 1)), P.pit[a], P.org[a]);
+        const float p0 = fmaf(static_cast<float>(L.lo[a]), scan_pit<RG>(P, sS, a),
+                              scan_org<RG>(P, sS, a));
+        const float p1 = fmaf(static_cast<float>(L.lo[a] + L.step[a] * (L.cnt[a] - 1)),
+                              scan_pit<RG>(P, sS, a), scan_org<RG>(P, sS, a));
         bmin[a] = fminf(p0, p1);
         bmax[a] = fmaxf(p0, p1);
       }
@@ -354,15 +452,15 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
           sD[i] = sqrtf(dn2);  // scratch until the tile computation starts
           sD[M + i] = sqrtf(df2);
         } else {
-          const float umin = fminf(fmaxf(sqrtf(dn2) * P.kscale - P.h, -1e8f), 1e8f);
-          const float umax = fminf(fmaxf(sqrtf(df2) * P.kscale - P.h, -1e8f), 1e8f);
+          const float umin = fminf(fmaxf(sqrtf(dn2) * kscale - P.h, -1e8f), 1e8f);
+          const float umax = fminf(fmaxf(sqrtf(df2) * kscale - P.h, -1e8f), 1e8f);
           atomicMin(&sInt[0], static_cast<int>(floorf(umin)) - 2);
           atomicMax(&sInt[1], static_cast<int>(floorf(umax)) + P.wpad + 3);
         }
       }
       if (MS) {
         __syncthreads();
-        const float half_k = 0.5f * P.kscale;
+        const float half_k = 0.5f * kscale;
         for (int r = tid; r < R; r += T) {
           const int2 c = sCh[r];
           const float umin = fminf(fmaxf((sD[c.x] + sD[c.y]) * half_k - P.h, -1e8f), 1e8f);
@@ -373,18 +471,22 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
         }
       }
       __syncthreads();
-      nlo = sInt[0] & ~3;  // TMA needs a 16-byte aligned sample coordinate
+      // TMA needs a 16-byte aligned sample coordinate (4 or 8 samples)
+      nlo = sInt[0] & (P.dtype == DT_F32 ? ~3 : ~7);
       fits = (static_cast<long long>(sInt[1]) - nlo) <= P.span;
       cl_lo = nlo;
       // a thread reads samples n0 .. n0 + (window chunk) of the staged row
       cl_hi = nlo + P.span - 1 - ((BF == BF_DMAS_LIT) ? P.wpad : V);
-      gTr = P.traces + static_cast<long long>(scan) * P.trace_stride;
       if (fits) {
-        if (tma_ok) {
+        const int tma_index = sS->tma;
+        if (tma_ok && tma_index >= 0) {
           if (tid == 0) {
+            const CUtensorMap* map = P.tmaps ? P.tmaps + tma_index : &tmap;
+            const int z = P.tmaps ? 0 : tma_index;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(R) * P.span * 4u);
-            tma_load_3d(sTr, &tmap, nlo - P.n_begin, 0, scan, bar);
+            mbar_arrive_expect_tx(
+                bar, static_cast<uint32_t>(R) * P.span * static_cast<uint32_t>(dtype_bytes(P.dtype)));
+            tma_load_3d(tma_dst, map, nlo - sS->n_begin, 0, z, bar);
           }
           uint32_t ok = 0;
           for (long it = 0; it < kWaitProbes && !ok; ++it) ok = mbar_try_wait(bar, phase);
@@ -398,12 +500,21 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
             return;
           }
           phase ^= 1u;
+          if (P.dtype != DT_F32) {  // widen the 16-bit window
+            const int total_s = R * P.span;
+            for (int j = tid; j < total_s; j += T) {
+              const unsigned short b = sRaw[j];
+              sTr[j] = P.dtype == DT_F16 ? __half2float(__ushort_as_half(b))
+                                         : __bfloat162float(__ushort_as_bfloat16(b));
+            }
+            __syncthreads();
+          }
         } else {
+          const ScanDesc S = *sS;
           const int total_s = R * P.span;
           for (int j = tid; j < total_s; j += T) {
             const int i = j / P.span;
-            const int n = nlo + (j - i * P.span) - P.n_begin;
-            sTr[j] = (n >= 0 && n < P.N) ? gTr[static_cast<size_t>(i) * P.pitch + n] : 0.f;
+            sTr[j] = sample_at(S, P.dtype, i, nlo + (j - i * P.span));
           }
           __syncthreads();
         }
@@ -422,27 +533,27 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
     const int gx = L.lo[0] + L.step[0] * kx;
     const int gy = L.lo[1] + L.step[1] * ky;
     const int gz = L.lo[2] + L.step[2] * kz;
-    const long long lin =
-        gx + static_cast<long long>(P.gn[0]) * (gy + static_cast<long long>(P.gn[1]) * gz);
+    const long long lin = gx + static_cast<long long>(scan_gn<RG>(P, sS, 0)) *
+                                   (gy + static_cast<long long>(scan_gn<RG>(P, sS, 1)) * gz);
     float energy = 0.f;
     if (valid) {
-      const float px = fmaf(static_cast<float>(gx), P.pit[0], P.org[0]);
-      const float py = fmaf(static_cast<float>(gy), P.pit[1], P.org[1]);
-      const float pz = fmaf(static_cast<float>(gz), P.pit[2], P.org[2]);
+      const float px = fmaf(static_cast<float>(gx), scan_pit<RG>(P, sS, 0), scan_org<RG>(P, sS, 0));
+      const float py = fmaf(static_cast<float>(gy), scan_pit<RG>(P, sS, 1), scan_org<RG>(P, sS, 1));
+      const float pz = fmaf(static_cast<float>(gz), scan_pit<RG>(P, sS, 2), scan_org<RG>(P, sS, 2));
       if constexpr (BF == BF_DMAS_LIT) {
-        energy = fits ? energy_literal<V, true>(P, sTr, sAnt, sNF, gTr, nlo, cl_lo, cl_hi, px,
-                                                py, pz)
-                      : energy_literal<V, false>(P, sTr, sAnt, sNF, gTr, nlo, cl_lo, cl_hi,
-                                                 px, py, pz);
+        energy = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi, px,
+                                                    py, pz)
+                      : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
       } else {
-        energy = fits ? energy_sum<BF, V, true, MS>(P, sTr, sAnt, sCh, sD, gTr, nlo, cl_lo,
-                                                    cl_hi, px, py, pz)
-                      : energy_sum<BF, V, false, MS>(P, sTr, sAnt, sCh, sD, gTr, nlo, cl_lo,
-                                                     cl_hi, px, py, pz);
+        energy = fits ? energy_sum<BF, V, true, MS, RG>(P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo,
+                                                        cl_hi, px, py, pz)
+                      : energy_sum_global<BF, V, MS>(P, sS, sAnt, sCh, sD, px, py, pz);
       }
-      if (P.image) P.image[static_cast<long long>(scan) * P.gP + lin] = energy;
+      const long long img_off = RG ? sS->img_off : static_cast<long long>(scan) * P.gP;
+      const long long cmp_off = RG ? sS->cmp_off : static_cast<long long>(scan) * P.compact_stride;
+      if (P.image) P.image[img_off + lin] = energy;
       if (P.compact)
-        P.compact[static_cast<long long>(scan) * P.compact_stride + kx +
+        P.compact[cmp_off + kx +
                   static_cast<long long>(L.cnt[0]) * (ky + static_cast<long long>(L.cnt[1]) * kz)] =
             energy;
     }
@@ -469,23 +580,46 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   }
 }
 
+// Instance selection: ragged batches (descriptors present) run the RG
+// instance; multistatic batches the MS one.
 template <int BF, int V, bool MS>
 cudaError_t launch_variant(const ImgParams& p, const CUtensorMap* tmap, int ctas, int threads,
                            size_t smem, cudaStream_t st) {
-  k_image<BF, V, MS><<<ctas, threads, smem, st>>>(*tmap, p);
+  if (p.descs && !MS)
+    k_image<BF, V, false, true><<<ctas, threads, smem, st>>>(*tmap, p);
+  else
+    k_image<BF, V, MS, false><<<ctas, threads, smem, st>>>(*tmap, p);
   return cudaGetLastError();
 }
 
-template <int BF, int V, bool MS>
-int occupancy_variant(int threads, size_t smem) {
-  if (cudaFuncSetAttribute(k_image<BF, V, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess)
+// The instance's dynamic shared-memory limit is raised to the device's
+// opt-in maximum (it is only a ceiling), so that launches of any smaller size
+// stay valid whichever size was queried last.
+template <int BF, int V, bool MS, bool RG>
+int occupancy_instance(int threads, size_t smem) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  if (smem > static_cast<size_t>(optin)) return 0;
+  if (cudaFuncSetAttribute(k_image<BF, V, MS, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin) != cudaSuccess)
     return 0;
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_image<BF, V, MS>, threads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_image<BF, V, MS, RG>, threads,
                                                     smem) != cudaSuccess)
     return 0;
   return blocks;
+}
+
+// Resident CTAs of the uniform instance; the ragged instance shares its shape
+// and gets the same dynamic shared-memory limit.
+template <int BF, int V, bool MS>
+int occupancy_variant(int threads, size_t smem) {
+  const int a = occupancy_instance<BF, V, MS, false>(threads, smem);
+  if (MS) return a;
+  const int b = occupancy_instance<BF, V, false, true>(threads, smem);
+  return a < b ? a : b;
 }
 
 }  // namespace uwb

@@ -31,7 +31,7 @@ struct KBox {
   long long n;
 };
 
-__device__ KBox lattice_in_box(const SelParams& P, const int lo[3], const int hi[3]) {
+__device__ KBox lattice_in_box(const SelScan& P, const int lo[3], const int hi[3]) {
   KBox b;
   b.n = 1;
 #pragma unroll
@@ -57,7 +57,7 @@ struct Stats {
 
 // Lane-partial sum and sum of squares of the raw energies of the decimated
 // points inside a box (one pass, float64).
-__device__ __forceinline__ void lane_sums(const SelParams& P, const float* prof, const KBox& b,
+__device__ __forceinline__ void lane_sums(const SelScan& P, const float* prof, const KBox& b,
                                           double& s1, double& s2) {
   const int lane = threadIdx.x & 31;
   const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
@@ -78,7 +78,7 @@ __device__ __forceinline__ void lane_sums(const SelParams& P, const float* prof,
 // mean and scatter (sum of squared deviations, as sum e^2 - (sum e)^2 / n; the
 // energies are non-negative and bounded, so float64 keeps ~14 digits even for
 // nearly flat segments). float64 is this GPU's slow path, so one pass.
-__device__ Stats box_stats(const SelParams& P, const float* prof, double pmax, const KBox& b) {
+__device__ Stats box_stats(const SelScan& P, const float* prof, double pmax, const KBox& b) {
   Stats st;
   st.n = b.n;
   st.sum = st.mean = st.scatter = 0.0;
@@ -116,7 +116,22 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   const int lane = threadIdx.x & 31;
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= P.B) return;
-  const float* prof = P.profile + static_cast<long long>(s) * P.prof_stride;
+  // this scan's lattice and grid
+  SelScan Q;
+  if (P.scans) {
+    Q = P.scans[s];
+  } else {
+    Q.prof_off = static_cast<long long>(s) * P.prof_stride;
+    for (int a = 0; a < 3; ++a) {
+      Q.gn[a] = P.gn[a];
+      Q.off[a] = P.off[a];
+      Q.step[a] = P.step[a];
+      Q.cnt[a] = P.cnt[a];
+    }
+    Q.D = P.D;
+    Q.max_iters = P.max_iters;
+  }
+  const float* prof = P.profile + Q.prof_off;
   uwb_result* R = P.out + s;
   LatBox* box = P.boxes + s;
 
@@ -126,7 +141,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     for (int j = lane; j < static_cast<int>(sizeof(uwb_result) / 4); j += 32) w[j] = 0;
     __syncwarp();
   }
-  const long long Pd = static_cast<long long>(P.cnt[0]) * P.cnt[1] * P.cnt[2];
+  const long long Pd = static_cast<long long>(Q.cnt[0]) * Q.cnt[1] * Q.cnt[2];
   float fmx = 0.f;
   bool bad = false;
   for (long long j = lane; j < Pd; j += 32) {
@@ -139,10 +154,10 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   for (int o = 16; o > 0; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(0xFFFFFFFFu, fmx, o));
 
   if (lane == 0) {
-    R->decim = P.D;
+    R->decim = Q.D;
     for (int a = 0; a < 3; ++a) {
-      R->offset[a] = P.off[a];
-      R->dcount[a] = P.cnt[a];
+      R->offset[a] = Q.off[a];
+      R->dcount[a] = Q.cnt[a];
       R->loc_idx[a] = -1;
     }
     R->profile_max = fmx;
@@ -165,13 +180,13 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   const int nchild = 1 << dim;
   const uwb_rule& rule = P.rule;
 
-  int Rlo[3] = {0, 0, 0}, Rhi[3] = {P.gn[0], P.gn[1], P.gn[2]};
-  Stats sa = box_stats(P, prof, pmax, lattice_in_box(P, Rlo, Rhi));
+  int Rlo[3] = {0, 0, 0}, Rhi[3] = {Q.gn[0], Q.gn[1], Q.gn[2]};
+  Stats sa = box_stats(Q, prof, pmax, lattice_in_box(Q, Rlo, Rhi));
   double var_prev = sa.scatter / static_cast<double>(sa.n);
   double B_prev = 0.0, W_prev = 0.0;
   int iters = 0, n_logged = 0, stop = UWB_STOP_NONE;
 
-  for (int i = 1; i <= P.max_iters; ++i) {
+  for (int i = 1; i <= Q.max_iters; ++i) {
     const int li = i - 1;
     int mid[3];
 #pragma unroll
@@ -195,9 +210,9 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
         }
       }
       if (!ok) continue;
-      const KBox kb = lattice_in_box(P, clo, chi);
+      const KBox kb = lattice_in_box(Q, clo, chi);
       if (kb.n == 0) continue;
-      const Stats sc = box_stats(P, prof, pmax, kb);
+      const Stats sc = box_stats(Q, prof, pmax, kb);
       const double m =
           decision_metric(rule.metric, sc.mean, sc.scatter / static_cast<double>(sc.n), var_prev);
       if (nvalid == 0 || m > best_m) {
@@ -227,14 +242,14 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
         const int side = bhi[a] - blo[a];
         const int grow = (side * rule.frame_num + rule.frame_den - 1) / rule.frame_den;
         Nlo[a] = max(blo[a] - grow, 0);
-        Nhi[a] = min(bhi[a] + grow, P.gn[a]);
+        Nhi[a] = min(bhi[a] + grow, Q.gn[a]);
       } else {
         Nlo[a] = blo[a];
         Nhi[a] = bhi[a];
       }
     }
     // Eq. 6-7 between the regions of consecutive iterations
-    const Stats sb = box_stats(P, prof, pmax, lattice_in_box(P, Nlo, Nhi));
+    const Stats sb = box_stats(Q, prof, pmax, lattice_in_box(Q, Nlo, Nhi));
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
@@ -275,7 +290,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     B_prev = Bi;
     W_prev = Wi;
     iters = i;
-    if (i == P.max_iters) {
+    if (i == Q.max_iters) {
       stop = UWB_STOP_CAP;
       break;
     }
@@ -341,21 +356,32 @@ __global__ void __launch_bounds__(1024) k_plan(const LatBox* boxes, int* prefix,
 __global__ void k_finish(const FinishParams P, const int* status) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P.B) return;
+  FinScan F;
+  if (P.scans) {
+    F = P.scans[s];
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      F.gn[a] = P.gn[a];
+      F.org[a] = P.org[a];
+      F.pit[a] = P.pit[a];
+    }
+    F.Pd = P.Pd;
+  }
   uwb_result* R = P.out + s;
   const LatBox b = P.boxes[s];
   const unsigned long long key = P.keys[s];
   const long long roi = b.tiles > 0 ? static_cast<long long>(b.cnt[0]) * b.cnt[1] * b.cnt[2] : 0;
-  R->points_evaluated = P.Pd + roi;
+  R->points_evaluated = F.Pd + roi;
   if (status && *status != UWB_OK) R->status = *status;
   if (key != 0ull && b.tiles > 0) {
     const long long lin = static_cast<long long>(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
-    const int ix = static_cast<int>(lin % P.gn[0]);
-    const int iy = static_cast<int>((lin / P.gn[0]) % P.gn[1]);
-    const int iz = static_cast<int>(lin / (static_cast<long long>(P.gn[0]) * P.gn[1]));
+    const int ix = static_cast<int>(lin % F.gn[0]);
+    const int iy = static_cast<int>((lin / F.gn[0]) % F.gn[1]);
+    const int iz = static_cast<int>(lin / (static_cast<long long>(F.gn[0]) * F.gn[1]));
     const int idx[3] = {ix, iy, iz};
     for (int a = 0; a < 3; ++a) {
       R->loc_idx[a] = idx[a];
-      R->loc_xyz[a] = P.org[a] + static_cast<double>(idx[a]) * P.pit[a];
+      R->loc_xyz[a] = F.org[a] + static_cast<double>(idx[a]) * F.pit[a];
     }
     R->peak = static_cast<double>(__uint_as_float(static_cast<unsigned int>(key >> 32)));
   } else {

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -245,43 +246,83 @@ void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
 
 // Samples staged per antenna: what the variant's shared-memory budget allows,
 // at most one TMA box width (256), at least the window plus a margin.
-int pick_span(const Variant& var, int M) {
-  const size_t fixed = image_smem_bytes(var.bf, M, var.rows, 0, var.threads, var.R, var.ms);
-  long long span = fixed >= var.smem_budget
-                       ? 0
-                       : static_cast<long long>((var.smem_budget - fixed) / (4 * var.rows));
-  span &= ~3LL;
+int pick_span(const Variant& var, int M, int dtype = DT_F32) {
+  const size_t fixed =
+      image_smem_layout(var.bf, M, var.R, var.rows, 0, var.threads, var.ms, dtype).total + 256;
+  const size_t per = static_cast<size_t>(var.rows) * (4 + (dtype == DT_F32 ? 0 : 2));
+  long long span =
+      fixed >= var.smem_budget ? 0 : static_cast<long long>((var.smem_budget - fixed) / per);
+  span &= ~7LL;  // 16-byte TMA rows for 16-bit traces too
   if (span > 256) span = 256;
-  const long long floor_span = (var.wpad + 8 + 3) & ~3LL;
+  const long long floor_span = (var.wpad + 8 + 7) & ~7LL;
   if (span < floor_span) span = floor_span;
   return static_cast<int>(span);
 }
 
-int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* map) {
+// 3-D tensor map (sample, row, scan) over `scans` scans of `rows` trace rows,
+// boxes of span x rows x 1. Returns 0 when TMA cannot serve the layout.
+int encode_map(const void* traces, int dtype, int N, int pitch, int n_begin, int rows, int scans,
+               int span, CUtensorMap* map) {
   memset(map, 0, sizeof *map);
   if (!g_encode) return 0;
-  if ((reinterpret_cast<uintptr_t>(traces) & 15) || (geo.pitch & 3) || (geo.n_begin & 3) ||
-      geo.N < 1 || geo.R > 256 || span > 256)
+  const int es = dtype_bytes(dtype);
+  const int align = 16 / es;  // elements per 16 bytes
+  if ((reinterpret_cast<uintptr_t>(traces) & 15) || (pitch % align) || (n_begin % align) ||
+      N < 1 || rows > 256 || span > 256 || (span % align))
     return 0;
-  cuuint64_t dims[3] = {static_cast<cuuint64_t>(geo.N), static_cast<cuuint64_t>(geo.R),
-                        static_cast<cuuint64_t>(geo.B)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(geo.pitch) * 4,
-                           static_cast<cuuint64_t>(geo.pitch) * geo.R * 4};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(geo.R), 1};
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(N), static_cast<cuuint64_t>(rows),
+                        static_cast<cuuint64_t>(scans)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(pitch) * es,
+                           static_cast<cuuint64_t>(pitch) * rows * es};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(span), static_cast<cuuint32_t>(rows), 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(traces),
-                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUtensorMapDataType dt = dtype == DT_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : dtype == DT_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  CUresult r = g_encode(map, dt, 3, const_cast<void*>(traces), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 1 : 0;
 }
 
-int occupancy(const Variant& var, size_t smem) {
-  switch (var.bf) {
-    case BF_DAS: return occupancy_image_das(var.v, var.ms, var.threads, smem);
-    case BF_DMAS_ID: return occupancy_image_dmas(var.v, var.ms, var.threads, smem);
-    default: return occupancy_image_literal(var.v, var.threads, smem);
+int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* map) {
+  return encode_map(traces, DT_F32, geo.N, geo.pitch, geo.n_begin, geo.R, geo.B, span, map);
+}
+
+// Resident CTAs per SM of a kernel instance at a shared-memory size; cached
+// per device, so that calls after the first (for example inside a CUDA-graph
+// capture) query nothing and change no attribute.
+struct OccKey {
+  int dev, bf, v, ms, threads;
+  size_t smem;
+  bool operator==(const OccKey& o) const {
+    return dev == o.dev && bf == o.bf && v == o.v && ms == o.ms && threads == o.threads &&
+           smem == o.smem;
   }
+};
+std::mutex g_occ_mu;
+std::vector<std::pair<OccKey, int>> g_occ;
+
+int occupancy(const Variant& var, size_t smem) {
+  int d = 0;
+  cudaGetDevice(&d);
+  const OccKey key{d, var.bf, var.v, var.ms ? 1 : 0, var.threads, smem};
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    for (const auto& kv : g_occ)
+      if (kv.first == key) return kv.second;
+  }
+  int occ;
+  switch (var.bf) {
+    case BF_DAS: occ = occupancy_image_das(var.v, var.ms, var.threads, smem); break;
+    case BF_DMAS_ID: occ = occupancy_image_dmas(var.v, var.ms, var.threads, smem); break;
+    default: occ = occupancy_image_literal(var.v, var.threads, smem); break;
+  }
+  if (occ > 0) {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    g_occ.emplace_back(key, occ);
+  }
+  return occ;
 }
 
 cudaError_t launch(const Variant& var, const ImgParams& p, const CUtensorMap* map, int ctas,
@@ -326,6 +367,9 @@ ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
     p.tdim[a] = var.tdim[a];
   }
   p.gP = geo.P;
+  p.dtype = DT_F32;
+  p.Mcap = geo.M;
+  p.Rcap = geo.R;
   p.span = span;
   p.wpad = var.wpad;
   p.use_tma = use_tma;
@@ -339,7 +383,8 @@ int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const 
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
   if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
   pick_warp(var.tdim, delta, p.wdim);
-  const size_t smem = image_smem_bytes(var.bf, p.M, var.rows, p.span, var.threads, var.R, var.ms);
+  const size_t smem = image_smem_layout(var.bf, p.Mcap, p.Rcap, var.rows, p.span, var.threads,
+                                        var.ms, p.dtype).total;
   const int occ = occupancy(var, smem);
   if (occ < 1) return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
   long long ctas = static_cast<long long>(dev.sms) * occ;
@@ -712,6 +757,110 @@ int host_checks(int batch, const float* traces, int M, int N, const float* ant,
   return UWB_OK;
 }
 
+// ---- ragged batches: plans of per-scan descriptors --------------------------
+
+struct PlanLayout {
+  size_t descs, maps, pboxes, pprefix, fboxes, fprefix, sel, fin;  // written at upload
+  size_t keys, status, profiles, rboxes, rprefix;                   // scratch of a run
+  size_t total;
+};
+
+}  // namespace
+}  // namespace uwb
+
+// The plan of a ragged batch (host object; see uwb_plan_create).
+struct uwb_plan {
+  int B = 0, dtype = 0, W = 0, bf = 0, dim = 0;
+  uwb_rule rule{};
+  uwb::Variant var{};
+  int span = 0;
+  int wdim_full[3] = {32, 1, 1}, wdim_dec[3] = {32, 1, 1};
+  std::vector<uwb::ScanDesc> descs;
+  std::vector<CUtensorMap> maps;
+  std::vector<uwb::LatBox> pboxes, fboxes;
+  std::vector<int> pprefix, fprefix;
+  std::vector<uwb::SelScan> sel;
+  std::vector<uwb::FinScan> fin;
+  std::vector<long long> img_off;
+  long long img_total = 0, prof_total = 0;
+  int any_tma = 0, max_iters_any = 0;
+  uwb::PlanLayout lay{};
+  char* ws = nullptr;  // uploaded workspace
+  size_t ws_bytes = 0;
+};
+
+namespace uwb {
+namespace {
+
+PlanLayout plan_layout(const uwb_plan& pl) {
+  PlanLayout L;
+  const size_t B = pl.B;
+  size_t off = 0;
+  auto take = [&off](size_t bytes, size_t align) {
+    off = align_up(off, align);
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  L.descs = take(B * sizeof(ScanDesc), 256);
+  L.maps = take(B * sizeof(CUtensorMap), 128);
+  L.pboxes = take(B * sizeof(LatBox), 256);
+  L.pprefix = take((B + 1) * 4, 256);
+  L.fboxes = take(B * sizeof(LatBox), 256);
+  L.fprefix = take((B + 1) * 4, 256);
+  L.sel = take(B * sizeof(SelScan), 256);
+  L.fin = take(B * sizeof(FinScan), 256);
+  L.keys = take(B * 8 + 4, 256);  // keys, then the status word
+  L.status = L.keys + B * 8;
+  L.profiles = take(static_cast<size_t>(pl.prof_total) * 4, 256);
+  L.rboxes = take(B * sizeof(LatBox), 256);
+  L.rprefix = take((B + 1) * 4, 256);
+  L.total = align_up(off, 256);
+  return L;
+}
+
+ImgParams plan_params(const uwb_plan& pl, int* status) {
+  ImgParams p;
+  memset(&p, 0, sizeof p);
+  p.B = pl.B;
+  p.W = pl.W;
+  p.h = pl.W / 2;
+  p.span = pl.span;
+  p.wpad = pl.var.wpad;
+  p.dtype = pl.dtype;
+  p.Mcap = pl.var.M;
+  p.Rcap = pl.var.R;
+  for (int a = 0; a < 3; ++a) p.tdim[a] = pl.var.tdim[a];
+  p.descs = reinterpret_cast<const ScanDesc*>(pl.ws + pl.lay.descs);
+  p.tmaps = pl.any_tma ? reinterpret_cast<const CUtensorMap*>(pl.ws + pl.lay.maps) : nullptr;
+  p.status = status;
+  p.uni.tiles = 1;
+  return p;
+}
+
+int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const int wdim[3],
+                cudaStream_t cs) {
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  for (int a = 0; a < 3; ++a) p.wdim[a] = wdim[a];
+  const size_t smem =
+      image_smem_layout(pl.var.bf, p.Mcap, p.Rcap, pl.var.rows, p.span, pl.var.threads, false,
+                        p.dtype)
+          .total;
+  const int occ = occupancy(pl.var, smem);
+  if (occ < 1)
+    return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
+  long long ctas = static_cast<long long>(dev->sms) * occ;
+  if (work_bound < ctas) ctas = work_bound;
+  if (ctas < 1) return UWB_OK;
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof dummy);
+  cudaError_t e = launch(pl.var, p, &dummy, static_cast<int>(ctas), smem, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
+  return UWB_OK;
+}
+
 }  // namespace
 }  // namespace uwb
 
@@ -967,6 +1116,253 @@ int uwb_localize_batch_noalloc(int batch, const float* traces, int M, int N,
   return localize_impl(batch, traces, M, N, antennas, antenna_stride, grid, v, fs, window,
                        beamformer, rule, scratch, UWB_NOALLOC_SCRATCH_BYTES, out, image, stream);
 }
+
+uwb_plan* uwb_plan_create(int batch, const uwb_scan* scans, int dtype, int window,
+                          int beamformer, const uwb_rule* rule, int* status) {
+  auto bad = [status](int code) -> uwb_plan* {
+    if (status) *status = code;
+    return nullptr;
+  };
+  if (batch < 1 || batch > (1 << 22) || !scans)
+    return bad(fail(UWB_ERR_ARG, "a plan needs 1..2^22 scans"));
+  if (dtype != UWB_F32 && dtype != UWB_F16 && dtype != UWB_BF16)
+    return bad(fail(UWB_ERR_ARG, "unknown trace element type %d", dtype));
+  int st = check_rule(rule);
+  if (st) return bad(st);
+  const int bf = bf_of(beamformer);
+  if (bf < 0) return bad(fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer));
+  std::unique_ptr<uwb_plan> pl(new uwb_plan);
+  pl->B = batch;
+  pl->dtype = dtype;
+  pl->W = window;
+  pl->bf = bf;
+  pl->rule = *rule;
+  pl->dim = scans[0].grid.dim;
+  int Mcap = 0;
+  double max_delta = 0.0;
+  std::vector<Geo> geos(batch);
+  for (int b = 0; b < batch; ++b) {
+    const uwb_scan& sc = scans[b];
+    st = check_common(1, static_cast<const float*>(sc.traces), sc.M, sc.N, sc.antennas, &sc.grid,
+                      sc.v, sc.fs, window, &geos[b]);
+    if (st) {
+      char why[sizeof t_err];
+      snprintf(why, sizeof why, "%s", t_err);
+      return bad(fail(st, "scan %d: %s", b, why));
+    }
+    if (sc.grid.dim != pl->dim) return bad(fail(UWB_ERR_ARG, "scan %d: all scans of a plan "
+                                                "share the grid dimensionality", b));
+    Mcap = sc.M > Mcap ? sc.M : Mcap;
+    for (int a = 0; a < sc.grid.dim; ++a)
+      max_delta = std::fmax(max_delta, sc.grid.pitch[a] * geos[b].kscale);
+  }
+  if ((st = pick_variant(bf, Mcap, window, pl->dim, &pl->var))) return bad(st);
+  pl->span = pick_span(pl->var, Mcap, dtype);
+  const double d1[3] = {max_delta, max_delta, pl->dim == 3 ? max_delta : 1e9};
+  pick_warp(pl->var.tdim, d1, pl->wdim_full);
+  pl->descs.resize(batch);
+  pl->maps.resize(batch);
+  pl->pboxes.resize(batch);
+  pl->fboxes.resize(batch);
+  pl->sel.resize(batch);
+  pl->fin.resize(batch);
+  pl->img_off.resize(batch);
+  pl->pprefix.assign(batch + 1, 0);
+  pl->fprefix.assign(batch + 1, 0);
+  double max_dec = 0.0;
+  for (int b = 0; b < batch; ++b) {
+    const uwb_scan& sc = scans[b];
+    const Geo& g = geos[b];
+    const Decim dc = decimate(g.g, *rule);
+    ScanDesc& d = pl->descs[b];
+    memset(&d, 0, sizeof d);
+    d.traces = sc.traces;
+    d.ant = sc.antennas;
+    d.img_off = pl->img_total;
+    d.cmp_off = pl->prof_total;
+    d.pitch = sc.N;
+    d.n_begin = 0;
+    d.N = sc.N;
+    d.M = sc.M;
+    d.R = sc.M;
+    d.kscale = g.kscale;
+    for (int a = 0; a < 3; ++a) {
+      d.org[a] = static_cast<float>(g.g.origin[a]);
+      d.pit[a] = static_cast<float>(g.g.pitch[a]);
+      d.gn[a] = g.g.n[a];
+    }
+    d.tma = encode_map(sc.traces, dtype, sc.N, sc.N, 0, sc.M, 1, pl->span, &pl->maps[b]) ? b : -1;
+    pl->any_tma |= d.tma >= 0;
+    pl->img_off[b] = pl->img_total;
+    pl->img_total += g.P;
+    LatBox& pb = pl->pboxes[b];
+    LatBox& fb = pl->fboxes[b];
+    for (int a = 0; a < 3; ++a) {
+      pb.lo[a] = dc.off[a];
+      pb.step[a] = dc.step[a];
+      pb.cnt[a] = dc.cnt[a];
+      fb.lo[a] = 0;
+      fb.step[a] = 1;
+      fb.cnt[a] = g.g.n[a];
+      max_dec = std::fmax(max_dec, dc.step[a] * g.g.pitch[a] * g.kscale * (a < pl->dim));
+    }
+    pb.tiles = tiles_of(pb.cnt, pl->var.tdim);
+    fb.tiles = tiles_of(fb.cnt, pl->var.tdim);
+    pl->pprefix[b + 1] = pl->pprefix[b] + pb.tiles;
+    pl->fprefix[b + 1] = pl->fprefix[b] + fb.tiles;
+    SelScan& q = pl->sel[b];
+    q.prof_off = pl->prof_total;
+    for (int a = 0; a < 3; ++a) {
+      q.gn[a] = g.g.n[a];
+      q.off[a] = dc.off[a];
+      q.step[a] = dc.step[a];
+      q.cnt[a] = dc.cnt[a];
+    }
+    q.D = dc.D;
+    q.max_iters = dc.max_iters;
+    FinScan& f = pl->fin[b];
+    for (int a = 0; a < 3; ++a) {
+      f.gn[a] = g.g.n[a];
+      f.org[a] = g.g.origin[a];
+      f.pit[a] = g.g.pitch[a];
+    }
+    f.Pd = dc.Pd;
+    pl->prof_total += dc.Pd;
+  }
+  const double d2[3] = {max_dec, max_dec, pl->dim == 3 ? max_dec : 1e9};
+  pick_warp(pl->var.tdim, d2, pl->wdim_dec);
+  pl->lay = plan_layout(*pl);
+  if (status) *status = UWB_OK;
+  return pl.release();
+}
+
+size_t uwb_plan_workspace(const uwb_plan* plan) { return plan ? plan->lay.total : 0; }
+
+long long uwb_plan_image_offset(const uwb_plan* plan, int scan) {
+  if (!plan || scan < 0 || scan > plan->B) return -1;
+  return scan == plan->B ? plan->img_total : plan->img_off[scan];
+}
+
+int uwb_plan_upload(uwb_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+  if (!plan) return fail(UWB_ERR_ARG, "null plan");
+  if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255)
+    return fail(UWB_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < plan->lay.total)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes,
+                plan->lay.total);
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  const size_t B = plan->B;
+  struct {
+    size_t at;
+    const void* src;
+    size_t bytes;
+  } parts[] = {
+      {plan->lay.descs, plan->descs.data(), B * sizeof(ScanDesc)},
+      {plan->lay.maps, plan->maps.data(), B * sizeof(CUtensorMap)},
+      {plan->lay.pboxes, plan->pboxes.data(), B * sizeof(LatBox)},
+      {plan->lay.pprefix, plan->pprefix.data(), (B + 1) * 4},
+      {plan->lay.fboxes, plan->fboxes.data(), B * sizeof(LatBox)},
+      {plan->lay.fprefix, plan->fprefix.data(), (B + 1) * 4},
+      {plan->lay.sel, plan->sel.data(), B * sizeof(SelScan)},
+      {plan->lay.fin, plan->fin.data(), B * sizeof(FinScan)},
+  };
+  for (const auto& part : parts) {
+    cudaError_t e = cudaMemcpyAsync(ws + part.at, part.src, part.bytes, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  }
+  plan->ws = ws;
+  plan->ws_bytes = ws_bytes;
+  return UWB_OK;
+}
+
+int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* stream) {
+  if (!plan || !plan->ws) return fail(UWB_ERR_ARG, "plan not uploaded");
+  if (!images) return fail(UWB_ERR_ARG, "null images");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  int* status = reinterpret_cast<int*>(plan->ws + plan->lay.status);
+  cudaError_t e = cudaMemsetAsync(status, 0, 4, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (peak_index) {
+    e = cudaMemsetAsync(peak_index, 0, sizeof(long long) * plan->B, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  }
+  ImgParams p = plan_params(*plan, status);
+  p.boxes = reinterpret_cast<const LatBox*>(plan->ws + plan->lay.fboxes);
+  p.prefix = reinterpret_cast<const int*>(plan->ws + plan->lay.fprefix);
+  p.image = images;
+  p.keys = reinterpret_cast<unsigned long long*>(peak_index);
+  int st = plan_launch(*plan, p, plan->fprefix[plan->B], plan->wdim_full, cs);
+  if (st) return st;
+  if (peak_index) {
+    e = launch_keys_to_index(p.keys, plan->B, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "argmax decode launch");
+  }
+  return UWB_OK;
+}
+
+int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream) {
+  if (!plan || !plan->ws) return fail(UWB_ERR_ARG, "plan not uploaded");
+  if (!out) return fail(UWB_ERR_ARG, "null result array");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = plan->ws;
+  const PlanLayout& L = plan->lay;
+  const int B = plan->B;
+  int* status = reinterpret_cast<int*>(ws + L.status);
+  auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
+  auto* rboxes = reinterpret_cast<LatBox*>(ws + L.rboxes);
+  auto* rprefix = reinterpret_cast<int*>(ws + L.rprefix);
+  cudaError_t e = cudaMemsetAsync(ws + L.keys, 0, static_cast<size_t>(B) * 8 + 4, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  PhaseTimer timer(cs);
+  timer.mark();
+  // 1. decimated profiles
+  ImgParams p1 = plan_params(*plan, status);
+  p1.boxes = reinterpret_cast<const LatBox*>(ws + L.pboxes);
+  p1.prefix = reinterpret_cast<const int*>(ws + L.pprefix);
+  p1.compact = reinterpret_cast<float*>(ws + L.profiles);
+  int st = plan_launch(*plan, p1, plan->pprefix[B], plan->wdim_dec, cs);
+  if (st) return st;
+  timer.mark();
+  // 2. selection (per-scan lattices) and work planning
+  SelParams sp;
+  memset(&sp, 0, sizeof sp);
+  sp.scans = reinterpret_cast<const SelScan*>(ws + L.sel);
+  sp.profile = reinterpret_cast<const float*>(ws + L.profiles);
+  sp.B = B;
+  sp.dim = plan->dim;
+  for (int a = 0; a < 3; ++a) sp.tdim[a] = plan->var.tdim[a];
+  sp.rule = plan->rule;
+  sp.boxes = rboxes;
+  sp.out = out;
+  if ((e = launch_select(sp, cs)) != cudaSuccess) return cuda_fail(e, "select launch");
+  if ((e = launch_plan(rboxes, rprefix, B, cs)) != cudaSuccess) return cuda_fail(e, "plan launch");
+  timer.mark();
+  // 3. final regions at full resolution + argmax
+  ImgParams p2 = plan_params(*plan, status);
+  p2.boxes = rboxes;
+  p2.prefix = rprefix;
+  p2.keys = keys;
+  if ((st = plan_launch(*plan, p2, plan->fprefix[B], plan->wdim_full, cs))) return st;
+  timer.mark();
+  FinishParams fp;
+  memset(&fp, 0, sizeof fp);
+  fp.scans = reinterpret_cast<const FinScan*>(ws + L.fin);
+  fp.keys = keys;
+  fp.boxes = rboxes;
+  fp.out = out;
+  fp.B = B;
+  if ((e = launch_finish(fp, status, cs)) != cudaSuccess) return cuda_fail(e, "finish launch");
+  timer.mark();
+  timer.commit();
+  return UWB_OK;
+}
+
+void uwb_plan_destroy(uwb_plan* plan) { delete plan; }
 
 int uwb_phase_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);

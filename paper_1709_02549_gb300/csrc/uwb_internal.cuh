@@ -11,6 +11,27 @@ namespace uwb {
 
 enum { BF_DAS = 0, BF_DMAS_ID = 1, BF_DMAS_LIT = 2 };
 
+// Element type of the stored traces (arithmetic is float32 either way).
+enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
+inline __host__ __device__ int dtype_bytes(int dt) { return dt == DT_F32 ? 4 : 2; }
+
+// Everything the image kernel needs to know about one scan. Uniform batches
+// derive it from ImgParams; ragged batches (scans of different antenna
+// counts, trace lengths, grids) pass one per scan.
+struct ScanDesc {
+  const void* traces;   // first stored sample of trace row 0
+  const float* ant;     // [M][3] antenna positions
+  long long img_off;    // element offset of this scan's image in ImgParams::image
+  long long cmp_off;    // element offset of this scan's compact profile
+  int pitch;            // elements between trace rows
+  int n_begin, N;       // stored samples [n_begin, n_begin + N); others read as 0
+  int M, R;             // antennas, trace rows (R = M monostatic)
+  int tma;              // ragged: index into ImgParams::tmaps (-1 = plain staging)
+  float kscale;         // 2 fs / v
+  float org[3], pit[3];
+  int gn[3];
+};
+
 // A box lattice of the focal grid: lattice point k (per axis) is grid index
 // lo + step * k, for 0 <= k < cnt. `tiles` = tiles of the image kernel's tile
 // shape needed to cover it.
@@ -25,9 +46,10 @@ struct LatBox {
 // and the lattice shape (uniform lattice) or each has its own box (per-scan
 // lattices with a tile prefix sum, used for the final regions).
 struct ImgParams {
-  // Sample n of antenna i of scan s is traces[s * trace_stride + i * pitch +
-  // (n - n_begin)] for n_begin <= n < n_begin + N, and 0 outside.
-  const float* traces;
+  // Uniform batches: sample n of antenna i of scan s is traces[s * trace_stride
+  // + i * pitch + (n - n_begin)] for n_begin <= n < n_begin + N, and 0 outside
+  // (elements of type `dtype`).
+  const void* traces;
   long long trace_stride;    // floats between scans
   int pitch;                 // floats between antenna rows
   int n_begin;               // sample index of the first stored sample
@@ -53,24 +75,71 @@ struct ImgParams {
   long long compact_stride;  // floats between scans in `compact`
   unsigned long long* keys;  // [B] argmax keys or nullptr
   int* status;               // device status word
+  int dtype;                 // DT_* of the traces
+  const ScanDesc* descs;     // ragged batches: [B] per-scan descriptors (device), else nullptr
+  const CUtensorMap* tmaps;  // ragged batches: per-scan tensor maps (device), or nullptr
+  int Mcap, Rcap;            // largest M and R of the launch (shared-memory layout)
 };
 
-// Bytes of dynamic shared memory of the image kernel: [rows][span] traces
-// (rows = M, or the antenna register block for literal DMAS), [M] antennas as
-// float4, the literal kernel's [rows][threads] (offset, fraction) pairs, then
-// an mbarrier, 32 reduction keys, 4 ints.
-inline size_t image_smem_bytes(int bf, int M, int rows, int span, int threads, int R = 0,
-                               bool ms = false) {
-  const size_t ant_words = 4 * static_cast<size_t>(M);
-  size_t b = (static_cast<size_t>(rows) * span + ant_words) * 4;
-  if (ms) b += static_cast<size_t>(R) * 8 + static_cast<size_t>(M) * threads * 4;
-  if (bf == BF_DMAS_LIT) b += static_cast<size_t>(rows) * threads * 8;
-  b = (b + 7) & ~static_cast<size_t>(7);
-  return b + 8 + 32 * 8 + 4 * 4;
+// Byte layout of the image kernel's dynamic shared memory:
+//   [rows][span] float32 trace window (rows = R, or the literal kernel's
+//   antenna block), [rows][span] raw 16-bit staging area (FP16/BF16 traces),
+//   [Mcap] antennas (float4), (multistatic) [Rcap] channels, (literal)
+//   [rows][threads] (offset, fraction) pairs, (multistatic) [Mcap][threads]
+//   distances, the scan descriptor, an mbarrier, 32 reduction keys, 4 ints.
+struct SmemLayout {
+  size_t raw, ant, ch, nf, d, desc, bar, key, ints, total;
+};
+
+inline __host__ __device__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline __host__ __device__ SmemLayout image_smem_layout(int bf, int Mcap, int Rcap, int rows,
+                                                        int span, int threads, bool ms,
+                                                        int dtype) {
+  SmemLayout L;
+  size_t off = static_cast<size_t>(rows) * span * 4;
+  off = align_up(off, 128);
+  L.raw = off;
+  if (dtype != DT_F32) off = align_up(off + static_cast<size_t>(rows) * span * 2, 128);
+  L.ant = off;
+  off += static_cast<size_t>(Mcap) * 16;
+  L.ch = off;
+  if (ms) off += static_cast<size_t>(Rcap) * 8;
+  L.nf = off;
+  if (bf == BF_DMAS_LIT) off += static_cast<size_t>(rows) * threads * 8;
+  L.d = off;
+  if (ms) off += static_cast<size_t>(Mcap) * threads * 4;
+  off = align_up(off, 16);
+  L.desc = off;
+  off += align_up(sizeof(ScanDesc), 16);
+  L.bar = off;
+  off += 8;
+  L.key = off;
+  off += 32 * 8;
+  L.ints = off;
+  off += 4 * 4;
+  L.total = off;
+  return L;
 }
+
+// Per-scan decimated lattice and decision inputs (ragged batches).
+struct SelScan {
+  long long prof_off;        // element offset of the scan's profile
+  int gn[3];                 // grid points per axis
+  int off[3], step[3], cnt[3];  // decimated lattice
+  int D, max_iters;
+};
+
+// Per-scan grid for decoding locations (ragged batches).
+struct FinScan {
+  int gn[3];
+  double org[3], pit[3];
+  long long Pd;              // decimated points
+};
 
 // Segment-selection inputs (one warp per scan).
 struct SelParams {
+  const SelScan* scans;      // ragged: [B] (device), else nullptr
   const float* profile;      // [B][Pd] decimated energies, lattice order (x fastest)
   long long prof_stride;
   int B, dim;
@@ -85,6 +154,7 @@ struct SelParams {
 };
 
 struct FinishParams {
+  const FinScan* scans;      // ragged: [B] (device), else nullptr
   const unsigned long long* keys;
   const LatBox* boxes;
   uwb_result* out;

@@ -24,6 +24,16 @@ def uwb():
     return u
 
 
+@pytest.fixture(scope="module")
+def gpu(uwb):
+    """The binding on a CUDA device; the device status word must stay clear."""
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    uwb.uwb_device_status(clear=True)
+    yield uwb
+    assert uwb.uwb_device_status(clear=True) == 0
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
 

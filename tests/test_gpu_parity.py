@@ -15,14 +15,6 @@ pytestmark = pytest.mark.gpu
 BFS = [0, 1, 2]  # UWB_DAS, UWB_DMAS, UWB_DMAS_LITERAL
 
 
-@pytest.fixture(scope="module")
-def gpu(uwb):
-    assert torch.cuda.is_available(), "GPU tests need CUDA"
-    uwb.uwb_device_status(clear=True)
-    yield uwb
-    assert uwb.uwb_device_status(clear=True) == 0
-
-
 def ring(M, radius, z=0.0, seed=0):
     rng = np.random.default_rng(seed)
     ang = np.sort(rng.uniform(0, 2 * np.pi, M))

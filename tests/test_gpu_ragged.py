@@ -1,0 +1,152 @@
+"""Ragged batches through the plan API: scans of different antenna counts,
+trace lengths, grids and media in one set of launches, traces in float32,
+float16 or bfloat16 (needs a GB300)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import phantom
+from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, record_to_dict,
+                    rule_pair)
+
+pytestmark = pytest.mark.gpu
+
+TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+
+
+def ragged_scans(n=5, seed=0):
+    """Scans of one 2-D workload family with different sizes and media."""
+    base = phantom.CONFIGS["das2d_64"]
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        cfg = phantom.with_changes(base, n_antennas=int(rng.choice([8, 13, 16, 24])),
+                                   n_samples=int(rng.choice([768, 1000, 1024, 1536])),
+                                   grid_n=(int(rng.integers(30, 80)), int(rng.integers(30, 80)), 1),
+                                   extent=float(rng.uniform(0.08, 0.11)),
+                                   eps_r=float(rng.uniform(8.0, 10.0)), n_clutter=5)
+        sc = phantom.make_scan(cfg, phantom.BASE_SEED + 900 + k)
+        out.append((cfg, sc))
+    return out
+
+
+def plan_for(gpu, scans, dtype, bf, rule):
+    specs, host = [], []
+    for cfg, sc in scans:
+        t = torch.from_numpy(sc["traces"]).cuda().to(TORCH_DT[dtype]).contiguous()
+        host.append(t.float().cpu().numpy())        # what the kernels actually read
+        specs.append({"traces": t, "antennas": torch.from_numpy(sc["antennas"]).cuda(),
+                      "grid": cfg.grid(), "v": cfg.v, "fs": cfg.fs})
+    plan = gpu.UwbPlan(specs, scans[0][0].window, bf, rule)
+    ws = torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    return plan, host
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("bf", [0, 1, 2])
+def test_ragged_images_match_oracle(gpu, dtype, bf):
+    scans = ragged_scans()
+    g_rule, _ = rule_pair(gpu)
+    plan, host = plan_for(gpu, scans, dtype, bf, g_rule)
+    imgs = torch.full((plan.image_offset(len(scans)),), -1.0, device="cuda")
+    peak = torch.zeros(len(scans), dtype=torch.int64, device="cuda")
+    plan.images(imgs, peak)
+    torch.cuda.synchronize()
+    imgs = imgs.cpu().numpy()
+    for k, (cfg, sc) in enumerate(scans):
+        g = cfg.grid()
+        ref = oracle.image(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, BF_ORACLE[bf])
+        got = imgs[plan.image_offset(k):plan.image_offset(k + 1)].reshape(ref.shape)
+        assert_image_close(got, ref, what=f"scan {k} ({dtype})")
+        flat = ref.ravel()
+        assert abs(flat[int(peak[k])] - flat.max()) <= IMG_TOL * flat.max()
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("bf", [0, 1, 2])
+def test_ragged_localize_matches_oracle(gpu, dtype, bf):
+    scans = ragged_scans(6, seed=1)
+    g_rule, o_rule = rule_pair(gpu)
+    plan, host = plan_for(gpu, scans, dtype, bf, g_rule)
+    out = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(out)
+    torch.cuda.synchronize()
+    res = [record_to_dict(r) for r in gpu.results_from_device(out)]
+    for k, (cfg, sc) in enumerate(scans):
+        g = cfg.grid()
+        o = oracle.localize(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, BF_ORACLE[bf],
+                            o_rule)
+
+        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
+            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, BF_ORACLE[bf], lo=idx,
+                                      cnt=[1, 1, 1])[0, 0, 0])
+        compare_localize(res[k], o, energy_at)
+    plan.close()
+
+
+def test_ragged_plan_of_equal_scans_equals_the_uniform_batch(gpu):
+    cfg = phantom.CONFIGS["dmas2d_512"]
+    batch = phantom.make_batch(cfg, 3)
+    g_rule, _ = rule_pair(gpu)
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    specs = [{"traces": traces[k], "antennas": ants, "grid": cfg.grid(), "v": cfg.v,
+              "fs": cfg.fs} for k in range(3)]
+    plan = gpu.UwbPlan(specs, cfg.window, 2, g_rule)
+    plan.upload(torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda"))
+    a = torch.empty(3 * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(a)
+    b = torch.empty_like(a)
+    ws = torch.empty(gpu.uwb_localize_workspace(3, cfg.n_antennas, cfg.n_samples, cfg.grid(), 2,
+                                                g_rule), dtype=torch.uint8, device="cuda")
+    gpu.uwb_localize_batch(traces, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, 2, g_rule, ws, b)
+    torch.cuda.synchronize()
+    ra = [record_to_dict(r) for r in gpu.results_from_device(a)]
+    rb = [record_to_dict(r) for r in gpu.results_from_device(b)]
+    for x, y in zip(ra, rb):
+        for key in ("iters", "roi_lo", "roi_hi", "loc_idx", "child", "points_evaluated", "peak"):
+            assert x[key] == y[key], key
+    plan.close()
+
+
+def test_ragged_localisation_replays_in_a_cuda_graph(gpu):
+    scans = ragged_scans(4, seed=2)
+    g_rule, _ = rule_pair(gpu)
+    plan, _ = plan_for(gpu, scans, "f16", 1, g_rule)
+    direct = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(direct)
+    torch.cuda.synchronize()
+    graphed = torch.zeros_like(direct)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        plan.localize(graphed, stream=s)
+    for _ in range(2):
+        graphed.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(graphed, direct)
+    plan.close()
+
+
+def test_half_precision_traces_stay_close_to_float32(gpu):
+    # the error that 16-bit trace storage adds to each image, against the
+    # float64 oracle on the float32 traces
+    scans = ragged_scans(3, seed=3)
+    g_rule, _ = rule_pair(gpu)
+    for dtype, bound in (("f16", 5e-3), ("bf16", 5e-2)):
+        plan, _ = plan_for(gpu, scans, dtype, 0, g_rule)
+        imgs = torch.empty(plan.image_offset(len(scans)), device="cuda")
+        plan.images(imgs)
+        torch.cuda.synchronize()
+        imgs = imgs.cpu().numpy()
+        for k, (cfg, sc) in enumerate(scans):
+            ref = oracle.image(sc["traces"], sc["antennas"], cfg.grid(), cfg.v, cfg.fs,
+                               cfg.window, oracle.DAS)
+            got = imgs[plan.image_offset(k):plan.image_offset(k + 1)].reshape(ref.shape)
+            rel = float(np.max(np.abs(got - ref)) / ref.max())
+            assert rel < bound, (dtype, k, rel)
+        plan.close()
