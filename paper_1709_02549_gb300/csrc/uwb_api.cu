@@ -204,7 +204,8 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     var.wpad = (W + 1) / 2 * 2;  // window samples go in pairs
     var.threads = 128;
     var.rows = var.v;
-    var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
+    // 4 CTAs per SM up to 32 antennas (the last 1.5 KB keeps a 184-sample span)
+    var.smem_budget = var.v <= 32 ? 57 * 1024 + 512 : 112 * 1024;
     if (dim == 2) {
       var.tdim[0] = 16; var.tdim[1] = 8; var.tdim[2] = 1;
     } else {
