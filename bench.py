@@ -263,6 +263,94 @@ def run_presence(args, cfg, bf, uwb, torch):
             "confirmed_rate": rates, "gpu_launches": 11 * args.steps}
 
 
+def run_ragged(args, uwb, torch):
+    """Uneven scans (16-96 antennas, 1024-4096 samples, 128^2-1024^2 grids) in one
+    plan per element type: localised scans/s after tile autotuning, full-resolution
+    images of the same scans, and each image's error against the FP64 oracle at
+    sampled focal points (traces stored in float32, float16, bfloat16)."""
+    import oracle
+    oracle.build()
+    B = args.batch
+    bf = BEAMFORMERS[args.beamformer] if args.beamformer != "literal" else 1
+    cfgs = phantom.ragged_configs(B)
+    scans = [phantom.make_scan(c, phantom.BASE_SEED + 200000 + k) for k, c in enumerate(cfgs)]
+    dev_tr = [torch.from_numpy(sc["traces"]).cuda() for sc in scans]
+    dev_an = [torch.from_numpy(sc["antennas"]).cuda() for sc in scans]
+    rule = uwb.uwb_default_rule()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(0)
+    out = {"metric": "localised scans/s, ragged batches (plan API)", "unit": "scans/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "data": "synthetic", "beamformer": args.beamformer if bf else "das",
+           "config": {"workload": f"{B} uneven scans: 16-96 antennas, 1024-4096 samples, "
+                                  "128^2-1024^2 grids over 12 cm, 50 clutter, 15 dB",
+                      "points_total": int(sum(np.prod(c.grid_n) for c in cfgs))},
+           "by_dtype": {}}
+    for name, tdt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+        specs = [{"traces": t.to(tdt).contiguous(), "antennas": a, "grid": c.grid(), "v": c.v,
+                  "fs": c.fs} for t, a, c in zip(dev_tr, dev_an, cfgs)]
+        plan = uwb.UwbPlan(specs, cfgs[0].window, bf, rule)
+        ws = torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda")
+        res = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        tile, _ = plan.autotune(ws, res)
+        plan.close()
+        plan = uwb.UwbPlan(specs, cfgs[0].window, bf, rule)
+        plan.upload(ws)
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            return tot / args.steps
+
+        loc_ms = timed(lambda: plan.localize(res))
+        imgs = torch.empty(plan.image_offset(B), device="cuda")
+        peak = torch.empty(B, dtype=torch.int64, device="cuda")
+        img_ms = timed(lambda: plan.images(imgs, peak))
+        recs = uwb.results_from_device(res)
+        pk = peak.cpu().numpy()
+        agree = float(np.mean([list(recs["loc_idx"][k][:2]) ==
+                               [int(pk[k] % cfgs[k].grid_n[0]), int(pk[k] // cfgs[k].grid_n[0])]
+                               for k in range(B)]))
+        # error per image against the FP64 oracle on the float32 traces, at 64
+        # sampled focal points and the argmax of each of the first 8 scans
+        errs = []
+        im = imgs.cpu().numpy()
+        for k in range(min(8, B)):
+            c, sc = cfgs[k], scans[k]
+            g = c.grid()
+            gx, gy = c.grid_n[0], c.grid_n[1]
+            pts = rng.integers(0, [gx, gy], size=(64, 2)).tolist() + [[int(pk[k] % gx),
+                                                                       int(pk[k] // gx)]]
+            got = np.array([im[plan.image_offset(k) + x + gx * y] for x, y in pts])
+            ref = np.array([oracle.image(sc["traces"], sc["antennas"], g, c.v, c.fs, c.window,
+                                         oracle.DAS if bf == 0 else oracle.DMAS, lo=[x, y, 0],
+                                         cnt=[1, 1, 1])[0, 0, 0] for x, y in pts])
+            errs.append(float(np.max(np.abs(got - ref)) / max(ref.max(), 1e-300)))
+        out["by_dtype"][name] = {
+            "value": B / (loc_ms / 1e3), "ms_per_step": loc_ms, "tile": tile,
+            "fullres": {"value": B / (img_ms / 1e3), "ms_per_step": img_ms},
+            "speedup_vs_fullres": img_ms / loc_ms, "loc_agreement": agree,
+            "max_image_error_vs_fp64_oracle": errs,
+            "status_ok": bool((recs["status"] == 0).all()),
+        }
+        plan.close()
+    out["value"] = out["by_dtype"]["f32"]["value"]
+    uwb.uwb_set_tile_shape(bf, 2, None)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,8 +364,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-scans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="localize", choices=["localize", "presence"],
-                    help="presence: time the two-decimation tumour-presence test instead")
+    ap.add_argument("--mode", default="localize", choices=["localize", "presence", "ragged"],
+                    help="presence: the two-decimation tumour-presence test; ragged: a batch "
+                         "of uneven scans through the plan API")
     ap.add_argument("--decimation2", type=int, default=0,
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()
@@ -303,6 +392,9 @@ def main():
     B = args.batch
     if args.mode == "presence":
         print(json.dumps(run_presence(args, cfg, bf, uwb, torch)), flush=True)
+        return
+    if args.mode == "ragged":
+        print(json.dumps(run_ragged(args, uwb, torch)), flush=True)
         return
     batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
     grid = cfg.grid()

@@ -204,6 +204,22 @@ int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* 
 int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream);
 void uwb_plan_destroy(uwb_plan* plan);
 
+/* Tile shapes of the image kernel (focal points per CTA along x, y, z; powers
+ * of two multiplying to 256, or 128 for UWB_DMAS_LITERAL; z = 1 for 2-D).
+ * uwb_autotune runs the given batch through uwb_plan_localize once per
+ * candidate shape (timed with CUDA events after a warm-up run), keeps the
+ * fastest for this beamformer and dimensionality in a process-wide table
+ * that later plans and uniform calls use, and reports it (tile_out, ms_out:
+ * host, optional). It synchronises the stream: call it before any stream
+ * capture. workspace: at least uwb_plan_workspace of a plan of the batch.
+ * uwb_set_tile_shape sets the table entry (tile NULL restores the default);
+ * uwb_tile_shape reads the shape currently in use. */
+int uwb_autotune(int batch, const uwb_scan* scans, int dtype, int window, int beamformer,
+                 const uwb_rule* rule, void* workspace, size_t ws_bytes, uwb_result* out,
+                 int tile_out[3], float* ms_out, void* stream);
+int uwb_set_tile_shape(int beamformer, int dim, const int tile[3]);
+int uwb_tile_shape(int beamformer, int dim, int tile[3]);
+
 /* Multistatic images (Section II.A: Eq. 2 delays; Eq. 4 DAS, DMAS over pairs
  * of channels): channel c is the echo sent by antenna channels[2c] and
  * received by antenna channels[2c+1] (int32 [C][2], device), its trace is

@@ -22,6 +22,7 @@ __all__ = [
     "uwb_localize_host_workspace", "uwb_localize_host", "uwb_presence_workspace",
     "uwb_presence_batch", "uwb_image_multistatic_batch", "uwb_localize_multistatic_workspace",
     "uwb_localize_multistatic_batch", "UwbScan", "UwbPlan", "UWB_F32", "UWB_F16", "UWB_BF16",
+    "uwb_set_tile_shape", "uwb_tile_shape",
     "UwbError",
 ]
 
@@ -128,6 +129,11 @@ def lib() -> ctypes.CDLL:
             "uwb_plan_images": (i, [vp, vp, vp, vp]),
             "uwb_plan_localize": (i, [vp, vp, vp]),
             "uwb_plan_destroy": (None, [vp]),
+            "uwb_autotune": (i, [i, ctypes.POINTER(UwbScan), i, i, i, rp, vp, sz, vp,
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                  vp]),
+            "uwb_set_tile_shape": (i, [i, i, ctypes.POINTER(ctypes.c_int)]),
+            "uwb_tile_shape": (i, [i, i, ctypes.POINTER(ctypes.c_int)]),
             "uwb_device_status": (i, [i]),
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
@@ -398,6 +404,7 @@ class UwbPlan:
             arr[k] = UwbScan(t.data_ptr(), a.data_ptr(), int(t.shape[0]), int(t.shape[1]),
                              make_grid(sc["grid"]), float(sc["v"]), float(sc["fs"]))
         st = ctypes.c_int(0)
+        self._arr, self._window, self._bf, self._rule = arr, int(window), int(beamformer), rule
         self.handle = lib().uwb_plan_create(self.B, arr, self.dtype, int(window), int(beamformer),
                                             ctypes.byref(rule), ctypes.byref(st))
         if not self.handle:
@@ -424,6 +431,17 @@ class UwbPlan:
     def localize(self, out, stream=None):
         _check(lib().uwb_plan_localize(self.handle, _ptr(out, "out"), _stream(stream)),
                "uwb_plan_localize")
+
+    def autotune(self, workspace, out, stream=None):
+        """Times the candidate tile shapes on this batch (uwb_autotune); returns
+        (tile, ms). Later plans of the same beamformer/dimensionality use it."""
+        tile = (ctypes.c_int * 3)()
+        ms = ctypes.c_float(0)
+        _check(lib().uwb_autotune(self.B, self._arr, self.dtype, self._window, self._bf,
+                                  ctypes.byref(self._rule), _ptr(workspace, "workspace"),
+                                  workspace.numel() * workspace.element_size(), _ptr(out, "out"),
+                                  tile, ctypes.byref(ms), _stream(stream)), "uwb_autotune")
+        return list(tile), ms.value
 
     def close(self):
         if getattr(self, "handle", None):
@@ -464,6 +482,17 @@ def uwb_phase_times():
     ms = (ctypes.c_double * 4)()
     calls = _check(lib().uwb_phase_times(ms), "uwb_phase_times")
     return calls, list(ms)
+
+
+def uwb_set_tile_shape(beamformer, dim, tile=None) -> None:
+    arr = None if tile is None else (ctypes.c_int * 3)(*tile)
+    _check(lib().uwb_set_tile_shape(int(beamformer), int(dim), arr), "uwb_set_tile_shape")
+
+
+def uwb_tile_shape(beamformer, dim):
+    t = (ctypes.c_int * 3)()
+    _check(lib().uwb_tile_shape(int(beamformer), int(dim), t), "uwb_tile_shape")
+    return list(t)
 
 
 def uwb_device_status(clear: bool = False) -> int:

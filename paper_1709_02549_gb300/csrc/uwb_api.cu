@@ -190,6 +190,18 @@ struct Variant {
   int M, R;           // antennas, trace rows per scan
 };
 
+// Tile shapes chosen by uwb_autotune / uwb_set_tile_shape, per beamformer and
+// dimensionality (0 = the built-in default).
+std::mutex g_tile_mu;
+int g_tile[3][4][3] = {};
+
+bool tile_ok(int bf, const int t[3]) {
+  const int threads = bf == BF_DMAS_LIT ? 128 : 256;
+  for (int a = 0; a < 3; ++a)
+    if (t[a] < 1 || (t[a] & (t[a] - 1))) return false;  // powers of two
+  return t[0] * t[1] * t[2] == threads;
+}
+
 int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   Variant var;
   var.bf = bf;
@@ -223,6 +235,12 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     } else {
       var.tdim[0] = 16; var.tdim[1] = 4; var.tdim[2] = 4;
     }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    const int* t = g_tile[bf][dim];
+    if (t[0] && (dim == 3 || t[2] == 1))
+      for (int a = 0; a < 3; ++a) var.tdim[a] = t[a];
   }
   *out = var;
   return UWB_OK;
@@ -1364,6 +1382,90 @@ int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream) {
 }
 
 void uwb_plan_destroy(uwb_plan* plan) { delete plan; }
+
+int uwb_tile_shape(int beamformer, int dim, int tile[3]) {
+  const int bf = bf_of(beamformer);
+  if (bf < 0 || (dim != 2 && dim != 3) || !tile) return fail(UWB_ERR_ARG, "bad tile query");
+  Variant v;
+  int st = pick_variant(bf, 16, 20, dim, &v);
+  if (st) return st;
+  for (int a = 0; a < 3; ++a) tile[a] = v.tdim[a];
+  return UWB_OK;
+}
+
+int uwb_set_tile_shape(int beamformer, int dim, const int tile[3]) {
+  const int bf = bf_of(beamformer);
+  if (bf < 0 || (dim != 2 && dim != 3)) return fail(UWB_ERR_ARG, "bad beamformer or dim");
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  if (!tile) {
+    for (int a = 0; a < 3; ++a) g_tile[bf][dim][a] = 0;
+    return UWB_OK;
+  }
+  if (!tile_ok(bf, tile) || (dim == 2 && tile[2] != 1))
+    return fail(UWB_ERR_ARG, "tile must be powers of two multiplying to the CTA size");
+  for (int a = 0; a < 3; ++a) g_tile[bf][dim][a] = tile[a];
+  return UWB_OK;
+}
+
+int uwb_autotune(int batch, const uwb_scan* scans, int dtype, int window, int beamformer,
+                 const uwb_rule* rule, void* workspace, size_t ws_bytes, uwb_result* out,
+                 int tile_out[3], float* ms_out, void* stream) {
+  const int bf = bf_of(beamformer);
+  if (bf < 0 || !scans || batch < 1) return fail(UWB_ERR_ARG, "bad autotune arguments");
+  const int dim = scans[0].grid.dim;
+  if (dim != 2 && dim != 3) return fail(UWB_ERR_ARG, "grid dim must be 2 or 3");
+  static const int c256_2[][3] = {{32, 8, 1}, {16, 16, 1}, {64, 4, 1}, {8, 32, 1}};
+  static const int c128_2[][3] = {{16, 8, 1}, {32, 4, 1}, {8, 16, 1}, {64, 2, 1}};
+  static const int c256_3[][3] = {{16, 4, 4}, {8, 8, 4}, {32, 4, 2}, {8, 4, 8}};
+  static const int c128_3[][3] = {{8, 4, 4}, {16, 4, 2}, {4, 8, 4}, {8, 8, 2}};
+  const int(*cand)[3] = bf == BF_DMAS_LIT ? (dim == 2 ? c128_2 : c128_3)
+                                          : (dim == 2 ? c256_2 : c256_3);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(UWB_ERR_CUDA, "cudaEventCreate");
+  float best_ms = 1e30f;
+  int best = -1, st = UWB_OK;
+  int saved[3];
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (int a = 0; a < 3; ++a) saved[a] = g_tile[bf][dim][a];
+  }
+  for (int c = 0; c < 4 && st == UWB_OK; ++c) {
+    st = uwb_set_tile_shape(beamformer, dim, cand[c]);
+    if (st) break;
+    uwb_plan* plan = uwb_plan_create(batch, scans, dtype, window, beamformer, rule, &st);
+    if (!plan) break;
+    if ((st = uwb_plan_upload(plan, workspace, ws_bytes, stream)) == UWB_OK &&
+        (st = uwb_plan_localize(plan, out, stream)) == UWB_OK) {  // warm-up
+      cudaEventRecord(e0, cs);
+      st = uwb_plan_localize(plan, out, stream);
+      cudaEventRecord(e1, cs);
+      if (st == UWB_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = c;
+        }
+      }
+    }
+    uwb_plan_destroy(plan);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  if (st != UWB_OK || best < 0) {
+    for (int a = 0; a < 3; ++a) g_tile[bf][dim][a] = saved[a];
+    return st ? st : fail(UWB_ERR_CUDA, "autotune timed nothing");
+  }
+  for (int a = 0; a < 3; ++a) {
+    g_tile[bf][dim][a] = cand[best][a];
+    if (tile_out) tile_out[a] = cand[best][a];
+  }
+  if (ms_out) *ms_out = best_ms;
+  return UWB_OK;
+}
 
 int uwb_phase_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);

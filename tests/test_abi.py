@@ -90,3 +90,15 @@ def test_bad_rule_and_workspace_are_rejected(uwb):
     # literal pairs are built for up to 64 antennas
     assert L.uwb_dmas_image(fake, 65, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 1, fake, None,
                             None) == -5
+
+
+def test_tile_shape_table(uwb):
+    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [32, 8, 1]
+    assert uwb.uwb_tile_shape(uwb.UWB_DMAS_LITERAL, 3) == [8, 4, 4]
+    uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, [16, 16, 1])
+    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [16, 16, 1]
+    uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, None)
+    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [32, 8, 1]
+    for bad in ([16, 8, 1], [24, 8, 1], [16, 4, 4]):   # wrong size, not a power of 2, z in 2-D
+        with pytest.raises(uwb.UwbError):
+            uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, bad)

@@ -150,3 +150,31 @@ def test_half_precision_traces_stay_close_to_float32(gpu):
             rel = float(np.max(np.abs(got - ref)) / ref.max())
             assert rel < bound, (dtype, k, rel)
         plan.close()
+
+
+def test_autotune_picks_a_valid_tile_and_keeps_the_results(gpu):
+    scans = ragged_scans(4, seed=5)
+    g_rule, _ = rule_pair(gpu)
+    plan, _ = plan_for(gpu, scans, "f32", 1, g_rule)
+    out0 = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(out0)
+    ws = torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda")
+    out1 = torch.empty_like(out0)
+    try:
+        tile, ms = plan.autotune(ws, out1)
+        assert tile in ([32, 8, 1], [16, 16, 1], [64, 4, 1], [8, 32, 1]) and ms > 0
+        assert gpu.uwb_tile_shape(1, 2) == tile
+        plan2, _ = plan_for(gpu, scans, "f32", 1, g_rule)
+        out2 = torch.empty_like(out0)
+        plan2.localize(out2)
+        torch.cuda.synchronize()
+        # focal points are computed the same way whatever the tile: same results
+        a = [record_to_dict(r) for r in gpu.results_from_device(out0)]
+        b = [record_to_dict(r) for r in gpu.results_from_device(out2)]
+        for x, y in zip(a, b):
+            for key in ("loc_idx", "roi_lo", "roi_hi", "peak", "child"):
+                assert x[key] == y[key], key
+        plan2.close()
+    finally:
+        gpu.uwb_set_tile_shape(1, 2, None)
+        plan.close()
