@@ -217,7 +217,9 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     var.threads = 128;
     var.rows = var.v;
     // 4 CTAs per SM up to 32 antennas (the last 1.5 KB keeps a 184-sample span)
-    var.smem_budget = var.v <= 32 ? 57 * 1024 + 512 : 112 * 1024;
+    // 4 CTAs (2 for the 64-antenna block) per SM, each with the 1 KB the
+    // runtime reserves per CTA, fill the SM's 228 KB
+    var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
     if (dim == 2) {
       var.tdim[0] = 16; var.tdim[1] = 8; var.tdim[2] = 1;
     } else {
@@ -266,16 +268,14 @@ void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
 // Samples staged per antenna: what the variant's shared-memory budget allows,
 // at most one TMA box width (256), at least the window plus a margin.
 int pick_span(const Variant& var, int M, int dtype = DT_F32) {
-  const size_t fixed =
-      image_smem_layout(var.bf, M, var.R, var.rows, 0, var.threads, var.ms, dtype).total + 256;
-  const size_t per = static_cast<size_t>(var.rows) * (4 + (dtype == DT_F32 ? 0 : 2));
-  long long span =
-      fixed >= var.smem_budget ? 0 : static_cast<long long>((var.smem_budget - fixed) / per);
-  span &= ~7LL;  // 16-byte TMA rows for 16-bit traces too
-  if (span > 256) span = 256;
-  const long long floor_span = (var.wpad + 8 + 7) & ~7LL;
-  if (span < floor_span) span = floor_span;
-  return static_cast<int>(span);
+  // the largest span (a multiple of 8: 16-byte TMA rows for 16-bit traces too)
+  // whose whole layout fits the budget
+  int span = 256;
+  while (span > 8 && image_smem_layout(var.bf, M, var.R, var.rows, span, var.threads, var.ms,
+                                       dtype).total > var.smem_budget)
+    span -= 8;
+  const int floor_span = (var.wpad + 8 + 7) & ~7;
+  return span < floor_span ? floor_span : span;
 }
 
 // 3-D tensor map (sample, row, scan) over `scans` scans of `rows` trace rows,
