@@ -79,6 +79,7 @@ extern "C" {
 #define UWB_STOP_MINSIZE 2    /* no child segment was large enough to choose */
 #define UWB_STOP_CAP 3        /* iteration cap reached */
 #define UWB_STOP_NO_TARGET 4  /* every decimated energy is zero */
+#define UWB_STOP_LEARNED 5    /* the learned proposal chose the final region */
 
 #define UWB_MAX_ITERS 32
 
@@ -360,6 +361,116 @@ int uwb_device_status(int clear);
 
 /* Text of the last error of the calling thread ("" if none). */
 const char* uwb_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Learned segment proposal. The paper has no counterpart: a small network
+ * proposes the segments that Section III's ROI selection would otherwise pick
+ * with the Eq. 5 metric, and Eq. 5 decides instead whenever the network is
+ * not confident.
+ *
+ * Network: a 32 x 32 coarse DAS energy map (Eq. 1 + Eq. 3) of a square region
+ * E is normalised, X0 = E / max E; three 3x3 zero-padded convolutions with 32
+ * channels, bias and ReLU (1 -> 32 -> 32 -> 32 channels); the mean of the last
+ * map over each of the 16 segments (4 x 4 squares of 8 x 8 map points,
+ * s = 4 * row + column, row along grid axis 1); a shared linear head gives 16
+ * segment scores z; confidence = the largest softmax probability of z.
+ * Convolution weights are BF16 and feature maps are stored in BF16; every sum
+ * accumulates in FP32 (the 32 -> 32 layers on the tensor cores).
+ *
+ * Parameters theta: UWB_CNN_PARAMS float32 values in the order
+ *   W1[32][9], b1[32], W2[32][9][32], b2[32], W3[32][9][32], b3[32], wh[32], bh[1]
+ * with W[c_out][tap][c_in] and tap = 3 (dy + 1) + (dx + 1), dy along grid axis
+ * 1, dx along axis 0. The kernels read a packed copy (UWB_CNN_PACKED_BYTES,
+ * 256-byte aligned device memory) made by uwb_cnn_pack or refreshed by
+ * uwb_cnn_adam.
+ *
+ * The first call of uwb_cnn_forward, uwb_cnn_gradients, uwb_cnn_train_step
+ * or uwb_localize_learned on a device runs a synchronous tensor-core
+ * self-check (make it before any stream capture); if it fails, those calls
+ * return UWB_ERR_UNSUPPORTED. All device pointers are caller-owned; the calls
+ * are asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+#define UWB_CNN_PARAMS 18849
+#define UWB_CNN_PACKED_BYTES 38912
+
+/* Runs (once per device) the tensor-core self-check: an exact integer-valued
+ * BF16 GEMM through the descriptor and TMEM conventions the network uses.
+ * *passed = 1 if the device reproduced it exactly. Returns UWB_OK or an error. */
+int uwb_cnn_selftest(int* passed);
+
+/* packed <- the kernels' copy of theta (device float[UWB_CNN_PARAMS]). */
+int uwb_cnn_pack(const float* theta, void* packed, void* stream);
+
+/* scores[b][16] <- segment scores of maps[b][32][32] (raw energies, row-major
+ * [y][x]), b < batch. Non-finite map values set UWB_ERR_NONFINITE in the
+ * device status word and read as 0. */
+int uwb_cnn_forward(const void* packed, const float* maps, int batch, float* scores,
+                    void* stream);
+
+/* Workspace of uwb_cnn_train_step (a per-map record of the forward pass plus
+ * one gradient vector); uwb_cnn_gradients needs batch * 242688 bytes. 0 for a
+ * batch outside [1, 2^20]. */
+size_t uwb_cnn_train_workspace(int batch);
+
+/* Gradient of the mean cross-entropy of softmax(z) against labels[b] in
+ * [0, 16) over the batch: grad (device float[UWB_CNN_PARAMS]) and loss (one
+ * device float) are overwritten. The backward pass follows the chain rule of
+ * the network with the gradient at each pre-activation rounded to BF16 before
+ * it meets the weights (BF16 operands, FP32 sums, on the CUDA cores). The
+ * workspace holds a per-map record of the forward pass; the backward pass
+ * consumes it. workspace: 256-byte aligned device memory. */
+int uwb_cnn_gradients(const void* packed, const float* maps, const int* labels, int batch,
+                      float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream);
+
+/* Adam step `step` (from 1; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
+ * of theta with learning rate lr; m and v are its moment vectors (zero before
+ * the first step). grad is consumed (zeroed) and packed refreshed. */
+int uwb_cnn_adam(float* theta, float* m, float* v, float* grad, void* packed, int step, float lr,
+                 void* stream);
+
+/* uwb_cnn_gradients followed by uwb_cnn_adam, the gradient kept in the
+ * workspace (uwb_cnn_train_workspace(batch) bytes). */
+int uwb_cnn_train_step(float* theta, float* m, float* v, void* packed, const float* maps,
+                       const int* labels, int batch, int step, float lr, float* loss,
+                       void* workspace, size_t ws_bytes, void* stream);
+
+/* Coarse DAS maps (Eq. 1 + Eq. 3 energies) of a square region per scan:
+ * maps[b][ky][kx] at grid point (lo_x + o + step * kx, lo_y + o + step * ky),
+ * step = side / 32, o = (step - 1) / 2. region_lo: device int[batch][2]
+ * (x, y) per scan, or NULL for the region at (0, 0). Trace, antenna and grid
+ * arguments as in uwb_localize_batch (2-D grids; side a multiple of 32 within
+ * the grid). A region outside the grid sets UWB_ERR_ARG in the status word
+ * and leaves its map at 0. workspace: uwb_coarse_maps_workspace(batch) bytes,
+ * needed only with region_lo. */
+size_t uwb_coarse_maps_workspace(int batch);
+int uwb_coarse_maps(int batch, const float* traces, int M, int N, const float* antennas,
+                    long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                    int window, const int* region_lo, int side, float* maps, void* workspace,
+                    size_t ws_bytes, void* stream);
+
+/* Localisation with the learned proposal, all on the device. For each of
+ * `levels` levels (1..3) the scan's current square region (first the whole
+ * grid) gets a coarse DAS map, the network scores its 16 segments, and the
+ * scan descends into the best segment when the confidence is >= threshold.
+ * After the last level the segment, framed by ceil(frame_num / frame_den *
+ * side) points per side and clipped to the grid (Section III, sliding
+ * framing), is imaged at full resolution with `beamformer` and its argmax
+ * (lowest linear index on ties) is the location; stop_reason =
+ * UWB_STOP_LEARNED, child[l] / metric_top[l] / box_lo[l] / box_hi[l] log the
+ * segment, confidence and region of level l. A level below the threshold
+ * hands the scan to the Eq. 5 framework of uwb_localize_batch (decimated
+ * profile, ROI selection, final region) with the given rule. The grid must be
+ * square and 2-D with a side divisible by 32 * 4^(levels - 1).
+ * points_evaluated counts coarse-map, profile (fallback only) and final-region
+ * points. workspace: uwb_localize_learned_workspace bytes, 256-byte aligned.
+ * Phase timing records: 0 = proposal, 1 = fallback profile and selection,
+ * 2 = final-region imaging, 3 = result decoding. */
+size_t uwb_localize_learned_workspace(int batch, const uwb_grid* grid, const uwb_rule* rule);
+int uwb_localize_learned(int batch, const float* traces, int M, int N, const float* antennas,
+                         long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                         int window, int beamformer, const uwb_rule* rule, const void* packed,
+                         float threshold, int levels, void* workspace, size_t ws_bytes,
+                         uwb_result* results, void* stream);
 
 #ifdef __cplusplus
 }

@@ -138,6 +138,19 @@ def lib() -> ctypes.CDLL:
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
             "uwb_last_error": (ctypes.c_char_p, []),
+            "uwb_cnn_selftest": (i, [ctypes.POINTER(ctypes.c_int)]),
+            "uwb_cnn_pack": (i, [vp, vp, vp]),
+            "uwb_cnn_forward": (i, [vp, vp, i, vp, vp]),
+            "uwb_cnn_train_workspace": (sz, [i]),
+            "uwb_cnn_gradients": (i, [vp, vp, vp, i, vp, vp, vp, sz, vp]),
+            "uwb_cnn_adam": (i, [vp, vp, vp, vp, vp, i, ctypes.c_float, vp]),
+            "uwb_cnn_train_step": (i, [vp, vp, vp, vp, vp, vp, i, i, ctypes.c_float, vp, vp, sz,
+                                       vp]),
+            "uwb_coarse_maps_workspace": (sz, [i]),
+            "uwb_coarse_maps": (i, [i, vp, i, i, vp, ll, gp, d, d, i, vp, i, vp, vp, sz, vp]),
+            "uwb_localize_learned_workspace": (sz, [i, gp, rp]),
+            "uwb_localize_learned": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp,
+                                         ctypes.c_float, i, vp, sz, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -503,3 +516,102 @@ def results_from_device(out) -> np.ndarray:
     """Copies a device uwb_result array (uint8 tensor) to a numpy record array."""
     host = out.detach().to("cpu").numpy()
     return host.view(RESULT_DTYPE)
+
+
+# ---------------------------------------------------------------- learned proposal
+CNN_PARAMS = 18849
+CNN_PACKED_BYTES = 38912
+UWB_STOP_LEARNED = 5
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def uwb_cnn_selftest() -> bool:
+    """Runs the tensor-core self-check on the current device (once)."""
+    ok = ctypes.c_int(0)
+    _check(lib().uwb_cnn_selftest(ctypes.byref(ok)), "uwb_cnn_selftest")
+    return bool(ok.value)
+
+
+def uwb_cnn_pack(theta, packed, stream=None):
+    """theta: CUDA float32 [CNN_PARAMS]; packed: CUDA uint8 [CNN_PACKED_BYTES]."""
+    _check(lib().uwb_cnn_pack(_f32(theta, "theta"), _ptr(packed, "packed"), _stream(stream)),
+           "uwb_cnn_pack")
+
+
+def uwb_cnn_forward(packed, maps, scores, stream=None):
+    """maps: CUDA float32 [B, 32, 32]; scores: CUDA float32 [B, 16]."""
+    _check(lib().uwb_cnn_forward(_ptr(packed, "packed"), _f32(maps, "maps"), maps.shape[0],
+                                 _f32(scores, "scores"), _stream(stream)), "uwb_cnn_forward")
+
+
+def uwb_cnn_train_workspace(batch) -> int:
+    n = lib().uwb_cnn_train_workspace(int(batch))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_cnn_train_workspace")
+    return n
+
+
+def uwb_cnn_gradients(packed, maps, labels, grad, loss, workspace, stream=None):
+    """labels: CUDA int32 [B]; grad: CUDA float32 [CNN_PARAMS]; loss: CUDA float32 [1]."""
+    _check(lib().uwb_cnn_gradients(_ptr(packed, "packed"), _f32(maps, "maps"),
+                                   _i32(labels, "labels"), maps.shape[0], _f32(grad, "grad"),
+                                   _f32(loss, "loss"), _ptr(workspace, "workspace"),
+                                   _nbytes(workspace), _stream(stream)), "uwb_cnn_gradients")
+
+
+def uwb_cnn_adam(theta, m, v, grad, packed, step, lr, stream=None):
+    _check(lib().uwb_cnn_adam(_f32(theta, "theta"), _f32(m, "m"), _f32(v, "v"),
+                              _f32(grad, "grad"), _ptr(packed, "packed"), int(step), float(lr),
+                              _stream(stream)), "uwb_cnn_adam")
+
+
+def uwb_cnn_train_step(theta, m, v, packed, maps, labels, step, lr, loss, workspace, stream=None):
+    _check(lib().uwb_cnn_train_step(_f32(theta, "theta"), _f32(m, "m"), _f32(v, "v"),
+                                    _ptr(packed, "packed"), _f32(maps, "maps"),
+                                    _i32(labels, "labels"), maps.shape[0], int(step), float(lr),
+                                    _f32(loss, "loss"), _ptr(workspace, "workspace"),
+                                    _nbytes(workspace), _stream(stream)), "uwb_cnn_train_step")
+
+
+def uwb_coarse_maps_workspace(batch) -> int:
+    return lib().uwb_coarse_maps_workspace(int(batch))
+
+
+def uwb_coarse_maps(traces, antennas, grid, v, fs, window, side, maps, region_lo=None,
+                    workspace=None, stream=None):
+    """traces [B, M, N]; antennas [M, 3] or [B, M, 3]; maps CUDA float32 [B, 32, 32];
+    region_lo: CUDA int32 [B, 2] (x, y) or None (the region at the origin)."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_coarse_maps(B, _f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                                 stride, ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                 int(window), None if region_lo is None else
+                                 _i32(region_lo, "region_lo"), int(side), _f32(maps, "maps"),
+                                 _ptr(workspace, "workspace", True),
+                                 0 if workspace is None else _nbytes(workspace),
+                                 _stream(stream)), "uwb_coarse_maps")
+
+
+def uwb_localize_learned_workspace(batch, grid, rule: UwbRule) -> int:
+    n = lib().uwb_localize_learned_workspace(int(batch), ctypes.byref(make_grid(grid)),
+                                             ctypes.byref(rule))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_localize_learned_workspace")
+    return n
+
+
+def uwb_localize_learned(traces, antennas, grid, v, fs, window, beamformer, rule: UwbRule, packed,
+                         threshold, levels, workspace, out, stream=None):
+    """traces [B, M, N]; antennas [M, 3] or [B, M, 3]; out uint8 [B * RESULT_BYTES]."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_localize_learned(B, _f32(traces, "traces"), M, N, _f32(antennas, "antennas"),
+                                      stride, ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                      int(window), int(beamformer), ctypes.byref(rule),
+                                      _ptr(packed, "packed"), float(threshold), int(levels),
+                                      _ptr(workspace, "workspace"), _nbytes(workspace),
+                                      _ptr(out, "out"), _stream(stream)), "uwb_localize_learned")
+

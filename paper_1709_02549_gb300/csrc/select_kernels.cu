@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   const int lane = threadIdx.x & 31;
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (s >= P.B) return;
+  if (P.skip && P.skip[s]) return;
   // this scan's lattice and grid
   SelScan Q;
   if (P.scans) {
@@ -372,6 +373,8 @@ __global__ void k_finish(const FinishParams P, const int* status) {
   const unsigned long long key = P.keys[s];
   const long long roi = b.tiles > 0 ? static_cast<long long>(b.cnt[0]) * b.cnt[1] * b.cnt[2] : 0;
   R->points_evaluated = F.Pd + roi;
+  if (P.learn)  // learned localisation: coarse maps, plus the profile where Eq. 5 decided
+    R->points_evaluated = (P.learn[s].fallback ? F.Pd : 0) + P.learn[s].map_points + roi;
   if (status && *status != UWB_OK) R->status = *status;
   if (key != 0ull && b.tiles > 0) {
     const long long lin = static_cast<long long>(0xFFFFFFFFull - (key & 0xFFFFFFFFull));

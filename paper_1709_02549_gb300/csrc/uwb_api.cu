@@ -1518,3 +1518,531 @@ int uwb_device_status(int clear) {
 const char* uwb_last_error(void) { return t_err; }
 
 }  // extern "C"
+
+// ---------------------------------------------------- learned segment proposal
+namespace {
+
+// The tensor-core self-check, once per device: an integer-valued BF16 GEMM
+// through the network's descriptor, TMEM and epilogue conventions, compared
+// exactly on the host. The network's kernels only run where it passed.
+std::mutex g_umma_mu;
+int g_umma_state[64] = {};  // 0 unknown, 1 passed, -1 failed
+
+uint16_t bf16_bits_of_small_int(int v) {
+  const float f = static_cast<float>(v);
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return static_cast<uint16_t>(u >> 16);  // exact for small integers
+}
+
+int umma_selftest_run(int* passed) {
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  int d = 0;
+  cudaError_t e = cudaGetDevice(&d);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_umma_mu);
+  if (g_umma_state[d] != 0) {
+    *passed = g_umma_state[d] > 0;
+    return UWB_OK;
+  }
+  std::vector<uint16_t> A(128 * 64), B(32 * 64);
+  std::vector<int> Ai(128 * 64), Bi(32 * 64);
+  for (int m = 0; m < 128; ++m)
+    for (int k = 0; k < 64; ++k) {
+      Ai[m * 64 + k] = (m * 7 + k * 3) % 9 - 4;
+      A[m * 64 + k] = bf16_bits_of_small_int(Ai[m * 64 + k]);
+    }
+  for (int n = 0; n < 32; ++n)
+    for (int k = 0; k < 64; ++k) {
+      Bi[n * 64 + k] = (n * 5 + k * 11 + 1) % 9 - 4;
+      B[n * 64 + k] = bf16_bits_of_small_int(Bi[n * 64 + k]);
+    }
+  void *dA = nullptr, *dB = nullptr, *dD = nullptr, *dS = nullptr;
+  std::vector<float> D(128 * 32, 0.f);
+  int sw = 0;
+  cudaStream_t cs = nullptr;
+  auto cleanup = [&]() {
+    if (cs) cudaStreamDestroy(cs);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(dS);
+  };
+  if ((e = cudaMalloc(&dA, A.size() * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&dB, B.size() * 2)) != cudaSuccess ||
+      (e = cudaMalloc(&dD, D.size() * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&dS, 4)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dA, A.data(), A.size() * 2, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dB, B.data(), B.size() * 2, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+      (e = cudaMemsetAsync(dD, 0, D.size() * 4, cs)) != cudaSuccess ||
+      (e = cudaMemsetAsync(dS, 0, 4, cs)) != cudaSuccess ||
+      (e = cnn::launch_selftest(static_cast<uint16_t*>(dA), static_cast<uint16_t*>(dB),
+                                static_cast<float*>(dD), static_cast<int*>(dS), cs)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(D.data(), dD, D.size() * 4, cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&sw, dS, 4, cudaMemcpyDeviceToHost, cs)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(cs)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "tensor-core self-check");
+  }
+  cleanup();
+  bool ok = sw == UWB_OK;
+  for (int m = 0; m < 128 && ok; ++m)
+    for (int n = 0; n < 32 && ok; ++n) {
+      int ref = 0;
+      for (int k = 0; k < 64; ++k) ref += Ai[m * 64 + k] * Bi[n * 64 + k];
+      ok = D[m * 32 + n] == static_cast<float>(ref);
+    }
+  g_umma_state[d] = ok ? 1 : -1;
+  *passed = ok;
+  return UWB_OK;
+}
+
+int umma_ready() {
+  int passed = 0;
+  int st = umma_selftest_run(&passed);
+  if (st) return st;
+  if (!passed)
+    return fail(UWB_ERR_UNSUPPORTED,
+                "tensor-core self-check failed on this device: the network's kernels are disabled");
+  return UWB_OK;
+}
+
+int cnn_ctas(const Device& dev, int batch) { return batch < dev.sms ? batch : dev.sms; }
+
+size_t train_layout_grad(int batch) { return align256(static_cast<size_t>(batch) * cnn::SAVE_BYTES); }
+
+int check_cnn_batch(int batch) {
+  if (batch < 1 || batch > (1 << 20)) return fail(UWB_ERR_ARG, "batch %d out of range", batch);
+  return UWB_OK;
+}
+
+int cnn_gradients_impl(const void* packed, const float* maps, const int* labels, int batch,
+                       float* grad, float* loss, void* ws, size_t ws_bytes, cudaStream_t cs) {
+  int st;
+  if ((st = check_cnn_batch(batch))) return st;
+  if (!packed || !maps || !labels || !grad || !loss) return fail(UWB_ERR_ARG, "null argument");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(UWB_ERR_WORKSPACE, "workspace must be non-null and 256-byte aligned");
+  if (ws_bytes < static_cast<size_t>(batch) * cnn::SAVE_BYTES)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes,
+                static_cast<size_t>(batch) * cnn::SAVE_BYTES);
+  if ((st = umma_ready())) return st;
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(grad, 0, cnn::N_PARAMS * 4, cs)) != cudaSuccess ||
+      (e = cudaMemsetAsync(loss, 0, 4, cs)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync");
+  const int ctas = cnn_ctas(*dev, batch);
+  if ((e = cnn::launch_forward(packed, maps, batch, nullptr, labels, ws, loss, dev->status, ctas,
+                               cs)) != cudaSuccess)
+    return cuda_fail(e, "network forward launch");
+  if ((e = cnn::launch_backward(packed, ws, batch, grad, ctas, cs)) != cudaSuccess)
+    return cuda_fail(e, "network backward launch");
+  return UWB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int uwb_cnn_selftest(int* passed) {
+  if (!passed) return fail(UWB_ERR_ARG, "null passed");
+  return umma_selftest_run(passed);
+}
+
+int uwb_cnn_pack(const float* theta, void* packed, void* stream) {
+  if (!theta || !packed) return fail(UWB_ERR_ARG, "null theta or packed");
+  cudaError_t e = cnn::launch_pack(theta, packed, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "pack launch");
+}
+
+int uwb_cnn_forward(const void* packed, const float* maps, int batch, float* scores,
+                    void* stream) {
+  int st;
+  if ((st = check_cnn_batch(batch))) return st;
+  if (!packed || !maps || !scores) return fail(UWB_ERR_ARG, "null argument");
+  if ((st = umma_ready())) return st;
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaError_t e = cnn::launch_forward(packed, maps, batch, scores, nullptr, nullptr, nullptr,
+                                      dev->status, cnn_ctas(*dev, batch),
+                                      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "network forward launch");
+}
+
+size_t uwb_cnn_train_workspace(int batch) {
+  if (batch < 1 || batch > (1 << 20)) return 0;
+  return train_layout_grad(batch) + align256(cnn::N_PARAMS * 4);
+}
+
+int uwb_cnn_gradients(const void* packed, const float* maps, const int* labels, int batch,
+                      float* grad, float* loss, void* workspace, size_t ws_bytes, void* stream) {
+  return cnn_gradients_impl(packed, maps, labels, batch, grad, loss, workspace, ws_bytes,
+                            static_cast<cudaStream_t>(stream));
+}
+
+int uwb_cnn_adam(float* theta, float* m, float* v, float* grad, void* packed, int step, float lr,
+                 void* stream) {
+  if (!theta || !m || !v || !grad || !packed) return fail(UWB_ERR_ARG, "null argument");
+  if (step < 1) return fail(UWB_ERR_ARG, "Adam step counts from 1 (got %d)", step);
+  if (!(lr > 0.f)) return fail(UWB_ERR_ARG, "learning rate must be positive");
+  const double b1 = 0.9, b2 = 0.999;
+  cnn::AdamConsts k;
+  k.lr = lr;
+  k.beta1 = static_cast<float>(b1);
+  k.beta2 = static_cast<float>(b2);
+  k.one_minus_beta1 = static_cast<float>(1.0 - b1);
+  k.one_minus_beta2 = static_cast<float>(1.0 - b2);
+  k.eps = 1e-8f;
+  k.c1 = static_cast<float>(1.0 / (1.0 - std::pow(b1, step)));
+  k.c2 = static_cast<float>(1.0 / (1.0 - std::pow(b2, step)));
+  cudaError_t e = cnn::launch_adam(theta, m, v, grad, packed, k, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "Adam launch");
+}
+
+int uwb_cnn_train_step(float* theta, float* m, float* v, void* packed, const float* maps,
+                       const int* labels, int batch, int step, float lr, float* loss,
+                       void* workspace, size_t ws_bytes, void* stream) {
+  const size_t need = uwb_cnn_train_workspace(batch);
+  if (need == 0) return fail(UWB_ERR_ARG, "batch %d out of range", batch);
+  if (ws_bytes < need)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, need);
+  if (!workspace) return fail(UWB_ERR_WORKSPACE, "null workspace");
+  float* grad = reinterpret_cast<float*>(static_cast<char*>(workspace) + train_layout_grad(batch));
+  int st = cnn_gradients_impl(packed, maps, labels, batch, grad, loss, workspace,
+                              train_layout_grad(batch), static_cast<cudaStream_t>(stream));
+  if (st) return st;
+  return uwb_cnn_adam(theta, m, v, grad, packed, step, lr, stream);
+}
+
+}  // extern "C"
+
+// ---- coarse DAS maps and the learned localisation
+namespace {
+
+struct LearnLayout {
+  size_t keys, status, maps, scores, state, map_boxes, final_boxes, prof_boxes, learned, prefix,
+      profile, total;
+};
+
+LearnLayout learn_layout(int B, long long Pd) {
+  LearnLayout w;
+  size_t off = 0;
+  w.keys = off;
+  off += static_cast<size_t>(B) * 8;
+  w.status = off;
+  off = align256(off + 4);
+  w.maps = off;
+  off += align256(static_cast<size_t>(B) * cnn::MAP * cnn::MAP * 4);
+  w.scores = off;
+  off += align256(static_cast<size_t>(B) * cnn::SEGS * 4);
+  w.state = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LearnState));
+  w.map_boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.final_boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.prof_boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.learned = off;
+  off += align256(static_cast<size_t>(B) * 4);
+  w.prefix = off;
+  off += align256(static_cast<size_t>(B + 1) * 4);
+  w.profile = off;
+  off += align256(static_cast<size_t>(B) * static_cast<size_t>(Pd) * 4);
+  w.total = off;
+  return w;
+}
+
+// Square 2-D grid whose side splits into `levels` levels of 4 x 4 segments
+// with a 32-point coarse map at every level.
+int check_learn_grid(const uwb_grid* g, int levels) {
+  if (levels < 1 || levels > 3) return fail(UWB_ERR_ARG, "levels %d not in [1, 3]", levels);
+  if (g->dim != 2 || g->n[0] != g->n[1] || g->n[2] != 1)
+    return fail(UWB_ERR_UNSUPPORTED, "the learned proposal needs a square 2-D grid");
+  int need = cnn::MAP;
+  for (int l = 1; l < levels; ++l) need *= cnn::SEG;
+  if (g->n[0] % need != 0)
+    return fail(UWB_ERR_UNSUPPORTED, "grid side %d is not a multiple of %d for %d level(s)",
+                g->n[0], need, levels);
+  return UWB_OK;
+}
+
+// One pass of the DAS image kernel over a 32 x 32 lattice per scan, written
+// compactly to maps[B][32][32]: the uniform lattice `uni`, or per-scan boxes.
+int run_map_pass(const Device& dev, const Geo& geo, const float* traces, const float* ant,
+                 long long ant_stride, const Variant& vm, int span, int use_tma,
+                 const CUtensorMap* map, const LatBox* uni, const LatBox* boxes,
+                 const int* prefix, float* maps, int* status, int step, cudaStream_t cs) {
+  ImgParams p = base_params(geo, traces, ant, ant_stride, vm, span, use_tma, status);
+  if (uni) {
+    p.uni = *uni;
+  } else {
+    p.boxes = boxes;
+    p.prefix = prefix;
+    p.uni.tiles = 1;
+  }
+  p.compact = maps;
+  p.compact_stride = cnn::MAP * cnn::MAP;
+  const double dstep[3] = {static_cast<double>(step), static_cast<double>(step), 1.0};
+  int cnt[3] = {cnn::MAP, cnn::MAP, 1};
+  return run_image_kernel(dev, vm, p, map, static_cast<long long>(geo.B) * tiles_of(cnt, vm.tdim),
+                          dstep, cs);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t uwb_coarse_maps_workspace(int batch) {
+  if (batch < 1 || batch > (1 << 24)) return 0;
+  return align256(static_cast<size_t>(batch) * sizeof(LatBox)) +
+         align256(static_cast<size_t>(batch + 1) * 4);
+}
+
+int uwb_coarse_maps(int batch, const float* traces, int M, int N, const float* antennas,
+                    long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                    int window, const int* region_lo, int side, float* maps, void* workspace,
+                    size_t ws_bytes, void* stream) {
+  Geo geo;
+  int st = check_common(batch, traces, M, N, antennas, grid, v, fs, window, &geo);
+  if (st) return st;
+  if (!maps) return fail(UWB_ERR_ARG, "null maps");
+  if (antenna_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  if (grid->dim != 2 || grid->n[2] != 1) return fail(UWB_ERR_UNSUPPORTED, "coarse maps need a 2-D grid");
+  if (side < cnn::MAP || side % cnn::MAP != 0 || side > grid->n[0] || side > grid->n[1])
+    return fail(UWB_ERR_ARG, "side %d must be a multiple of %d within the grid", side, cnn::MAP);
+  if (region_lo) {
+    const size_t need = uwb_coarse_maps_workspace(batch);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || ws_bytes < need)
+      return fail(UWB_ERR_WORKSPACE, "per-scan regions need %zu bytes of 256-byte aligned workspace",
+                  need);
+  }
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  Variant vm;
+  if ((st = pick_variant(BF_DAS, M, window, 2, &vm))) return st;
+  const int span = pick_span(vm, M);
+  CUtensorMap map;
+  const int use_tma = encode_traces(geo, traces, span, &map);
+  cudaError_t e = cudaMemsetAsync(maps, 0, static_cast<size_t>(batch) * cnn::MAP * cnn::MAP * 4, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const int step = side / cnn::MAP, o = (step - 1) / 2;
+  if (!region_lo) {
+    LatBox uni;
+    const int lo[3] = {o, o, 0}, stp[3] = {step, step, 1}, cnt[3] = {cnn::MAP, cnn::MAP, 1};
+    for (int a = 0; a < 3; ++a) {
+      uni.lo[a] = lo[a];
+      uni.step[a] = stp[a];
+      uni.cnt[a] = cnt[a];
+    }
+    uni.tiles = tiles_of(uni.cnt, vm.tdim);
+    return run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span, use_tma, &map, &uni,
+                        nullptr, nullptr, maps, dev->status, step, cs);
+  }
+  auto* boxes = static_cast<LatBox*>(workspace);
+  auto* prefix = reinterpret_cast<int*>(static_cast<char*>(workspace) +
+                                        align256(static_cast<size_t>(batch) * sizeof(LatBox)));
+  if ((e = cnn::launch_region_boxes(region_lo, side, grid->n[0], batch, vm.tdim, boxes, dev->status,
+                                    cs)) != cudaSuccess)
+    return cuda_fail(e, "region boxes launch");
+  if ((e = launch_plan(boxes, prefix, batch, cs)) != cudaSuccess) return cuda_fail(e, "plan launch");
+  return run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span, use_tma, &map, nullptr,
+                      boxes, prefix, maps, dev->status, step, cs);
+}
+
+size_t uwb_localize_learned_workspace(int batch, const uwb_grid* grid, const uwb_rule* rule) {
+  if (batch < 1 || batch > (1 << 24) || !grid || !rule || check_rule(rule)) return 0;
+  if (grid->dim != 2) return 0;
+  return learn_layout(batch, decimate(*grid, *rule).Pd).total;
+}
+
+int uwb_localize_learned(int batch, const float* traces, int M, int N, const float* antennas,
+                         long long antenna_stride, const uwb_grid* grid, double v, double fs,
+                         int window, int beamformer, const uwb_rule* rule, const void* packed,
+                         float threshold, int levels, void* workspace, size_t ws_bytes,
+                         uwb_result* out, void* stream) {
+  Geo geo;
+  int st = check_common(batch, traces, M, N, antennas, grid, v, fs, window, &geo);
+  if (st) return st;
+  if ((st = check_rule(rule))) return st;
+  if ((st = check_learn_grid(grid, levels))) return st;
+  if (!out || !packed) return fail(UWB_ERR_ARG, "null results or parameters");
+  if (antenna_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  if (!(threshold >= 0.f && threshold <= 1.f)) return fail(UWB_ERR_ARG, "threshold not in [0, 1]");
+  const int bf = bf_of(beamformer);
+  if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  const Decim dc = decimate(geo.g, *rule);
+  const LearnLayout L = learn_layout(batch, dc.Pd);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(UWB_ERR_WORKSPACE, "workspace must be non-null and 256-byte aligned");
+  if (ws_bytes < L.total)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  if ((st = umma_ready())) return st;
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  Variant vm, var;
+  if ((st = pick_variant(BF_DAS, M, window, 2, &vm))) return st;
+  if ((st = pick_variant(bf, M, window, 2, &var))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
+  auto* status = reinterpret_cast<int*>(ws + L.status);
+  auto* maps = reinterpret_cast<float*>(ws + L.maps);
+  auto* scores = reinterpret_cast<float*>(ws + L.scores);
+  auto* state = reinterpret_cast<LearnState*>(ws + L.state);
+  auto* map_boxes = reinterpret_cast<LatBox*>(ws + L.map_boxes);
+  auto* final_boxes = reinterpret_cast<LatBox*>(ws + L.final_boxes);
+  auto* prof_boxes = reinterpret_cast<LatBox*>(ws + L.prof_boxes);
+  auto* learned = reinterpret_cast<int*>(ws + L.learned);
+  auto* prefix = reinterpret_cast<int*>(ws + L.prefix);
+  auto* profile = reinterpret_cast<float*>(ws + L.profile);
+  cudaError_t e = cudaMemsetAsync(ws + L.keys, 0, L.status + 4 - L.keys, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+
+  const int span_m = pick_span(vm, M), span = pick_span(var, M);
+  CUtensorMap map_m, map_f;
+  const int tma_m = encode_traces(geo, traces, span_m, &map_m);
+  const int tma_f = encode_traces(geo, traces, span, &map_f);
+  const int ctas = cnn_ctas(*dev, batch);
+  PhaseTimer timer(cs);
+  timer.mark();
+
+  cnn::LearnParams lp;
+  memset(&lp, 0, sizeof lp);
+  lp.B = batch;
+  lp.n = grid->n[0];
+  lp.levels = levels;
+  lp.threshold = threshold;
+  lp.frame_num = rule->frame_num;
+  lp.frame_den = rule->frame_den;
+  lp.scores = scores;
+  lp.state = state;
+  lp.out = out;
+  lp.map_boxes = map_boxes;
+  lp.final_boxes = final_boxes;
+  lp.prof_boxes = prof_boxes;
+  lp.learned = learned;
+  for (int a = 0; a < 3; ++a) {
+    lp.doff[a] = dc.off[a];
+    lp.dstep[a] = dc.step[a];
+    lp.dcnt[a] = dc.cnt[a];
+    lp.tdim_map[a] = vm.tdim[a];
+    lp.tdim_final[a] = var.tdim[a];
+  }
+
+  // 1. the proposal, level by level: coarse DAS map, network, decision
+  int side = grid->n[0];
+  for (int level = 0; level < levels; ++level) {
+    const int step = side / cnn::MAP;
+    if (level == 0) {
+      LatBox uni;
+      const int o = (step - 1) / 2;
+      for (int a = 0; a < 2; ++a) {
+        uni.lo[a] = o;
+        uni.step[a] = step;
+        uni.cnt[a] = cnn::MAP;
+      }
+      uni.lo[2] = 0;
+      uni.step[2] = 1;
+      uni.cnt[2] = 1;
+      uni.tiles = tiles_of(uni.cnt, vm.tdim);
+      st = run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span_m, tma_m, &map_m,
+                        &uni, nullptr, nullptr, maps, status, step, cs);
+    } else {
+      if ((e = launch_plan(map_boxes, prefix, batch, cs)) != cudaSuccess)
+        return cuda_fail(e, "plan launch");
+      st = run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span_m, tma_m, &map_m,
+                        nullptr, map_boxes, prefix, maps, status, step, cs);
+    }
+    if (st) return st;
+    if ((e = cnn::launch_forward(packed, maps, batch, scores, nullptr, nullptr, nullptr, status,
+                                 ctas, cs)) != cudaSuccess)
+      return cuda_fail(e, "network forward launch");
+    if ((e = cnn::launch_decide(lp, level, cs)) != cudaSuccess) return cuda_fail(e, "decide launch");
+    side /= cnn::SEG;
+  }
+  timer.mark();
+
+  // 2. where the network was not confident: the decimated profile and the
+  // Eq. 5 selection (Section III) for those scans only
+  if ((e = launch_plan(prof_boxes, prefix, batch, cs)) != cudaSuccess)
+    return cuda_fail(e, "plan launch");
+  {
+    ImgParams p1 = base_params(geo, traces, antennas, antenna_stride, var, span, tma_f, status);
+    p1.boxes = prof_boxes;
+    p1.prefix = prefix;
+    p1.uni.tiles = 1;
+    p1.compact = profile;
+    p1.compact_stride = dc.Pd;
+    const double dstep[3] = {static_cast<double>(dc.step[0]), static_cast<double>(dc.step[1]),
+                             static_cast<double>(dc.step[2])};
+    const int pc[3] = {dc.cnt[0], dc.cnt[1], dc.cnt[2]};
+    if ((st = run_image_kernel(*dev, var, p1, &map_f,
+                               static_cast<long long>(batch) * tiles_of(pc, var.tdim), dstep, cs)))
+      return st;
+  }
+  SelParams sp;
+  memset(&sp, 0, sizeof sp);
+  sp.profile = profile;
+  sp.prof_stride = dc.Pd;
+  sp.B = batch;
+  sp.dim = 2;
+  for (int a = 0; a < 3; ++a) {
+    sp.gn[a] = geo.g.n[a];
+    sp.off[a] = dc.off[a];
+    sp.step[a] = dc.step[a];
+    sp.cnt[a] = dc.cnt[a];
+    sp.tdim[a] = var.tdim[a];
+  }
+  sp.D = dc.D;
+  sp.rule = *rule;
+  sp.max_iters = dc.max_iters;
+  sp.skip = learned;
+  sp.boxes = final_boxes;
+  sp.out = out;
+  if ((e = launch_select(sp, cs)) != cudaSuccess) return cuda_fail(e, "select launch");
+  if ((e = launch_plan(final_boxes, prefix, batch, cs)) != cudaSuccess)
+    return cuda_fail(e, "plan launch");
+  timer.mark();
+
+  // 3. final region of every scan at full resolution + argmax
+  {
+    ImgParams p2 = base_params(geo, traces, antennas, antenna_stride, var, span, tma_f, status);
+    p2.boxes = final_boxes;
+    p2.prefix = prefix;
+    p2.uni.tiles = 1;
+    p2.keys = keys;
+    int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
+    const double step1[3] = {1, 1, 1};
+    if ((st = run_image_kernel(*dev, var, p2, &map_f,
+                               static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                               cs)))
+      return st;
+  }
+  timer.mark();
+  FinishParams fp;
+  memset(&fp, 0, sizeof fp);
+  fp.learn = state;
+  fp.keys = keys;
+  fp.boxes = final_boxes;
+  fp.out = out;
+  fp.B = batch;
+  for (int a = 0; a < 3; ++a) {
+    fp.gn[a] = geo.g.n[a];
+    fp.org[a] = geo.g.origin[a];
+    fp.pit[a] = geo.g.pitch[a];
+  }
+  fp.Pd = dc.Pd;
+  if ((e = launch_finish(fp, status, cs)) != cudaSuccess) return cuda_fail(e, "finish launch");
+  timer.mark();
+  timer.commit();
+  return UWB_OK;
+}
+
+}  // extern "C"

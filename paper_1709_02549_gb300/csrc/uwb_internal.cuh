@@ -149,11 +149,21 @@ struct SelParams {
   uwb_rule rule;
   int max_iters;
   int tdim[3];               // tile shape of the final-region image kernel
+  const int* skip;           // per scan: nonzero = decided elsewhere, leave alone (or nullptr)
   LatBox* boxes;             // out: final region per scan
   uwb_result* out;           // out: results
 };
 
+// Per-scan state of the learned proposal across its levels.
+struct LearnState {
+  int lo[2];                 // current square region [lo, lo + side) per axis (x, y)
+  int side;
+  int fallback;              // 1: the Eq. 5 framework decides this scan
+  int map_points;            // coarse-map points evaluated so far
+};
+
 struct FinishParams {
+  const LearnState* learn;   // learned localisation: per-scan state, else nullptr
   const FinScan* scans;      // ragged: [B] (device), else nullptr
   const unsigned long long* keys;
   const LatBox* boxes;
@@ -186,5 +196,71 @@ cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t
 cudaError_t launch_keys_to_index(unsigned long long* keys, int B, cudaStream_t st);
 cudaError_t launch_presence(const uwb_result* a, const uwb_result* b, int* present, int B,
                             cudaStream_t st);
+
+// ------------------------------------------------------ learned proposal
+namespace cnn {
+constexpr int MAP = 32;              // coarse map side
+constexpr int CH = 32;               // channels
+constexpr int TAPS = 9;              // 3 x 3
+constexpr int SEG = 4;               // segments per axis
+constexpr int SEGS = SEG * SEG;
+constexpr int N_PARAMS = 18849;
+// parameter vector offsets (floats): W1[32][9], b1, W2[32][9][32], b2, W3, b3, wh, bh
+constexpr int TH_W1 = 0, TH_B1 = TH_W1 + CH * TAPS, TH_W2 = TH_B1 + CH;
+constexpr int TH_B2 = TH_W2 + CH * TAPS * CH, TH_W3 = TH_B2 + CH;
+constexpr int TH_B3 = TH_W3 + CH * TAPS * CH, TH_WH = TH_B3 + CH, TH_BH = TH_WH + CH;
+static_assert(TH_BH + 1 == N_PARAMS, "parameter count");
+// packed parameters (bytes): BF16 W1, W2, W3; FP32 b1, b2, b3, wh, bh
+constexpr int PK_W1 = 0, PK_W2 = 1024, PK_W3 = PK_W2 + CH * TAPS * CH * 2;
+constexpr int PK_F32 = PK_W3 + CH * TAPS * CH * 2, PK_BYTES = 38912;
+static_assert(PK_F32 + (4 * CH + 1) * 4 <= PK_BYTES, "packed size");
+// activation maps in shared memory: padded rows of Q positions, PAD0 zero
+// positions first, U positions per 8-channel group of LBO_ACT bytes
+constexpr int Q = MAP + 1, PAD0 = Q + 1, NPOS = MAP * Q, TILES = (NPOS + 127) / 128;
+constexpr int U = 1224, LBO_ACT = U * 16 + 32, ACT_BYTES = 4 * LBO_ACT;
+// per-map training record (bytes): X0 (float, U), A1, A2, A3 (padded BF16
+// maps), segment means F[16][32], dz[16]
+constexpr int SAVE_X0 = 0, SAVE_A1 = 5120, SAVE_A2 = SAVE_A1 + ACT_BYTES;
+constexpr int SAVE_A3 = SAVE_A2 + ACT_BYTES, SAVE_F = SAVE_A3 + ACT_BYTES;
+constexpr int SAVE_DZ = SAVE_F + SEGS * CH * 4, SAVE_BYTES = 242688;
+static_assert(SAVE_DZ + SEGS * 4 <= SAVE_BYTES && U * 4 <= SAVE_A1, "training record");
+
+struct LearnParams {
+  int B, n, levels;
+  float threshold;
+  int frame_num, frame_den;
+  const float* scores;       // [B][16]
+  LearnState* state;         // [B]
+  uwb_result* out;           // [B]
+  LatBox* map_boxes;         // next level's coarse-map lattice (cnt 0: none)
+  LatBox* final_boxes;       // final region of confident scans
+  LatBox* prof_boxes;        // decimated lattice of fallback scans (cnt 0: none)
+  int* learned;              // 1: the network decided the scan
+  int doff[3], dstep[3], dcnt[3];  // the rule's decimated lattice
+  int tdim_map[3], tdim_final[3];  // tile shapes of the map and final passes
+};
+
+size_t forward_smem();
+size_t backward_smem();
+size_t selftest_smem();
+cudaError_t launch_selftest(const uint16_t* a, const uint16_t* b, float* d, int* status,
+                            cudaStream_t st);
+cudaError_t launch_forward(const void* packed, const float* maps, int B, float* scores,
+                           const int* labels, void* save, float* loss, int* status, int ctas,
+                           cudaStream_t st);
+cudaError_t launch_backward(const void* packed, void* save, int B, float* grad, int ctas,
+                            cudaStream_t st);
+cudaError_t launch_pack(const float* theta, void* packed, cudaStream_t st);
+// Adam constants, each rounded once to float from its double value:
+// c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)
+struct AdamConsts {
+  float lr, beta1, beta2, one_minus_beta1, one_minus_beta2, eps, c1, c2;
+};
+cudaError_t launch_adam(float* theta, float* m, float* v, float* grad, void* packed,
+                        const AdamConsts& k, cudaStream_t st);
+cudaError_t launch_decide(const LearnParams& p, int level, cudaStream_t st);
+cudaError_t launch_region_boxes(const int* region_lo, int side, int n, int B, const int tdim[3],
+                                LatBox* boxes, int* status, cudaStream_t st);
+}  // namespace cnn
 
 }  // namespace uwb

@@ -102,3 +102,40 @@ def test_tile_shape_table(uwb):
     for bad in ([16, 8, 1], [24, 8, 1], [16, 4, 4]):   # wrong size, not a power of 2, z in 2-D
         with pytest.raises(uwb.UwbError):
             uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, bad)
+
+
+def test_learned_proposal_arguments_are_rejected_on_the_host(uwb):
+    L = uwb.lib()
+    fake = ctypes.c_void_p(0x1000)
+    ok = uwb.uwb_default_rule()
+    sq = uwb.make_grid({"dim": 2, "n": [512, 512, 1], "origin": [0, 0, 0],
+                        "pitch": [2e-4] * 2 + [1.0]})
+    rect = uwb.make_grid({"dim": 2, "n": [512, 256, 1], "origin": [0, 0, 0],
+                          "pitch": [2e-4] * 2 + [1.0]})
+    odd = uwb.make_grid({"dim": 2, "n": [96, 96, 1], "origin": [0, 0, 0],
+                         "pitch": [2e-4] * 2 + [1.0]})
+
+    def learned(grid, threshold=0.5, levels=2, ws=fake, nbytes=1 << 30):
+        return L.uwb_localize_learned(4, fake, 8, 256, fake, 0, ctypes.byref(grid), 1e8, 5e10, 4,
+                                      uwb.UWB_DAS, ctypes.byref(ok), fake, threshold, levels, ws,
+                                      nbytes, fake, None)
+
+    assert learned(rect) == uwb.UWB_ERR_UNSUPPORTED          # not square
+    assert learned(odd, levels=2) == uwb.UWB_ERR_UNSUPPORTED  # two levels need a multiple of 128
+    assert learned(sq, levels=4) == uwb.UWB_ERR_ARG
+    assert learned(sq, threshold=1.5) == uwb.UWB_ERR_ARG
+    assert learned(sq, ws=None) == uwb.UWB_ERR_WORKSPACE
+    assert learned(sq, nbytes=16) == uwb.UWB_ERR_WORKSPACE
+    assert uwb.uwb_localize_learned_workspace(4, sq, ok) > 4 * 32 * 32 * 4
+    assert L.uwb_cnn_train_workspace(0) == 0
+    assert L.uwb_cnn_train_workspace(8) >= 8 * 242688 + 4 * uwb.CNN_PARAMS
+    assert L.uwb_cnn_forward(fake, fake, 0, fake, None) == uwb.UWB_ERR_ARG
+    assert L.uwb_cnn_adam(fake, fake, fake, fake, fake, 0, 1e-3, None) == uwb.UWB_ERR_ARG
+    assert L.uwb_cnn_adam(fake, fake, fake, fake, fake, 1, -1.0, None) == uwb.UWB_ERR_ARG
+    assert L.uwb_cnn_gradients(fake, fake, fake, 4, fake, fake, None, 0, None) == \
+        uwb.UWB_ERR_WORKSPACE
+    # coarse maps: the side must be a multiple of 32 inside the grid
+    assert L.uwb_coarse_maps(4, fake, 8, 256, fake, 0, ctypes.byref(sq), 1e8, 5e10, 4, None, 48,
+                             fake, None, 0, None) == uwb.UWB_ERR_ARG
+    assert L.uwb_coarse_maps(4, fake, 8, 256, fake, 0, ctypes.byref(sq), 1e8, 5e10, 4, fake, 64,
+                             fake, None, 0, None) == uwb.UWB_ERR_WORKSPACE
