@@ -351,6 +351,145 @@ def run_ragged(args, uwb, torch):
     return out
 
 
+def _timed(torch, stream, flush, fn, steps):
+    """Mean device milliseconds of fn() over `steps` calls, L2 flushed before each."""
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def run_learned(args, cfg, bf, uwb, torch):
+    """Localisation with the learned segment proposal (trained weights shipped
+    with the package) on held-out scans, against the plain framework and the
+    full-resolution image with the same beamformer on the same scans."""
+    from paper_1709_02549_gb300 import proposal
+    B = args.batch
+    theta, record = proposal.load()
+    threshold = record["threshold"]
+    wl = proposal.Workload(cfg.name)
+    packed = torch.zeros(uwb.CNN_PACKED_BYTES, dtype=torch.uint8, device="cuda")
+    uwb.uwb_cnn_pack(torch.from_numpy(theta).cuda(), packed)
+    batch = phantom.make_batch(cfg, B, first_scan=proposal.EVAL_FIRST_SCAN)
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = wl.ants
+    grid, rule = wl.grid, wl.rule
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ws_l = torch.empty(uwb.uwb_localize_learned_workspace(B, grid, rule), dtype=torch.uint8,
+                       device="cuda")
+    out_l = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    ws_f = torch.empty(uwb.uwb_localize_workspace(B, cfg.n_antennas, cfg.n_samples, grid, bf,
+                                                  rule), dtype=torch.uint8, device="cuda")
+    out_f = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+
+    def learned():
+        uwb.uwb_localize_learned(traces, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule, packed,
+                                 threshold, 2, ws_l, out_l, stream)
+
+    def framework():
+        uwb.uwb_localize_batch(traces, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule, ws_f,
+                               out_f, None, stream)
+
+    for _ in range(args.warmup):
+        learned()
+        framework()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    uwb.uwb_phase_timing(True)
+    ms_l = _timed(torch, stream, flush, learned, args.steps)
+    calls, phase_ms = uwb.uwb_phase_times()
+    uwb.uwb_phase_timing(False)
+    ms_f = _timed(torch, stream, flush, framework, args.steps)
+    clock_info = clocks.stop()
+    rl = uwb.results_from_device(out_l)
+    rf = uwb.results_from_device(out_f)
+
+    # the network alone: forward passes over B coarse maps (tensor cores)
+    maps = torch.rand(B, 32, 32, device="cuda")
+    scores = torch.empty(B, 16, device="cuda")
+    ms_cnn = _timed(torch, stream, flush,
+                    lambda: uwb.uwb_cnn_forward(packed, maps, scores, stream), args.steps)
+    # algorithmic FLOPs per map: layer 1 (1 -> 32) and two 32 -> 32 layers, 3x3
+    cnn_flops = B * 2.0 * 1024 * 32 * 9 * (1 + 2 * 32)
+    cnn_tflops = cnn_flops / (ms_cnn / 1e3) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(ROOT / "MEASURED_PEAKS.json"))
+    except (OSError, ValueError):
+        pass
+    bf16_peak = peaks.get("bf16_tflops") or 1900.0
+
+    # full-resolution images of the same scans
+    P = int(np.prod(grid["n"]))
+    img = torch.empty(B, P, device="cuda")
+    peak = torch.empty(B, dtype=torch.int64, device="cuda")
+    fr = lambda: uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img,
+                                     peak)
+    fr()
+    ms_fr = _timed(torch, stream, flush, fr, args.fullres_steps)
+    pk = peak.cpu().numpy()
+    del img
+    gx = grid["n"][0]
+    full_idx = np.stack([pk % gx, pk // gx], 1)
+
+    def err_mm(idx):
+        xy = np.stack([grid["origin"][a] + idx[:, a] * grid["pitch"][a] for a in range(2)], 1)
+        truth = np.array([t[0][:2] for t in batch["tumors"]])
+        return float(np.mean(np.linalg.norm(xy - truth, axis=1)) * 1e3)
+
+    learned_mask = rl["stop_reason"] == uwb.UWB_STOP_LEARNED
+    pts_final = np.prod(rl["roi_hi"] - rl["roi_lo"], axis=1).astype(np.float64)
+    fpp = flops_per_point(bf, cfg.n_antennas, cfg.window)
+    per = [p / max(calls, 1) for p in phase_ms]
+    final_tflops = float(pts_final.sum()) * fpp / (per[2] / 1e3) / 1e12 if per[2] > 0 else None
+    return {
+        "metric": "localised scans/s with the learned segment proposal (1 GB300)",
+        "value": B / (ms_l / 1e3), "unit": "scans/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True,
+        "dtype": "f32 image, bf16 network", "data": "synthetic (held-out seeds)",
+        "config": {"workload": workload_name(cfg, args.beamformer, B),
+                   "scans_first_seed_offset": proposal.EVAL_FIRST_SCAN,
+                   "threshold": threshold, "levels": 2,
+                   "trained_on": f"{record['train_scans']} scans, seeds from offset "
+                                 f"{record['train_first_scan']}",
+                   "l2": "256 MB buffer written before every timed step (not timed)"},
+        "framework": {"value": B / (ms_f / 1e3), "ms_per_step": ms_f},
+        "fullres": {"value": B / (ms_fr / 1e3), "ms_per_step": ms_fr},
+        "speedup_vs_framework": ms_f / ms_l, "speedup_vs_fullres": ms_fr / ms_l,
+        "agreement_with_framework": float(np.mean(np.all(rl["loc_idx"][:, :2] ==
+                                                          rf["loc_idx"][:, :2], axis=1))),
+        "agreement_with_fullres": float(np.mean(np.all(rl["loc_idx"][:, :2] == full_idx,
+                                                        axis=1))),
+        "fallback_rate": float(1.0 - learned_mask.mean()),
+        "loc_error_mm": {"learned": err_mm(rl["loc_idx"]), "framework": err_mm(rf["loc_idx"]),
+                         "fullres": err_mm(full_idx)},
+        "points_per_scan": {"learned": float(rl["points_evaluated"].mean()),
+                            "framework": float(rf["points_evaluated"].mean()), "full": P},
+        "phase_ms_per_step": {"proposal": per[0], "fallback_select": per[1], "final": per[2],
+                              "finish": per[3]},
+        "roofline": {"bound": "alu", "achieved": final_tflops, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s",
+                     "frac": final_tflops / FP32_PEAK_TFLOPS if final_tflops else None,
+                     "kernel": "k_image final-region pass", "traffic": None},
+        "cnn_roofline": {"bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak,
+                         "unit": "TFLOP/s", "frac": cnn_tflops / bf16_peak,
+                         "kernel": "k_cnn_forward (tcgen05, BF16 -> FP32)",
+                         "ms_per_launch": ms_cnn, "maps_per_launch": B,
+                         "peak_source": "MEASURED_PEAKS bf16 burst" if peaks else "fallback"},
+        "clocks": clock_info,
+        "gpu_launches": args.steps * 15,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,9 +503,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-scans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="localize", choices=["localize", "presence", "ragged"],
+    ap.add_argument("--mode", default="localize",
+                    choices=["localize", "presence", "ragged", "learned"],
                     help="presence: the two-decimation tumour-presence test; ragged: a batch "
-                         "of uneven scans through the plan API")
+                         "of uneven scans through the plan API; learned: the learned segment "
+                         "proposal against the plain framework")
     ap.add_argument("--decimation2", type=int, default=0,
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()
@@ -395,6 +536,9 @@ def main():
         return
     if args.mode == "ragged":
         print(json.dumps(run_ragged(args, uwb, torch)), flush=True)
+        return
+    if args.mode == "learned":
+        print(json.dumps(run_learned(args, cfg, bf, uwb, torch)), flush=True)
         return
     batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
     grid = cfg.grid()

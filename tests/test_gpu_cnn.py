@@ -284,3 +284,52 @@ def test_unconfident_scans_fall_back_to_the_framework(gpu):
                     "box_lo", "box_hi"):
             assert r[key] == p[key], key
         assert r["points_evaluated"] == p["points_evaluated"] + 1024
+
+
+# ------------------------------------------------------------ the trained network
+
+def test_trained_network_gains_over_the_framework(gpu):
+    """The shipped weights on held-out scans of the 512 x 512 workload: the same
+    locations as the plain Eq. 5 framework (same literal-DMAS final imaging)
+    at the same localisation error, from far fewer focal points and in less
+    device time."""
+    from paper_1709_02549_gb300 import proposal
+    theta, record = proposal.load()
+    wl = proposal.Workload("dmas2d_512")
+    _, pk = packed_of(gpu, theta)
+    B = 512
+    b = phantom.make_batch(wl.cfg, B, proposal.EVAL_FIRST_SCAN + 50_000)
+    tr = dev(b["traces"])
+    th = record["threshold"]
+    rl = wl.learned(tr, pk, th, gpu.UWB_DMAS_LITERAL)
+    rf = wl.framework(tr, gpu.UWB_DMAS_LITERAL)
+    agree = np.mean(np.all(rl["loc_idx"][:, :2] == rf["loc_idx"][:, :2], axis=1))
+    fallback = np.mean(rl["stop_reason"] != gpu.UWB_STOP_LEARNED)
+    g = wl.grid
+    truth = np.array([t[0][:2] for t in b["tumors"]])
+
+    def err(r):
+        xy = np.stack([g["origin"][a] + r["loc_idx"][:, a] * g["pitch"][a] for a in range(2)], 1)
+        return np.mean(np.linalg.norm(xy - truth, axis=1)) * 1e3
+
+    assert agree >= 0.99, agree
+    assert fallback <= 0.05, fallback
+    assert rl["points_evaluated"].mean() <= 0.3 * rf["points_evaluated"].mean()
+    assert err(rl) <= err(rf) + 0.02
+    # device time of the two searches on the same scans
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_l = timed(lambda: wl.learned(tr, pk, th, gpu.UWB_DMAS_LITERAL))
+    t_f = timed(lambda: wl.framework(tr, gpu.UWB_DMAS_LITERAL))
+    assert t_l * 2.0 < t_f, (t_l, t_f)

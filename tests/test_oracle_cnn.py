@@ -189,3 +189,18 @@ def test_below_threshold_the_plain_framework_decides():
     assert r["fallback"]
     ref = oracle.localize(tr, ants, g, cfg.v, cfg.fs, cfg.window, oracle.DAS, rule)
     assert r["loc_idx"] == ref["loc_idx"][:2]
+
+
+def test_shipped_weights_load_with_their_training_record():
+    from paper_1709_02549_gb300 import proposal
+    theta, record = proposal.load()
+    assert theta.shape == (cnn.N_PARAMS,) and theta.dtype == np.float32
+    assert np.all(np.isfinite(theta))
+    assert record["workload"] == "dmas2d_512"
+    assert record["train_scans"] >= 100_000
+    assert 0.0 < record["threshold"] <= 1.0
+    # training, validation and evaluation seeds never overlap the benchmark's
+    assert record["train_first_scan"] >= 1_000_000
+    # the proposal's own initialisation follows the oracle's parameter layout
+    assert proposal.N_PARAMS == cnn.N_PARAMS
+    assert [tuple(s) for s in proposal.SIZES] == [s for _, s in cnn.SIZES]
