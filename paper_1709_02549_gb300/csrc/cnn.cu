@@ -80,18 +80,27 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t phase, int* sta
 }
 
 // One 3x3 convolution layer (32 -> 32 channels) into TMEM: tile i's
-// accumulator is columns [32 i, 32 i + 32).
+// accumulator is columns [32 i, 32 i + 32). The descriptors are built once;
+// each MMA adds its operand's byte offset / 16 to the 14-bit address field,
+// which stays inside [0, 2^14) for every operand of the layer (shared-memory
+// addresses are below 256 KB and all offsets land inside the buffers), so
+// nothing carries into the stride fields.
 __device__ __forceinline__ void issue_conv(uint32_t in_base, uint32_t w_base, uint32_t tmem) {
-  for (int i = 0; i < TILES; ++i)
-    for (int t = 0; t < TAPS; ++t) {
-      const int row0 = i * 128 + PAD0 + tap_shift(t);
+  const uint64_t a0 = umma_desc(in_base + PAD0 * 16, LBO_ACT, 128);
+  const uint64_t b0 = umma_desc(w_base, 512, 128);
+#pragma unroll 1
+  for (int i = 0; i < TILES; ++i) {
+    const uint64_t ai = a0 + static_cast<uint64_t>(i * 128);  // 128 rows of 16 bytes
+    const uint32_t d = tmem + i * CH;
+#pragma unroll
+    for (int t = 0; t < TAPS; ++t)
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        const uint64_t a = umma_desc(in_base + ks * 2 * LBO_ACT + row0 * 16, LBO_ACT, 128);
-        const uint64_t b = umma_desc(w_base + t * WTAP + ks * 2 * 512, 512, 128);
-        umma_bf16(tmem + i * CH, a, b, kIdesc, (t | ks) != 0);
+        const int64_t da = (ks * 2 * LBO_ACT) / 16 + tap_shift(t);
+        const uint64_t b = b0 + static_cast<uint64_t>((t * WTAP + ks * 2 * 512) / 16);
+        umma_bf16(d, ai + static_cast<uint64_t>(da), b, kIdesc, (t | ks) != 0);
       }
-    }
+  }
 }
 
 // ---------------------------------------------------------------- self-check
@@ -154,9 +163,10 @@ constexpr int F_ACT1 = F_ACT0 + ACT_BYTES;
 constexpr int F_W2 = F_ACT1 + ACT_BYTES;
 constexpr int F_W3 = F_W2 + WOP_BYTES;
 constexpr int F_X = F_W3 + WOP_BYTES;          // X0, float, buffer positions
-constexpr int F_W1 = F_X + U * 4;              // W1 as float [32][9]
-constexpr int F_BIAS = F_W1 + CH * TAPS * 4;   // b1, b2, b3, wh [32] each, bh
-constexpr int F_F = F_BIAS + 144 * 4;          // segment means [16][32]
+constexpr int W1_ROW = 12;                     // W1 rows padded to 3 float4
+constexpr int F_W1 = F_X + U * 4;              // W1 as float [32][12]
+constexpr int F_BIAS = F_W1 + CH * W1_ROW * 4; // b1, b2, b3, wh [32] each, bh
+constexpr int F_F = F_BIAS + 144 * 4;          // segment means, [32 channels][16 segments]
 constexpr int F_RED = F_F + SEGS * CH * 4;     // reduction scratch [8]
 constexpr int F_BAR = F_RED + 64;
 constexpr int F_SLOT = F_BAR + 8;
@@ -210,7 +220,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint16_t* pw2 = reinterpret_cast<const uint16_t*>(packed + PK_W2);
   const uint16_t* pw3 = reinterpret_cast<const uint16_t*>(packed + PK_W3);
   const float* pf = reinterpret_cast<const float*>(packed + PK_F32);
-  for (int i = tid; i < CH * TAPS; i += THREADS) sW1[i] = bf2f(pw1[i]);
+  for (int i = tid; i < CH * W1_ROW; i += THREADS) {
+    const int c = i / W1_ROW, t = i % W1_ROW;
+    sW1[i] = t < TAPS ? bf2f(pw1[c * TAPS + t]) : 0.f;
+  }
   for (int i = tid; i < 4 * CH + 1; i += THREADS) sBias[i] = pf[i];
   for (int i = tid; i < CH * TAPS * CH; i += THREADS) {
     const int o = i / (TAPS * CH), t = (i / CH) % TAPS, c = i % CH;  // W[o][t][c]
@@ -225,15 +238,26 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem = *slot;
   uint32_t phase = 0;
 
+  // each map's energies are loaded one map ahead
+  float e_next[4] = {0.f, 0.f, 0.f, 0.f};
+  if (blockIdx.x < B)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      e_next[j] = maps[static_cast<size_t>(blockIdx.x) * (MAP * MAP) + tid + THREADS * j];
+
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     unsigned char* sv = save ? save + static_cast<size_t>(b) * SAVE_BYTES : nullptr;
     // ---- X0 = E / max E (all-zero maps stay zero; non-finite values are
     // recorded and read as zero)
-    const float* E = maps + static_cast<size_t>(b) * (MAP * MAP);
     float e[4], mx = 0.f;
 #pragma unroll
+    for (int j = 0; j < 4; ++j) e[j] = e_next[j];
+    if (b + static_cast<int>(gridDim.x) < B)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        e_next[j] = maps[static_cast<size_t>(b + gridDim.x) * (MAP * MAP) + tid + THREADS * j];
+#pragma unroll
     for (int j = 0; j < 4; ++j) {
-      e[j] = E[tid + THREADS * j];
       if (!isfinite(e[j])) {
         if (status) atomicExch(status, UWB_ERR_NONFINITE);
         e[j] = 0.f;
@@ -255,29 +279,47 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     if (sv) copy16(sv + SAVE_X0, sX, U * 4);
 
-    // ---- layer 1 (1 -> 32 channels) on the CUDA cores
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      const int p = tid + THREADS * j;
-      const int u = pos_u(p >> 5, p & 31);
-      float xv[TAPS];
+    // ---- layer 1 (1 -> 32 channels) on the CUDA cores: this thread's 4
+    // positions at once, so that every weight is read once per 4 positions
+    {
+      float xv[4][TAPS];
+      int uu[4];
 #pragma unroll
-      for (int t = 0; t < TAPS; ++t) xv[t] = sX[u + tap_shift(t)];
-      uint32_t w[16];
+      for (int j = 0; j < 4; ++j) {
+        const int p = tid + THREADS * j;
+        uu[j] = pos_u(p >> 5, p & 31);
 #pragma unroll
-      for (int c = 0; c < 32; c += 2) {
-        float z0 = sBias[c], z1 = sBias[c + 1];
-#pragma unroll
-        for (int t = 0; t < TAPS; ++t) {
-          z0 = fmaf(sW1[c * TAPS + t], xv[t], z0);
-          z1 = fmaf(sW1[(c + 1) * TAPS + t], xv[t], z1);
-        }
-        w[c >> 1] = pack2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
+        for (int t = 0; t < TAPS; ++t) xv[j][t] = sX[uu[j] + tap_shift(t)];
       }
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        uint32_t w[4][4];
 #pragma unroll
-      for (int g = 0; g < 4; ++g)
-        *reinterpret_cast<uint4*>(act0 + act_off(u, 8 * g)) =
-            make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+        for (int c2 = 0; c2 < 4; ++c2) {
+          float z[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = 8 * g + 2 * c2 + h;
+            const float4* wr = reinterpret_cast<const float4*>(sW1 + c * W1_ROW);
+            const float4 q0 = wr[0], q1 = wr[1], q2 = wr[2];
+            const float wt[TAPS] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
+            const float bc = sBias[c];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float acc = bc;
+#pragma unroll
+              for (int t = 0; t < TAPS; ++t) acc = fmaf(wt[t], xv[j][t], acc);
+              z[h][j] = fmaxf(acc, 0.f);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) w[j][c2] = pack2(z[0][j], z[1][j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          *reinterpret_cast<uint4*>(act0 + act_off(uu[j], 8 * g)) =
+              make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
+      }
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -305,14 +347,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (!alive) break;
 
-    // ---- segment means F[s][c] of A3 (in act0)
-    if (tid < SEGS * 4) {
-      const int s = tid >> 2, g = tid & 3, sy = s >> 2, sx = s & 3;
+    // ---- segment means F[s][c] of A3 (in act0): thread = (segment s,
+    // 8-channel group g, pair of segment rows r); the 4 row pairs of a
+    // (s, g) are neighbouring lanes and are summed with shuffles
+    {
+      const int r = tid & 3, g = (tid >> 2) & 3, s = tid >> 4, sy = s >> 2, sx = s & 3;
       float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int iy = 0; iy < 8; ++iy)
+#pragma unroll
+      for (int iy = 2 * r; iy < 2 * r + 2; ++iy)
+#pragma unroll
         for (int ix = 0; ix < 8; ++ix) {
-          const uint4 v =
-              *reinterpret_cast<const uint4*>(act0 + act_off(pos_u(8 * sy + iy, 8 * sx + ix), 8 * g));
+          const uint4 v = *reinterpret_cast<const uint4*>(
+              act0 + act_off(pos_u(8 * sy + iy, 8 * sx + ix), 8 * g));
           const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -321,7 +367,13 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sF[s * CH + 8 * g + k] = acc[k] * (1.0f / 64.0f);
+      for (int k = 0; k < 8; ++k) {
+        acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], 1);
+        acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], 2);
+      }
+      if (r == 0)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sF[(8 * g + k) * SEGS + s] = acc[k] * (1.0f / 64.0f);
     }
     __syncthreads();
 
@@ -330,7 +382,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       float z = -INFINITY;
       if (lane < SEGS) {
         z = sBias[4 * CH];
-        for (int c = 0; c < CH; ++c) z = fmaf(sBias[3 * CH + c], sF[lane * CH + c], z);
+        for (int c = 0; c < CH; ++c) z = fmaf(sBias[3 * CH + c], sF[c * SEGS + lane], z);
         if (scores) scores[static_cast<size_t>(b) * SEGS + lane] = z;
       }
       if (labels) {
@@ -352,7 +404,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (sv)
       for (int i = tid; i < SEGS * CH; i += THREADS)
-        reinterpret_cast<float*>(sv + SAVE_F)[i] = sF[i];
+        reinterpret_cast<float*>(sv + SAVE_F)[i] = sF[(i % CH) * SEGS + i / CH];  // F[s][c]
     __syncthreads();
   }
 
@@ -651,8 +703,6 @@ __global__ void k_learned_decide(const LearnParams P, int level) {
     st.fallback = 0;
     st.map_points = 0;
     P.learned[s] = 0;
-    long long* r64 = reinterpret_cast<long long*>(R);
-    for (int k = 0; k < static_cast<int>(sizeof(uwb_result) / 8); ++k) r64[k] = 0;
     empty_box(P.prof_boxes[s]);
   }
   if (st.fallback) {
@@ -757,15 +807,26 @@ cudaError_t launch_region_boxes(const int* region_lo, int side, int n, int B, co
   return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit of a kernel, raised once per device.
+static bool smem_ready(const void* fn, int smem, int* done) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return false;
+  if (done[d]) return true;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return false;
+  done[d] = 1;  // a race only repeats the same call
+  return true;
+}
+static int g_fwd_attr[64], g_bwd_attr[64], g_self_attr[64];
+
 size_t forward_smem() { return F_SMEM; }
 size_t backward_smem() { return G_SMEM; }
 size_t selftest_smem() { return ST_SMEM; }
 
 cudaError_t launch_selftest(const uint16_t* a, const uint16_t* b, float* d, int* status,
                             cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_umma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ST_SMEM);
-  if (e != cudaSuccess) return e;
+  if (!smem_ready(reinterpret_cast<const void*>(k_umma_selftest), ST_SMEM, g_self_attr))
+    return cudaErrorInvalidValue;
   k_umma_selftest<<<1, 128, ST_SMEM, st>>>(a, b, d, status);
   return cudaGetLastError();
 }
@@ -773,9 +834,8 @@ cudaError_t launch_selftest(const uint16_t* a, const uint16_t* b, float* d, int*
 cudaError_t launch_forward(const void* packed, const float* maps, int B, float* scores,
                            const int* labels, void* save, float* loss, int* status, int ctas,
                            cudaStream_t st) {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, F_SMEM);
-  if (e != cudaSuccess) return e;
+  if (!smem_ready(reinterpret_cast<const void*>(k_cnn_forward), F_SMEM, g_fwd_attr))
+    return cudaErrorInvalidValue;
   k_cnn_forward<<<ctas, THREADS, F_SMEM, st>>>(static_cast<const unsigned char*>(packed), maps, B,
                                                scores, labels, static_cast<unsigned char*>(save),
                                                loss, status);
@@ -784,9 +844,8 @@ cudaError_t launch_forward(const void* packed, const float* maps, int B, float* 
 
 cudaError_t launch_backward(const void* packed, void* save, int B, float* grad, int ctas,
                             cudaStream_t st) {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_cnn_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM);
-  if (e != cudaSuccess) return e;
+  if (!smem_ready(reinterpret_cast<const void*>(k_cnn_backward), G_SMEM, g_bwd_attr))
+    return cudaErrorInvalidValue;
   k_cnn_backward<<<ctas, THREADS, G_SMEM, st>>>(static_cast<const unsigned char*>(packed),
                                                 static_cast<unsigned char*>(save), B, grad);
   return cudaGetLastError();

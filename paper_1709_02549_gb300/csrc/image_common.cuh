@@ -284,6 +284,111 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
   return energy;
 }
 
+// Four window samples per pass (k0 .. k0 + 3) as two float2 streams: the
+// per-antenna loads, offset and interpolation work is shared by twice as many
+// pair products as in energy_literal. Used for the 16-antenna register block,
+// where the 2 x 16 float2 values still allow 4 resident CTAs; for 32 antennas
+// the pair version at 4 CTAs per SM measured faster than this one at 2.
+struct LitRaw4 {
+  float y0, y1, y2, y3, y4, f;
+};
+
+template <bool STAGED, bool RG>
+__device__ __forceinline__ LitRaw4 lit_load4(const ImgParams& P, const ScanDesc* __restrict__ sS,
+                                             const float* __restrict__ sTr,
+                                             const float2* __restrict__ sNF, int i, int T,
+                                             int tid, int k0) {
+  const float2 nf = sNF[i * T + tid];
+  const int off = __float_as_int(nf.x) + k0;
+  LitRaw4 r;
+  r.f = nf.y;
+  if (STAGED) {
+    const float* row = sTr + i * P.span + off;
+    r.y0 = row[0];
+    r.y1 = row[1];
+    r.y2 = row[2];
+    r.y3 = row[3];
+    r.y4 = row[4];
+  } else if (i < scan_M<RG>(P, sS)) {
+    const ScanDesc S = *sS;
+    r.y0 = sample_at(S, P.dtype, i, off);
+    r.y1 = sample_at(S, P.dtype, i, off + 1);
+    r.y2 = sample_at(S, P.dtype, i, off + 2);
+    r.y3 = sample_at(S, P.dtype, i, off + 3);
+    r.y4 = sample_at(S, P.dtype, i, off + 4);
+  } else {
+    r.y0 = r.y1 = r.y2 = r.y3 = r.y4 = 0.f;
+  }
+  return r;
+}
+
+template <int MMAX, bool STAGED, bool RG>
+__device__ __forceinline__ float energy_literal4(const ImgParams& P,
+                                                 const ScanDesc* __restrict__ sS,
+                                                 const float* __restrict__ sTr,
+                                                 const float4* __restrict__ sAnt,
+                                                 float2* __restrict__ sNF, int nlo, int cl_lo,
+                                                 int cl_hi, float px, float py, float pz) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int M = scan_M<RG>(P, sS);
+  const float kscale = scan_kscale<RG>(P, sS);
+  const float hf = static_cast<float>(P.h);
+  for (int i = 0; i < MMAX; ++i) {
+    int n0 = 0;
+    float f = 0.f;
+    if (i < M) {
+      const float4 a = sAnt[i];
+      const float dx = px - a.x;
+      const float dy = py - a.y;
+      const float dz = pz - a.z;
+      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float t = fmaf(d, kscale, -hf);
+      const float fl = floorf(t);
+      f = t - fl;
+      n0 = static_cast<int>(fl);
+      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo;
+    }
+    sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
+  }
+  float energy = 0.f;
+  for (int k0 = 0; k0 < P.W; k0 += 4) {
+    float2 xa[MMAX], xb[MMAX];
+    float2 acc[8], bcc[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      acc[a] = make_float2(0.f, 0.f);
+      bcc[a] = make_float2(0.f, 0.f);
+    }
+    LitRaw4 next = lit_load4<STAGED, RG>(P, sS, sTr, sNF, 0, T, tid, k0);
+#pragma unroll
+    for (int j = 0; j < MMAX; ++j) {
+      const LitRaw4 cur = next;
+      if (j + 1 < MMAX) next = lit_load4<STAGED, RG>(P, sS, sTr, sNF, j + 1, T, tid, k0);
+      const float2 ff = make_float2(cur.f, cur.f), nf2 = make_float2(-cur.f, -cur.f);
+      const float2 lo_a = make_float2(cur.y0, cur.y1), hi_a = make_float2(cur.y1, cur.y2);
+      const float2 lo_b = make_float2(cur.y2, cur.y3), hi_b = make_float2(cur.y3, cur.y4);
+      xa[j] = __ffma2_rn(ff, hi_a, __ffma2_rn(nf2, lo_a, lo_a));
+      xb[j] = __ffma2_rn(ff, hi_b, __ffma2_rn(nf2, lo_b, lo_b));
+#pragma unroll
+      for (int i = 0; i < j; ++i) {
+        acc[(i + j) & 7] = __ffma2_rn(xa[i], xa[j], acc[(i + j) & 7]);
+        bcc[(i + j) & 7] = __ffma2_rn(xb[i], xb[j], bcc[(i + j) & 7]);
+      }
+      // keep later loads from being hoisted above these products
+      asm volatile("" ::: "memory");
+    }
+    const float2 pa = __fadd2_rn(__fadd2_rn(__fadd2_rn(acc[0], acc[1]), __fadd2_rn(acc[2], acc[3])),
+                                 __fadd2_rn(__fadd2_rn(acc[4], acc[5]), __fadd2_rn(acc[6], acc[7])));
+    const float2 pb = __fadd2_rn(__fadd2_rn(__fadd2_rn(bcc[0], bcc[1]), __fadd2_rn(bcc[2], bcc[3])),
+                                 __fadd2_rn(__fadd2_rn(bcc[4], bcc[5]), __fadd2_rn(bcc[6], bcc[7])));
+    energy = fmaf(pa.x, pa.x, energy);
+    if (k0 + 1 < P.W) energy = fmaf(pa.y, pa.y, energy);
+    if (k0 + 2 < P.W) energy = fmaf(pb.x, pb.x, energy);
+    if (k0 + 3 < P.W) energy = fmaf(pb.y, pb.y, energy);
+  }
+  return energy;
+}
+
 // The global-load fallback (a window wider than the staged span) runs as a
 // real call, so its bounds checks and type conversions do not add to the
 // register allocation of the staged hot path.
@@ -298,7 +403,10 @@ template <int MMAX>
 __device__ __noinline__ float energy_literal_global(const ImgParams& P, const ScanDesc* sS,
                                                     const float4* sAnt, float2* sNF, float px,
                                                     float py, float pz) {
-  return energy_literal<MMAX, false, true>(P, sS, nullptr, sAnt, sNF, 0, 0, 0, px, py, pz);
+  if constexpr (MMAX <= 16)
+    return energy_literal4<MMAX, false, true>(P, sS, nullptr, sAnt, sNF, 0, 0, 0, px, py, pz);
+  else
+    return energy_literal<MMAX, false, true>(P, sS, nullptr, sAnt, sNF, 0, 0, 0, px, py, pz);
 }
 
 // The descriptor of scan `scan`: from the per-scan array of a ragged batch, or
@@ -541,9 +649,14 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
       const float py = fmaf(static_cast<float>(gy), scan_pit<RG>(P, sS, 1), scan_org<RG>(P, sS, 1));
       const float pz = fmaf(static_cast<float>(gz), scan_pit<RG>(P, sS, 2), scan_org<RG>(P, sS, 2));
       if constexpr (BF == BF_DMAS_LIT) {
-        energy = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi, px,
-                                                    py, pz)
-                      : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
+        if constexpr (V <= 16)
+          energy = fits ? energy_literal4<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                       px, py, pz)
+                        : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
+        else
+          energy = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                      px, py, pz)
+                        : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
       } else {
         energy = fits ? energy_sum<BF, V, true, MS, RG>(P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo,
                                                         cl_hi, px, py, pz)

@@ -213,10 +213,10 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   if (bf == BF_DMAS_LIT) {
     if (M > 64) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 64 (M=%d)", M);
     var.v = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
-    var.wpad = (W + 1) / 2 * 2;  // window samples go in pairs
+    // window samples go in fours (16-antenna block) or pairs
+    var.wpad = var.v <= 16 ? (W + 3) / 4 * 4 : (W + 1) / 2 * 2;
     var.threads = 128;
     var.rows = var.v;
-    // 4 CTAs per SM up to 32 antennas (the last 1.5 KB keeps a 184-sample span)
     // 4 CTAs (2 for the 64-antenna block) per SM, each with the 1 KB the
     // runtime reserves per CTA, fill the SM's 228 KB
     var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
@@ -1903,6 +1903,8 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
   auto* prefix = reinterpret_cast<int*>(ws + L.prefix);
   auto* profile = reinterpret_cast<float*>(ws + L.profile);
   cudaError_t e = cudaMemsetAsync(ws + L.keys, 0, L.status + 4 - L.keys, cs);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(out, 0, static_cast<size_t>(batch) * sizeof(uwb_result), cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
   const int span_m = pick_span(vm, M), span = pick_span(var, M);
