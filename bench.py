@@ -492,6 +492,56 @@ def run_learned(args, cfg, bf, uwb, torch):
     }
 
 
+def run_progressive(args, cfg, bf, uwb, torch):
+    """The progressive re-evaluation variant against the framework (same
+    beamformer, same scans): scans/s, points, agreement and errors."""
+    B = args.batch
+    batch = phantom.make_batch(cfg, B, first_scan=0)
+    grid = cfg.grid()
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    rule = uwb.uwb_default_rule()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    M, N = cfg.n_antennas, cfg.n_samples
+    ws_p = torch.empty(uwb.uwb_localize_progressive_workspace(B, M, N, grid, bf, rule),
+                       dtype=torch.uint8, device="cuda")
+    ws_f = torch.empty(uwb.uwb_localize_workspace(B, M, N, grid, bf, rule), dtype=torch.uint8,
+                       device="cuda")
+    out_p = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    out_f = torch.empty_like(out_p)
+    prog = lambda: uwb.uwb_localize_progressive(traces, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                                bf, rule, ws_p, out_p, stream)
+    fw = lambda: uwb.uwb_localize_batch(traces, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule,
+                                        ws_f, out_f, None, stream)
+    for _ in range(args.warmup):
+        prog()
+        fw()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_p = _timed(torch, stream, flush, prog, args.steps)
+    ms_f = _timed(torch, stream, flush, fw, args.steps)
+    clock_info = clocks.stop()
+    rp, rf = uwb.results_from_device(out_p), uwb.results_from_device(out_f)
+    err = lambda r: float(np.mean([nearest_error_mm(r["loc_xyz"][k], batch["tumors"][k])
+                                   for k in range(B)]))
+    return {"metric": "localised scans/s with progressive re-evaluation (variant, 1 GB300)",
+            "value": B / (ms_p / 1e3), "unit": "scans/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_p, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, args.beamformer, B)},
+            "framework": {"value": B / (ms_f / 1e3), "ms_per_step": ms_f},
+            "agreement_with_framework": float(np.mean(np.all(rp["loc_idx"] == rf["loc_idx"],
+                                                             axis=1))),
+            "iterations_mean": {"progressive": float(rp["iters"].mean()),
+                                "framework": float(rf["iters"].mean())},
+            "points_per_scan": {"progressive": float(rp["points_evaluated"].mean()),
+                                "framework": float(rf["points_evaluated"].mean())},
+            "loc_error_mm": {"progressive": err(rp), "framework": err(rf)},
+            "clocks": clock_info}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,7 +556,7 @@ def main():
     ap.add_argument("--ref-scans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="localize",
-                    choices=["localize", "presence", "ragged", "learned"],
+                    choices=["localize", "presence", "ragged", "learned", "progressive"],
                     help="presence: the two-decimation tumour-presence test; ragged: a batch "
                          "of uneven scans through the plan API; learned: the learned segment "
                          "proposal against the plain framework")
@@ -541,6 +591,9 @@ def main():
         return
     if args.mode == "learned":
         print(json.dumps(run_learned(args, cfg, bf, uwb, torch)), flush=True)
+        return
+    if args.mode == "progressive":
+        print(json.dumps(run_progressive(args, cfg, bf, uwb, torch)), flush=True)
         return
     batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
     grid = cfg.grid()

@@ -362,6 +362,27 @@ int uwb_device_status(int clear);
 /* Text of the last error of the calling thread ("" if none). */
 const char* uwb_last_error(void);
 
+/* Progressive re-evaluation: a variant of uwb_localize_batch (the paper's
+ * selection loop reads only the decimated profile). Iteration 1 is the
+ * paper's. Every later iteration first images again the region being split on
+ * its own lattice -- per axis at most the decimated lattice's point count c0,
+ * step ceil(side / c0), centred like the decimated lattice -- and takes its
+ * child choice from it: the variance of the region being split (sigma^2_{i-1}
+ * of Eq. 5) and the children's Eq. 5 metrics. The Eq. 6-7 stopping rule keeps
+ * reading the decimated profile, so consecutive iterations compare scatters
+ * over one lattice; energies are divided by the profile maximum throughout.
+ * Framing, final imaging and argmax as in uwb_localize_batch; arguments,
+ * result records and errors as there, except points_evaluated, which also
+ * counts every region lattice imaged. The loop runs as device kernels with
+ * no host round trip (per iteration: one step kernel and one image pass). */
+size_t uwb_localize_progressive_workspace(int batch, int M, int N, const uwb_grid* grid,
+                                          int beamformer, const uwb_rule* rule);
+int uwb_localize_progressive(int batch, const float* traces, int M, int N,
+                             const float* antennas, long long antenna_stride,
+                             const uwb_grid* grid, double v, double fs, int window,
+                             int beamformer, const uwb_rule* rule, void* workspace,
+                             size_t ws_bytes, uwb_result* results, void* stream);
+
 /* ------------------------------------------------------------------------
  * Learned segment proposal. The paper has no counterpart: a small network
  * proposes the segments that Section III's ROI selection would otherwise pick

@@ -143,6 +143,10 @@ def lib():
                                    ctypes.POINTER(Rule), ctypes.c_int, ctypes.POINTER(Result),
                                    ctypes.POINTER(Result)]
         L.orc_presence.restype = ctypes.c_int
+        L.orc_localize_progressive.argtypes = L.orc_localize.argtypes
+        L.orc_localize_progressive.restype = ctypes.c_int
+        L.orc_region_lattice.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ip]
+        L.orc_region_lattice.restype = None
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -242,6 +246,31 @@ def localize(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
     lib().orc_localize(trp, M, N, anp, ctypes.byref(g), float(v), float(fs), int(window),
                        int(beamformer), ctypes.byref(rule), ctypes.byref(res))
     return res.to_dict()
+
+
+def localize_progressive(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
+                         rule: Rule | None = None) -> dict:
+    """The framework with progressive re-evaluation (orc_localize_progressive)."""
+    tr, trp = _f32(traces)
+    an, anp = _f32(antennas)
+    M, N = tr.shape
+    g = make_grid(grid)
+    res = Result()
+    rule = make_rule() if rule is None else rule
+    st = lib().orc_localize_progressive(trp, M, N, anp, ctypes.byref(g), float(v), float(fs),
+                                        int(window), int(beamformer), ctypes.byref(rule),
+                                        ctypes.byref(res))
+    out = res.to_dict()
+    out["status"] = st if st != 0 else out["status"]
+    return out
+
+
+def region_lattice(lo: int, hi: int, c0: int):
+    """(first index, step, count) of orc_region_lattice."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib().orc_region_lattice(int(lo), int(hi), int(c0), ctypes.byref(a), ctypes.byref(b),
+                             ctypes.byref(c))
+    return a.value, b.value, c.value
 
 
 def presence(traces, antennas, grid: dict, v, fs, window, beamformer=DAS, rule: Rule | None = None,

@@ -591,6 +591,240 @@ static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* 
   return ORC_OK;
 }
 
+/* ------------------------------------------------- progressive re-evaluation */
+
+void orc_region_lattice(int lo, int hi, int c0, int* first, int* step, int* cnt) {
+  const int side = hi - lo;
+  int s = (side + c0 - 1) / c0;
+  if (s < 1) s = 1;
+  const int o = ((side - 1) % s) / 2;
+  *first = lo + o;
+  *step = s;
+  *cnt = (side - 1 - o) / s + 1;
+}
+
+int orc_localize_progressive(const float* traces, int M, int N, const float* antennas,
+                             const orc_grid* g, double v, double fs, int window,
+                             int beamformer, const orc_rule* r, orc_result* res) {
+  scan_data d = {traces, M, N, NULL, antennas, M, v, fs, window, beamformer};
+  memset(res, 0, sizeof *res);
+  for (int a = 0; a < 3; ++a) res->loc_idx[a] = -1;
+  if (!g || !r || g->dim < 2 || g->dim > 3 || (g->dim == 2 && g->n[2] != 1) ||
+      r->frame_den < 1 || r->frame_num < 0 || r->min_segment < 1) {
+    res->status = ORC_ERR_ARG;
+    return ORC_ERR_ARG;
+  }
+  const int D = orc_decimation(r, g);
+  lattice L0, L;
+  make_lattice(g, D, &L0);
+  res->decim = D;
+  for (int a = 0; a < 3; ++a) {
+    res->offset[a] = L0.off[a];
+    res->dcount[a] = L0.cnt[a];
+  }
+  const long nd = (long)L0.cnt[0] * L0.cnt[1] * L0.cnt[2];
+  double* prof = (double*)malloc(sizeof(double) * (size_t)nd);
+  double* e = (double*)malloc(sizeof(double) * (size_t)nd);
+  double* bufa = (double*)malloc(sizeof(double) * (size_t)nd);
+  double* bufb = (double*)malloc(sizeof(double) * (size_t)nd);
+  double* bufc = (double*)malloc(sizeof(double) * (size_t)nd);
+  if (!prof || !e || !bufa || !bufb || !bufc) {
+    free(prof); free(e); free(bufa); free(bufb); free(bufc);
+    res->status = ORC_ERR_ARG;
+    return ORC_ERR_ARG;
+  }
+  int st = scan_image(&d, g, L0.off, L0.step, L0.cnt, prof);
+  double pmax = 0.0;
+  if (st == ORC_OK)
+    for (long p = 0; p < nd; ++p) {
+      if (!isfinite(prof[p])) st = ORC_ERR_NONFINITE;
+      else if (prof[p] > pmax) pmax = prof[p];
+    }
+  res->points_evaluated = nd;
+  res->profile_max = pmax;
+  if (st != ORC_OK || pmax == 0.0) {
+    free(prof); free(e); free(bufa); free(bufb); free(bufc);
+    res->status = st;
+    if (st == ORC_OK) res->stop_reason = ORC_STOP_NO_TARGET;
+    return st;
+  }
+  for (long p = 0; p < nd; ++p) prof[p] /= pmax;
+
+  int max_iters = r->max_iters > 0 ? r->max_iters : default_iters(g);
+  if (max_iters > ORC_MAX_ITERS) max_iters = ORC_MAX_ITERS;
+  const int nchild = 1 << g->dim;
+  int R_lo[3] = {0, 0, 0}, R_hi[3] = {g->n[0], g->n[1], g->n[2]};
+  long na = gather_box(prof, &L0, R_lo, R_hi, bufa); /* Eq. 6-7 class of R (profile) */
+  double B_prev = 0.0, W_prev = 0.0;
+  res->stop_reason = ORC_STOP_NONE;
+
+  for (int i = 1; i <= max_iters; ++i) {
+    const int li = i - 1;
+    /* the lattice the child choice reads: the profile at iteration 1, then
+     * the region being split imaged again on its own lattice */
+    const double* ce = prof;
+    L = L0;
+    if (i >= 2) {
+      for (int a = 0; a < 3; ++a) {
+        if (a < g->dim) {
+          orc_region_lattice(R_lo[a], R_hi[a], L0.cnt[a], &L.off[a], &L.step[a], &L.cnt[a]);
+        } else {
+          L.off[a] = 0;
+          L.step[a] = 1;
+          L.cnt[a] = g->n[a];
+        }
+      }
+      const long ni = (long)L.cnt[0] * L.cnt[1] * L.cnt[2];
+      st = scan_image(&d, g, L.off, L.step, L.cnt, e);
+      for (long p = 0; st == ORC_OK && p < ni; ++p)
+        if (!isfinite(e[p])) st = ORC_ERR_NONFINITE;
+      if (st != ORC_OK) break;
+      for (long p = 0; p < ni; ++p) e[p] /= pmax;
+      res->points_evaluated += ni;
+      ce = e;
+    }
+    /* sigma^2_{i-1} of Eq. 5: the region being split, on the same lattice */
+    const long nr = gather_box(ce, &L, R_lo, R_hi, bufc);
+    const double var_prev = var_of(bufc, nr);
+    int mid[3];
+    for (int a = 0; a < 3; ++a) mid[a] = R_lo[a] + (R_hi[a] - R_lo[a]) / 2;
+    int best = -1, nvalid = 0;
+    double best_m = 0.0, second_m = 0.0;
+    int best_lo[3] = {0, 0, 0}, best_hi[3] = {0, 0, 0};
+    for (int c = 0; c < nchild; ++c) {
+      int clo[3], chi[3];
+      int ok = 1;
+      for (int a = 0; a < 3; ++a) {
+        if (a < g->dim) {
+          int bit = (c >> a) & 1;
+          clo[a] = bit ? mid[a] : R_lo[a];
+          chi[a] = bit ? R_hi[a] : mid[a];
+          if (chi[a] - clo[a] < r->min_segment) ok = 0;
+        } else {
+          clo[a] = R_lo[a];
+          chi[a] = R_hi[a];
+        }
+      }
+      if (!ok) continue;
+      long nc = gather_box(ce, &L, clo, chi, bufc);
+      if (nc == 0) continue;
+      double mu = mean_of(bufc, nc), var = var_of(bufc, nc);
+      double m;
+      if (r->metric == ORC_METRIC_MEAN)
+        m = mu;
+      else if (r->metric == ORC_METRIC_VARIANCE)
+        m = var;
+      else if (r->metric == ORC_METRIC_HYBRID_UNCLIPPED)
+        m = orc_hybrid_metric_unclipped(mu, var, var_prev);
+      else
+        m = orc_hybrid_metric(mu, var, var_prev);
+      if (nvalid == 0 || m > best_m) {
+        if (nvalid > 0) second_m = best_m;
+        best_m = m;
+        best = c;
+        memcpy(best_lo, clo, sizeof clo);
+        memcpy(best_hi, chi, sizeof chi);
+      } else if (nvalid == 1 || m > second_m) {
+        second_m = m;
+      }
+      ++nvalid;
+    }
+    if (nvalid == 0) {
+      res->stop_reason = ORC_STOP_MINSIZE;
+      res->iters = i - 1;
+      break;
+    }
+    res->child[li] = best;
+    res->n_children[li] = nvalid;
+    res->metric_top[li] = best_m;
+    res->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
+    int N_lo[3], N_hi[3];
+    for (int a = 0; a < 3; ++a) {
+      if (a < g->dim) {
+        int side = best_hi[a] - best_lo[a];
+        int grow = (side * r->frame_num + r->frame_den - 1) / r->frame_den;
+        N_lo[a] = best_lo[a] - grow < 0 ? 0 : best_lo[a] - grow;
+        N_hi[a] = best_hi[a] + grow > g->n[a] ? g->n[a] : best_hi[a] + grow;
+      } else {
+        N_lo[a] = best_lo[a];
+        N_hi[a] = best_hi[a];
+      }
+      res->box_lo[li][a] = N_lo[a];
+      res->box_hi[li][a] = N_hi[a];
+    }
+    /* Eq. 6-7 on the decimated profile, as in the paper's loop */
+    long nb = gather_box(prof, &L0, N_lo, N_hi, bufb);
+    double Wi, Bi;
+    orc_scatter(bufa, (int)na, bufb, (int)nb, &Wi, &Bi);
+    res->within[li] = Wi;
+    res->between[li] = Bi;
+    res->n_logged = i;
+    if (i >= 2) {
+      double mB = rel_gap(Bi, B_prev);
+      double mW = rel_gap(W_prev, Wi);
+      int cont = (Bi > B_prev) && (Wi < W_prev);
+      res->stop_margin[li] = cont ? (mB < mW ? mB : mW) : (-mB > -mW ? -mB : -mW);
+      if (!cont) {
+        res->stop_reason = ORC_STOP_METRIC;
+        res->iters = i - 1;
+        break;
+      }
+    } else {
+      res->stop_margin[li] = 1e300;
+    }
+    memcpy(R_lo, N_lo, sizeof N_lo);
+    memcpy(R_hi, N_hi, sizeof N_hi);
+    memcpy(bufa, bufb, sizeof(double) * (size_t)nb);
+    na = nb;
+    B_prev = Bi;
+    W_prev = Wi;
+    res->iters = i;
+    if (i == max_iters) {
+      res->stop_reason = ORC_STOP_CAP;
+      break;
+    }
+  }
+  free(prof); free(e); free(bufa); free(bufb); free(bufc);
+  if (st != ORC_OK) {
+    res->status = st;
+    return st;
+  }
+  for (int a = 0; a < 3; ++a) {
+    res->roi_lo[a] = R_lo[a];
+    res->roi_hi[a] = R_hi[a];
+  }
+  /* final imaging of the region at full resolution, then its argmax */
+  int step1[3] = {1, 1, 1}, cnt[3];
+  for (int a = 0; a < 3; ++a) cnt[a] = R_hi[a] - R_lo[a];
+  const long long nf = (long long)cnt[0] * cnt[1] * cnt[2];
+  double* img = (double*)malloc(sizeof(double) * (size_t)(nf > 0 ? nf : 1));
+  if (!img) {
+    res->status = ORC_ERR_ARG;
+    return ORC_ERR_ARG;
+  }
+  st = scan_image(&d, g, R_lo, step1, cnt, img);
+  if (st != ORC_OK) {
+    free(img);
+    res->status = st;
+    return st;
+  }
+  res->points_evaluated += nf;
+  long long bestp = -1;
+  for (long long p = 0; p < nf; ++p)
+    if (bestp < 0 || img[p] > img[bestp]) bestp = p;
+  if (bestp >= 0) {
+    long long k[3] = {bestp % cnt[0], (bestp / cnt[0]) % cnt[1],
+                      bestp / ((long long)cnt[0] * cnt[1])};
+    for (int a = 0; a < 3; ++a) {
+      res->loc_idx[a] = R_lo[a] + (int)k[a];
+      res->loc_xyz[a] = g->origin[a] + (double)res->loc_idx[a] * g->pitch[a];
+    }
+    res->peak = img[bestp];
+  }
+  free(img);
+  return ORC_OK;
+}
+
 int orc_presence(const float* traces, int M, int N, const float* antennas, const orc_grid* g,
                  double v, double fs, int window, int beamformer, const orc_rule* r,
                  int decimation2, orc_result* res1, orc_result* res2) {

@@ -142,6 +142,27 @@ int orc_localize_multistatic(const float* traces, int C, int N, const int* chan,
                              double fs, int window, int beamformer, const orc_rule* r,
                              orc_result* res);
 
+/* Progressive re-evaluation (a variant of Section III's ROI selection; the
+ * paper's loop reads only the decimated profile). Iteration 1 is the paper's.
+ * Every later iteration first images again the region being split, on the
+ * lattice orc_region_lattice gives per axis with c0 = the decimated
+ * lattice's point count on that axis, and takes its child choice from that
+ * lattice: the region's variance (sigma^2_{i-1} of Eq. 5) and the children's
+ * Eq. 5 metrics. The stopping rule (Eq. 6-7) keeps reading the decimated
+ * profile, so that consecutive iterations compare scatters over one lattice.
+ * Energies are divided by the maximum of the first profile throughout.
+ * Framing, final imaging and argmax as in orc_localize; points_evaluated
+ * counts every lattice point imaged plus the final region. */
+int orc_localize_progressive(const float* traces, int M, int N, const float* antennas,
+                             const orc_grid* g, double v, double fs, int window,
+                             int beamformer, const orc_rule* r, orc_result* res);
+
+/* Lattice of the index range [lo, hi) with at most c0 points: step
+ * ceil((hi - lo) / c0), offset ((hi - lo - 1) mod step) / 2 from lo (the
+ * centring rule of the decimated lattice), count (hi - lo - 1 - offset) / step
+ * + 1. Writes the first index, the step and the count. */
+void orc_region_lattice(int lo, int hi, int c0, int* first, int* step, int* cnt);
+
 /* Eq. 5 hybrid metric for one candidate, weight clipped to [0, 1], and the
  * printed formula without the clip (exposed for the tests). */
 double orc_hybrid_metric(double mean_i, double var_i, double var_prev);

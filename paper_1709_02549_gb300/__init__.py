@@ -148,6 +148,9 @@ def lib() -> ctypes.CDLL:
                                        vp]),
             "uwb_coarse_maps_workspace": (sz, [i]),
             "uwb_coarse_maps": (i, [i, vp, i, i, vp, ll, gp, d, d, i, vp, i, vp, vp, sz, vp]),
+            "uwb_localize_progressive_workspace": (sz, [i, i, i, gp, i, rp]),
+            "uwb_localize_progressive": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp, sz, vp,
+                                             vp]),
             "uwb_localize_learned_workspace": (sz, [i, gp, rp]),
             "uwb_localize_learned": (i, [i, vp, i, i, vp, ll, gp, d, d, i, i, rp, vp,
                                          ctypes.c_float, i, vp, sz, vp, vp]),
@@ -281,6 +284,31 @@ def uwb_localize_batch(traces, antennas, grid, v, fs, window, beamformer, rule: 
                                     workspace.numel() * workspace.element_size(),
                                     _ptr(out, "out"), _f32(image, "image", True),
                                     _stream(stream)), "uwb_localize_batch")
+
+
+def uwb_localize_progressive_workspace(batch, M, N, grid, beamformer, rule: UwbRule) -> int:
+    n = lib().uwb_localize_progressive_workspace(int(batch), int(M), int(N),
+                                                 ctypes.byref(make_grid(grid)), int(beamformer),
+                                                 ctypes.byref(rule))
+    if n == 0:
+        raise UwbError(UWB_ERR_ARG, "uwb_localize_progressive_workspace")
+    return n
+
+
+def uwb_localize_progressive(traces, antennas, grid, v, fs, window, beamformer, rule: UwbRule,
+                             workspace, out, stream=None):
+    """Progressive re-evaluation; traces [B, M, N]; antennas [M, 3] or [B, M, 3];
+    out uint8 [B * RESULT_BYTES]."""
+    B, M, N = traces.shape
+    stride = 0 if antennas.dim() == 2 else M * 3
+    _check(lib().uwb_localize_progressive(B, _f32(traces, "traces"), M, N,
+                                          _f32(antennas, "antennas"), stride,
+                                          ctypes.byref(make_grid(grid)), float(v), float(fs),
+                                          int(window), int(beamformer), ctypes.byref(rule),
+                                          _ptr(workspace, "workspace"),
+                                          workspace.numel() * workspace.element_size(),
+                                          _ptr(out, "out"), _stream(stream)),
+           "uwb_localize_progressive")
 
 
 def _host_f32(a, name):

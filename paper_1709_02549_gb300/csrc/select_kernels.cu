@@ -314,6 +314,300 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   }
 }
 
+// ----------------------------------------------- progressive re-evaluation
+// A variant of the loop above (the paper's loop reads only the decimated
+// profile): from the second iteration on, the child choice -- the variance of
+// the region being split (sigma^2_{i-1} of Eq. 5) and the children's Eq. 5
+// metrics -- reads a fresh lattice of that region, imaged just before this
+// kernel, with at most the decimated lattice's point count per axis (step
+// ceil(side / c0), centred). The Eq. 6-7 stopping rule keeps reading the
+// decimated profile, so consecutive iterations compare scatters over one
+// lattice. Energies are divided by the profile maximum throughout.
+
+// Lattice of the index range [lo, hi) with at most c0 points (first, step, count).
+__host__ __device__ inline void region_lattice(int lo, int hi, int c0, int& first, int& step,
+                                               int& cnt) {
+  const int side = hi - lo;
+  int s = (side + c0 - 1) / c0;
+  if (s < 1) s = 1;
+  const int o = ((side - 1) % s) / 2;
+  first = lo + o;
+  step = s;
+  cnt = (side - 1 - o) / s + 1;
+}
+
+__device__ void set_full_box(LatBox* box, const int lo[3], const int hi[3], const int tdim[3]) {
+  int tiles = 1;
+  for (int a = 0; a < 3; ++a) {
+    box->lo[a] = lo[a];
+    box->step[a] = 1;
+    box->cnt[a] = hi[a] - lo[a];
+    tiles *= (box->cnt[a] + tdim[a] - 1) / tdim[a];
+  }
+  box->tiles = tiles;
+}
+
+__device__ void set_empty_box(LatBox* box) {
+  for (int a = 0; a < 3; ++a) {
+    box->lo[a] = 0;
+    box->step[a] = 1;
+    box->cnt[a] = 0;
+  }
+  box->tiles = 0;
+}
+
+__global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (s >= P.B) return;
+  SelScan Q0;  // the decimated lattice (profile)
+  Q0.prof_off = static_cast<long long>(s) * P.stride;
+  for (int a = 0; a < 3; ++a) {
+    Q0.gn[a] = P.gn[a];
+    Q0.off[a] = P.off[a];
+    Q0.step[a] = P.step[a];
+    Q0.cnt[a] = P.cnt[a];
+  }
+  Q0.D = P.D;
+  Q0.max_iters = P.max_iters;
+  const float* prof = P.profile + Q0.prof_off;
+  ProgState* S = P.state + s;
+  uwb_result* R = P.out + s;
+  LatBox* next = P.next_boxes + s;
+  LatBox* fin = P.final_boxes + s;
+  const int dim = P.dim;
+  const long long Pd = static_cast<long long>(Q0.cnt[0]) * Q0.cnt[1] * Q0.cnt[2];
+
+  if (it == 1) {  // the decimated profile: record, maximum, validity
+    int* w = reinterpret_cast<int*>(R);
+    for (int j = lane; j < static_cast<int>(sizeof(uwb_result) / 4); j += 32) w[j] = 0;
+    float fmx = 0.f;
+    bool bad = false;
+    for (long long j = lane; j < Pd; j += 32) {
+      const float v = prof[j];
+      bad |= !isfinite(v);
+      fmx = fmaxf(fmx, v);
+    }
+    bad = __any_sync(0xFFFFFFFFu, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(0xFFFFFFFFu, fmx, o));
+    __syncwarp();
+    if (lane == 0) {
+      R->decim = Q0.D;
+      for (int a = 0; a < 3; ++a) {
+        R->offset[a] = Q0.off[a];
+        R->dcount[a] = Q0.cnt[a];
+        R->loc_idx[a] = -1;
+        S->Rlo[a] = 0;
+        S->Rhi[a] = Q0.gn[a];
+      }
+      R->profile_max = fmx;
+      S->pmax = fmx;
+      S->B_prev = S->W_prev = 0.0;
+      S->points = Pd;
+      S->iters = S->n_logged = 0;
+      S->stop = UWB_STOP_NONE;
+      S->active = !(bad || fmx == 0.f);
+      set_empty_box(next);
+      if (!S->active) {
+        R->status = bad ? UWB_ERR_NONFINITE : UWB_OK;
+        R->stop_reason = bad ? UWB_STOP_NONE : UWB_STOP_NO_TARGET;
+        set_empty_box(fin);
+      }
+    }
+    __syncwarp();
+  }
+  if (!S->active) {
+    if (lane == 0) set_empty_box(next);
+    return;
+  }
+  const uwb_rule& rule = P.rule;
+  const double pmax = S->pmax;
+  int Rlo[3], Rhi[3];
+  for (int a = 0; a < 3; ++a) {
+    Rlo[a] = S->Rlo[a];
+    Rhi[a] = S->Rhi[a];
+  }
+  // the lattice the child choice reads
+  SelScan Qc = Q0;
+  const float* cv = prof;
+  if (it >= 2) {
+    for (int a = 0; a < 3; ++a)
+      if (a < dim)
+        region_lattice(Rlo[a], Rhi[a], Q0.cnt[a], Qc.off[a], Qc.step[a], Qc.cnt[a]);
+    cv = P.lattice + Q0.prof_off;
+    const long long ni = static_cast<long long>(Qc.cnt[0]) * Qc.cnt[1] * Qc.cnt[2];
+    bool bad = false;
+    for (long long j = lane; j < ni; j += 32) bad |= !isfinite(cv[j]);
+    if (__any_sync(0xFFFFFFFFu, bad)) {
+      __syncwarp();
+      if (lane == 0) {
+        S->active = 0;
+        R->status = UWB_ERR_NONFINITE;
+        set_empty_box(next);
+        set_empty_box(fin);
+      }
+      return;
+    }
+  }
+  const Stats sr = box_stats(Qc, cv, pmax, lattice_in_box(Qc, Rlo, Rhi));
+  const double var_prev = sr.n > 0 ? sr.scatter / static_cast<double>(sr.n) : 0.0;
+  const int nchild = 1 << dim;
+  int mid[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) mid[a] = Rlo[a] + (Rhi[a] - Rlo[a]) / 2;
+  int best = -1, nvalid = 0;
+  double best_m = 0.0, second_m = 0.0;
+  int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+  for (int c = 0; c < nchild; ++c) {
+    int clo[3], chi[3];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim) {
+        const int bit = (c >> a) & 1;
+        clo[a] = bit ? mid[a] : Rlo[a];
+        chi[a] = bit ? Rhi[a] : mid[a];
+        if (chi[a] - clo[a] < rule.min_segment) ok = false;
+      } else {
+        clo[a] = Rlo[a];
+        chi[a] = Rhi[a];
+      }
+    }
+    if (!ok) continue;
+    const KBox kb = lattice_in_box(Qc, clo, chi);
+    if (kb.n == 0) continue;
+    const Stats sc = box_stats(Qc, cv, pmax, kb);
+    const double m =
+        decision_metric(rule.metric, sc.mean, sc.scatter / static_cast<double>(sc.n), var_prev);
+    if (nvalid == 0 || m > best_m) {
+      if (nvalid > 0) second_m = best_m;
+      best_m = m;
+      best = c;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        blo[a] = clo[a];
+        bhi[a] = chi[a];
+      }
+    } else if (nvalid == 1 || m > second_m) {
+      second_m = m;
+    }
+    ++nvalid;
+  }
+  const int li = it - 1;
+  bool stopped = false;
+  int stop = UWB_STOP_NONE, iters = it;
+  int Nlo[3] = {0, 0, 0}, Nhi[3] = {0, 0, 0};
+  if (nvalid == 0) {
+    stopped = true;
+    stop = UWB_STOP_MINSIZE;
+    iters = it - 1;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim) {
+        const int side = bhi[a] - blo[a];
+        const int grow = (side * rule.frame_num + rule.frame_den - 1) / rule.frame_den;
+        Nlo[a] = max(blo[a] - grow, 0);
+        Nhi[a] = min(bhi[a] + grow, Q0.gn[a]);
+      } else {
+        Nlo[a] = blo[a];
+        Nhi[a] = bhi[a];
+      }
+    }
+    // Eq. 6-7 on the decimated profile between the region and the framed child
+    const Stats sa = box_stats(Q0, prof, pmax, lattice_in_box(Q0, Rlo, Rhi));
+    const Stats sb = box_stats(Q0, prof, pmax, lattice_in_box(Q0, Nlo, Nhi));
+    const double Wi = sa.scatter + sb.scatter;
+    const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
+    const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
+                      static_cast<double>(sb.n) * (sb.mean - pooled) * (sb.mean - pooled);
+    double margin = 1e300;
+    bool cont = true;
+    if (it >= 2) {
+      const double mB = rel_gap(Bi, S->B_prev), mW = rel_gap(S->W_prev, Wi);
+      cont = (Bi > S->B_prev) && (Wi < S->W_prev);
+      margin = cont ? fmin(mB, mW) : fmax(-mB, -mW);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      R->child[li] = best;
+      R->n_children[li] = nvalid;
+      R->metric_top[li] = best_m;
+      R->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
+      for (int a = 0; a < 3; ++a) {
+        R->box_lo[li][a] = Nlo[a];
+        R->box_hi[li][a] = Nhi[a];
+      }
+      R->within[li] = Wi;
+      R->between[li] = Bi;
+      R->stop_margin[li] = margin;
+      S->n_logged = it;
+      S->B_prev = Bi;
+      S->W_prev = Wi;
+    }
+    if (!cont) {
+      stopped = true;
+      stop = UWB_STOP_METRIC;
+      iters = it - 1;
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Rlo[a] = Nlo[a];
+        Rhi[a] = Nhi[a];
+      }
+      if (it == P.max_iters) {
+        stopped = true;
+        stop = UWB_STOP_CAP;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      S->Rlo[a] = Rlo[a];
+      S->Rhi[a] = Rhi[a];
+    }
+    S->iters = iters;
+    if (stopped) {
+      S->active = 0;
+      R->status = UWB_OK;
+      R->iters = iters;
+      R->n_logged = S->n_logged;
+      R->stop_reason = stop;
+      for (int a = 0; a < 3; ++a) {
+        R->roi_lo[a] = Rlo[a];
+        R->roi_hi[a] = Rhi[a];
+      }
+      set_full_box(fin, Rlo, Rhi, P.tdim);
+      set_empty_box(next);
+    } else {
+      // the next iteration's lattice of the new region
+      int lo[3], st[3], cn[3];
+      long long n = 1;
+      for (int a = 0; a < 3; ++a) {
+        if (a < dim) {
+          region_lattice(Rlo[a], Rhi[a], Q0.cnt[a], lo[a], st[a], cn[a]);
+        } else {
+          lo[a] = 0;
+          st[a] = 1;
+          cn[a] = Q0.gn[a];
+        }
+        n *= cn[a];
+      }
+      int tiles = 1;
+      for (int a = 0; a < 3; ++a) {
+        next->lo[a] = lo[a];
+        next->step[a] = st[a];
+        next->cnt[a] = cn[a];
+        tiles *= (cn[a] + P.tdim[a] - 1) / P.tdim[a];
+      }
+      next->tiles = tiles;
+      S->points += n;
+    }
+  }
+}
+
 // Exclusive prefix sum of the per-scan tile counts (one CTA).
 __global__ void __launch_bounds__(1024) k_plan(const LatBox* boxes, int* prefix, int B) {
   __shared__ int warp_tot[32];
@@ -375,6 +669,8 @@ __global__ void k_finish(const FinishParams P, const int* status) {
   R->points_evaluated = F.Pd + roi;
   if (P.learn)  // learned localisation: coarse maps, plus the profile where Eq. 5 decided
     R->points_evaluated = (P.learn[s].fallback ? F.Pd : 0) + P.learn[s].map_points + roi;
+  if (P.prog)  // progressive loop: the profile and every region lattice imaged
+    R->points_evaluated = P.prog[s].points + roi;
   if (status && *status != UWB_OK) R->status = *status;
   if (key != 0ull && b.tiles > 0) {
     const long long lin = static_cast<long long>(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
@@ -427,6 +723,11 @@ cudaError_t launch_select(const SelParams& p, cudaStream_t st) {
 
 cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st) {
   k_plan<<<1, 1024, 0, st>>>(boxes, prefix, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prog_step(const ProgParams& p, int iteration, cudaStream_t st) {
+  k_prog_step<<<(p.B + 7) / 8, 256, 0, st>>>(p, iteration);
   return cudaGetLastError();
 }
 

@@ -2048,3 +2048,181 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
 }
 
 }  // extern "C"
+
+// ---- progressive re-evaluation (a variant of the ROI selection loop)
+namespace {
+
+struct ProgLayout {
+  size_t keys, status, profile, lattice, state, next_boxes, final_boxes, prefix, total;
+};
+
+ProgLayout prog_layout(int B, long long Pd) {
+  ProgLayout w;
+  size_t off = 0;
+  w.keys = off;
+  off += static_cast<size_t>(B) * 8;
+  w.status = off;
+  off = align256(off + 4);
+  w.profile = off;
+  off += align256(static_cast<size_t>(B) * static_cast<size_t>(Pd) * 4);
+  w.lattice = off;
+  off += align256(static_cast<size_t>(B) * static_cast<size_t>(Pd) * 4);
+  w.state = off;
+  off += align256(static_cast<size_t>(B) * sizeof(ProgState));
+  w.next_boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.final_boxes = off;
+  off += align256(static_cast<size_t>(B) * sizeof(LatBox));
+  w.prefix = off;
+  off += align256(static_cast<size_t>(B + 1) * 4);
+  w.total = off;
+  return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t uwb_localize_progressive_workspace(int batch, int M, int N, const uwb_grid* grid,
+                                          int beamformer, const uwb_rule* rule) {
+  if (batch < 1 || M < 1 || N < 1 || !grid || !rule || bf_of(beamformer) < 0 ||
+      check_rule(rule))
+    return 0;
+  return prog_layout(batch, decimate(*grid, *rule).Pd).total;
+}
+
+int uwb_localize_progressive(int batch, const float* traces, int M, int N,
+                             const float* antennas, long long antenna_stride,
+                             const uwb_grid* grid, double v, double fs, int window,
+                             int beamformer, const uwb_rule* rule, void* workspace,
+                             size_t ws_bytes, uwb_result* out, void* stream) {
+  Geo geo;
+  int st = check_common(batch, traces, M, N, antennas, grid, v, fs, window, &geo);
+  if (st) return st;
+  if ((st = check_rule(rule))) return st;
+  if (!out) return fail(UWB_ERR_ARG, "null result array");
+  if (antenna_stride < 0) return fail(UWB_ERR_ARG, "negative antenna stride");
+  const int bf = bf_of(beamformer);
+  if (bf < 0) return fail(UWB_ERR_ARG, "unknown beamformer %d", beamformer);
+  Variant var;
+  if ((st = pick_variant(bf, M, window, geo.g.dim, &var))) return st;
+  const Decim dc = decimate(geo.g, *rule);
+  const ProgLayout L = prog_layout(batch, dc.Pd);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(UWB_ERR_WORKSPACE, "workspace must be non-null and 256-byte aligned");
+  if (ws_bytes < L.total)
+    return fail(UWB_ERR_WORKSPACE, "workspace of %zu bytes < %zu needed", ws_bytes, L.total);
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
+  auto* status = reinterpret_cast<int*>(ws + L.status);
+  auto* profile = reinterpret_cast<float*>(ws + L.profile);
+  auto* lattice = reinterpret_cast<float*>(ws + L.lattice);
+  auto* state = reinterpret_cast<ProgState*>(ws + L.state);
+  auto* next_boxes = reinterpret_cast<LatBox*>(ws + L.next_boxes);
+  auto* final_boxes = reinterpret_cast<LatBox*>(ws + L.final_boxes);
+  auto* prefix = reinterpret_cast<int*>(ws + L.prefix);
+  cudaError_t e = cudaMemsetAsync(ws + L.keys, 0, L.status + 4 - L.keys, cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const int span = pick_span(var, M);
+  CUtensorMap map;
+  const int use_tma = encode_traces(geo, traces, span, &map);
+  PhaseTimer timer(cs);
+  timer.mark();
+
+  // 1. the decimated profile (Section III, "Spatial Decimation")
+  const double dstep[3] = {static_cast<double>(dc.step[0]), static_cast<double>(dc.step[1]),
+                           static_cast<double>(dc.step[2])};
+  const int pc[3] = {dc.cnt[0], dc.cnt[1], dc.cnt[2]};
+  const long long lattice_work = static_cast<long long>(batch) * tiles_of(pc, var.tdim);
+  {
+    ImgParams p1 = base_params(geo, traces, antennas, antenna_stride, var, span, use_tma, status);
+    for (int a = 0; a < 3; ++a) {
+      p1.uni.lo[a] = dc.off[a];
+      p1.uni.step[a] = dc.step[a];
+      p1.uni.cnt[a] = dc.cnt[a];
+    }
+    p1.uni.tiles = tiles_of(p1.uni.cnt, var.tdim);
+    p1.compact = profile;
+    p1.compact_stride = dc.Pd;
+    if ((st = run_image_kernel(*dev, var, p1, &map, lattice_work, dstep, cs))) return st;
+  }
+  timer.mark();
+
+  // 2. the selection loop: one step kernel per iteration, each followed by
+  // the image pass over every active scan's next region lattice
+  ProgParams pp;
+  memset(&pp, 0, sizeof pp);
+  pp.profile = profile;
+  pp.lattice = lattice;
+  pp.stride = dc.Pd;
+  pp.B = batch;
+  pp.dim = geo.g.dim;
+  for (int a = 0; a < 3; ++a) {
+    pp.gn[a] = geo.g.n[a];
+    pp.off[a] = dc.off[a];
+    pp.step[a] = dc.step[a];
+    pp.cnt[a] = dc.cnt[a];
+    pp.tdim[a] = var.tdim[a];
+  }
+  pp.D = dc.D;
+  pp.max_iters = dc.max_iters;
+  pp.rule = *rule;
+  pp.state = state;
+  pp.next_boxes = next_boxes;
+  pp.final_boxes = final_boxes;
+  pp.out = out;
+  for (int it = 1; it <= dc.max_iters; ++it) {
+    if ((e = launch_prog_step(pp, it, cs)) != cudaSuccess) return cuda_fail(e, "step launch");
+    if (it == dc.max_iters) break;
+    if ((e = launch_plan(next_boxes, prefix, batch, cs)) != cudaSuccess)
+      return cuda_fail(e, "plan launch");
+    ImgParams pl = base_params(geo, traces, antennas, antenna_stride, var, span, use_tma, status);
+    pl.boxes = next_boxes;
+    pl.prefix = prefix;
+    pl.uni.tiles = 1;
+    pl.compact = lattice;
+    pl.compact_stride = dc.Pd;
+    if ((st = run_image_kernel(*dev, var, pl, &map, lattice_work, dstep, cs))) return st;
+  }
+  if ((e = launch_plan(final_boxes, prefix, batch, cs)) != cudaSuccess)
+    return cuda_fail(e, "plan launch");
+  timer.mark();
+
+  // 3. final region at full resolution + argmax
+  {
+    ImgParams p2 = base_params(geo, traces, antennas, antenna_stride, var, span, use_tma, status);
+    p2.boxes = final_boxes;
+    p2.prefix = prefix;
+    p2.uni.tiles = 1;
+    p2.keys = keys;
+    int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
+    const double step1[3] = {1, 1, 1};
+    if ((st = run_image_kernel(*dev, var, p2, &map,
+                               static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                               cs)))
+      return st;
+  }
+  timer.mark();
+  FinishParams fp;
+  memset(&fp, 0, sizeof fp);
+  fp.prog = state;
+  fp.keys = keys;
+  fp.boxes = final_boxes;
+  fp.out = out;
+  fp.B = batch;
+  for (int a = 0; a < 3; ++a) {
+    fp.gn[a] = geo.g.n[a];
+    fp.org[a] = geo.g.origin[a];
+    fp.pit[a] = geo.g.pitch[a];
+  }
+  fp.Pd = dc.Pd;
+  if ((e = launch_finish(fp, status, cs)) != cudaSuccess) return cuda_fail(e, "finish launch");
+  timer.mark();
+  timer.commit();
+  return UWB_OK;
+}
+
+}  // extern "C"

@@ -162,8 +162,35 @@ struct LearnState {
   int map_points;            // coarse-map points evaluated so far
 };
 
+// Per-scan state of the progressive re-evaluation loop.
+struct ProgState {
+  int Rlo[3], Rhi[3];        // current region
+  double pmax;               // maximum of the decimated profile
+  double B_prev, W_prev;     // Eq. 6-7 of the previous iteration
+  long long points;          // focal points imaged so far (profile + region lattices)
+  int active, iters, n_logged, stop;
+};
+
+// One iteration of the progressive loop for every scan (one warp per scan).
+struct ProgParams {
+  const float* profile;      // [B][Pd] decimated energies
+  const float* lattice;      // [B][Pd] energies of each scan's region lattice (iteration >= 2)
+  long long stride;          // Pd
+  int B, dim;
+  int gn[3];
+  int off[3], step[3], cnt[3];  // decimated lattice
+  int D, max_iters;
+  uwb_rule rule;
+  int tdim[3];               // tile shape of the image kernel
+  ProgState* state;
+  LatBox* next_boxes;        // out: region lattice of the next iteration (cnt 0: none)
+  LatBox* final_boxes;       // out: final region of scans that stopped
+  uwb_result* out;
+};
+
 struct FinishParams {
   const LearnState* learn;   // learned localisation: per-scan state, else nullptr
+  const ProgState* prog;     // progressive loop: per-scan state, else nullptr
   const FinScan* scans;      // ragged: [B] (device), else nullptr
   const unsigned long long* keys;
   const LatBox* boxes;
@@ -191,6 +218,7 @@ int occupancy_image_dmas(int v, bool ms, int threads, size_t smem);
 int occupancy_image_literal(int v, int threads, size_t smem);
 
 cudaError_t launch_select(const SelParams& p, cudaStream_t st);
+cudaError_t launch_prog_step(const ProgParams& p, int iteration, cudaStream_t st);
 cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t st);
 cudaError_t launch_keys_to_index(unsigned long long* keys, int B, cudaStream_t st);

@@ -474,3 +474,108 @@ def test_multistatic_scene_locates_its_tumour():
     r = oracle.localize_multistatic(sc["traces"], ch, sc["antennas"], g, cfg.v, cfg.fs,
                                     cfg.window, oracle.DAS)
     assert np.linalg.norm(np.array(r["loc_xyz"]) - sc["tumors"][0]) < 2 * g["pitch"][0]
+
+
+# ------------------------------------------------- progressive re-evaluation (variant)
+
+@pytest.mark.parametrize("lo,hi,c0,want", [
+    (0, 512, 18, (9, 29, 18)),     # step ceil(512/18) = 29; (511 mod 29) // 2 = 9
+    (128, 320, 18, (130, 11, 18)),  # side 192: step 11, (191 mod 11) // 2 = 2
+    (5, 21, 18, (5, 1, 16)),        # a side below c0 is imaged at full resolution
+    (0, 37, 18, (0, 3, 13)),
+])
+def test_region_lattice_hand_values(lo, hi, c0, want):
+    assert oracle.region_lattice(lo, hi, c0) == want
+
+
+def test_region_lattice_stays_inside_and_below_the_count():
+    rng = np.random.default_rng(5)
+    for _ in range(500):
+        lo = int(rng.integers(0, 300))
+        hi = lo + int(rng.integers(1, 400))
+        c0 = int(rng.integers(1, 40))
+        first, step, cnt = oracle.region_lattice(lo, hi, c0)
+        last = first + step * (cnt - 1)
+        assert lo <= first and last < hi and cnt <= c0 and step >= 1
+        # one more point would leave the range, and the lattice is centred
+        assert last + step >= hi
+        assert abs((first - lo) - (hi - 1 - last)) <= step
+
+
+def _scene_for_progressive(seed, n=(24, 20), M=6):
+    rng = np.random.default_rng(seed)
+    ang = np.sort(rng.uniform(0, 2 * np.pi, M))
+    ants = np.stack([0.05 * np.cos(ang), 0.05 * np.sin(ang), np.zeros(M)], 1).astype(np.float32)
+    pitch = 0.06 / n[0]
+    grid = {"dim": 2, "n": [n[0], n[1], 1], "origin": [-0.03 + pitch / 2, -0.025, 0.0],
+            "pitch": [pitch, pitch, 1.0]}
+    pts = [[rng.uniform(-0.02, 0.02), rng.uniform(-0.015, 0.015), 0.0]]
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], n_antennas=M, snr_db=None)
+    tr = phantom.synthesize(cfg, np.array(pts), np.array([1.0]), np.array([cfg.eps_r]),
+                            ants.astype(np.float64)).astype(np.float32)
+    tr += rng.normal(0, 0.05, tr.shape).astype(np.float32)
+    return tr, ants, grid, cfg
+
+
+SAME_KEYS = ("status", "iters", "n_logged", "stop_reason", "roi_lo", "roi_hi", "loc_idx",
+             "child", "n_children", "box_lo", "box_hi")
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_progressive_on_a_full_resolution_lattice_is_the_paper_method(seed, bf):
+    # D = 1: every region lattice is the region at full resolution, the same
+    # points the paper's loop reads from its (full-resolution) profile
+    tr, ants, grid, cfg = _scene_for_progressive(seed)
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, min_segment=2)
+    a = oracle.localize(tr, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule)
+    b = oracle.localize_progressive(tr, ants, grid, cfg.v, cfg.fs, cfg.window, bf, rule)
+    for k in SAME_KEYS:
+        assert a[k] == b[k], k
+    np.testing.assert_allclose(b["metric_top"], a["metric_top"], rtol=1e-12)
+    np.testing.assert_allclose(b["between"], a["between"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(b["within"], a["within"], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_progressive_first_iteration_is_the_paper_method(seed):
+    cfg = phantom.CONFIGS["dmas2d_512"]
+    cfg = phantom.with_changes(cfg, grid_n=(96, 96, 1), extent=0.08)
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 70 + seed)
+    rule = oracle.make_rule(max_iters=1)
+    a = oracle.localize(sc["traces"], sc["antennas"], cfg.grid(), cfg.v, cfg.fs, cfg.window,
+                        oracle.DAS, rule)
+    b = oracle.localize_progressive(sc["traces"], sc["antennas"], cfg.grid(), cfg.v, cfg.fs,
+                                    cfg.window, oracle.DAS, rule)
+    for k in SAME_KEYS + ("points_evaluated",):
+        assert a[k] == b[k], k
+
+
+def test_progressive_points_are_the_lattices_it_imaged():
+    cfg = phantom.with_changes(phantom.CONFIGS["dmas2d_512"], grid_n=(128, 128, 1), extent=0.08)
+    sc = phantom.make_scan(cfg, phantom.BASE_SEED + 91)
+    g = cfg.grid()
+    r = oracle.localize_progressive(sc["traces"], sc["antennas"], g, cfg.v, cfg.fs, cfg.window,
+                                    oracle.DAS, oracle.make_rule())
+    c0 = r["dcount"]
+    pts = c0[0] * c0[1]
+    for l in range(1, r["n_logged"]):       # iterations 2.. image the region before them
+        lo, hi = r["box_lo"][l - 1], r["box_hi"][l - 1]
+        pts += oracle.region_lattice(lo[0], hi[0], c0[0])[2] * \
+            oracle.region_lattice(lo[1], hi[1], c0[1])[2]
+    pts += (r["roi_hi"][0] - r["roi_lo"][0]) * (r["roi_hi"][1] - r["roi_lo"][1])
+    assert r["points_evaluated"] == pts
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_progressive_noiseless_scatterer_at_its_pixel(bf):
+    cfg = phantom.with_changes(phantom.CONFIGS["dmas2d_512"], grid_n=(128, 128, 1), extent=0.08,
+                               snr_db=None, n_clutter=0)
+    g = cfg.grid()
+    ants = phantom.antenna_positions(cfg).astype(np.float32)
+    for ix, iy in [(41, 87), (100, 20), (64, 63)]:
+        p = [g["origin"][0] + ix * g["pitch"][0], g["origin"][1] + iy * g["pitch"][1], 0.0]
+        tr = phantom.point_scatterer_traces(cfg, [p], [1.0])
+        r = oracle.localize_progressive(tr, ants, g, cfg.v, cfg.fs, cfg.window, bf,
+                                        oracle.make_rule())
+        assert r["loc_idx"][:2] == [ix, iy]
