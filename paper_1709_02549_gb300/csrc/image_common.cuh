@@ -205,8 +205,8 @@ __device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const ScanDesc* _
   const int off = __float_as_int(nf.x) + k0;
   LitRaw r;
   r.f = nf.y;
-  if (STAGED) {
-    const float* row = sTr + i * P.span + off;
+  if (STAGED) {  // off is the word index into the staged window (row i included)
+    const float* row = sTr + off;
     r.y0 = row[0];
     r.y1 = row[1];
     r.y2 = row[2];
@@ -236,7 +236,10 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
                                                 const float4* __restrict__ sAnt,
                                                 float2* __restrict__ sNF, int nlo, int cl_lo,
                                                 int cl_hi, float px, float py, float pz) {
-  const int T = blockDim.x, tid = threadIdx.x;
+  // the literal kernel always runs 128 threads: a constant T turns the
+  // per-antenna (offset, fraction) addresses into immediate offsets
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX>::threads;
+  const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
   const float hf = static_cast<float>(P.h);
@@ -254,7 +257,9 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
-      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo;
+      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo + i * P.span;
+    } else if (STAGED) {
+      n0 = i * P.span;  // rows M..MMAX-1 of the staged window are zero
     }
     sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
   }
@@ -302,8 +307,8 @@ __device__ __forceinline__ LitRaw4 lit_load4(const ImgParams& P, const ScanDesc*
   const int off = __float_as_int(nf.x) + k0;
   LitRaw4 r;
   r.f = nf.y;
-  if (STAGED) {
-    const float* row = sTr + i * P.span + off;
+  if (STAGED) {  // off is the word index into the staged window (row i included)
+    const float* row = sTr + off;
     r.y0 = row[0];
     r.y1 = row[1];
     r.y2 = row[2];
@@ -329,7 +334,10 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
                                                  const float4* __restrict__ sAnt,
                                                  float2* __restrict__ sNF, int nlo, int cl_lo,
                                                  int cl_hi, float px, float py, float pz) {
-  const int T = blockDim.x, tid = threadIdx.x;
+  // the literal kernel always runs 128 threads: a constant T turns the
+  // per-antenna (offset, fraction) addresses into immediate offsets
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX>::threads;
+  const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
   const float hf = static_cast<float>(P.h);
@@ -346,7 +354,9 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
-      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo;
+      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo + i * P.span;
+    } else if (STAGED) {
+      n0 = i * P.span;  // rows M..MMAX-1 of the staged window are zero
     }
     sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
   }
