@@ -205,11 +205,16 @@ __device__ __forceinline__ LitRaw lit_load(const ImgParams& P, const ScanDesc* _
   const int off = __float_as_int(nf.x) + k0;
   LitRaw r;
   r.f = nf.y;
-  if (STAGED) {  // off is the word index into the staged window (row i included)
-    const float* row = sTr + off;
-    r.y0 = row[0];
-    r.y1 = row[1];
-    r.y2 = row[2];
+  if (STAGED) {
+    // nf.x holds the shared-window byte address of sample 0 of this antenna's
+    // window: three loads at immediate offsets, no per-antenna address scaling
+    const uint32_t a = __float_as_uint(nf.x) + 4u * static_cast<uint32_t>(k0);
+    asm volatile(
+        "ld.shared.f32 %0, [%3];\n\t"
+        "ld.shared.f32 %1, [%3+4];\n\t"
+        "ld.shared.f32 %2, [%3+8];"
+        : "=f"(r.y0), "=f"(r.y1), "=f"(r.y2)
+        : "r"(a));
   } else if (i < scan_M<RG>(P, sS)) {
     const ScanDesc S = *sS;
     r.y0 = sample_at(S, P.dtype, i, off);
@@ -257,9 +262,12 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
-      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo + i * P.span;
+      if (STAGED)
+        n0 = static_cast<int>(smem_u32(sTr)) +
+             4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
     } else if (STAGED) {
-      n0 = i * P.span;  // rows M..MMAX-1 of the staged window are zero
+      // rows M..MMAX-1 of the staged window are zero
+      n0 = static_cast<int>(smem_u32(sTr)) + 4 * i * P.span;
     }
     sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
   }
@@ -307,13 +315,16 @@ __device__ __forceinline__ LitRaw4 lit_load4(const ImgParams& P, const ScanDesc*
   const int off = __float_as_int(nf.x) + k0;
   LitRaw4 r;
   r.f = nf.y;
-  if (STAGED) {  // off is the word index into the staged window (row i included)
-    const float* row = sTr + off;
-    r.y0 = row[0];
-    r.y1 = row[1];
-    r.y2 = row[2];
-    r.y3 = row[3];
-    r.y4 = row[4];
+  if (STAGED) {  // nf.x: shared-window byte address of the antenna's window (see lit_load)
+    const uint32_t a = __float_as_uint(nf.x) + 4u * static_cast<uint32_t>(k0);
+    asm volatile(
+        "ld.shared.f32 %0, [%5];\n\t"
+        "ld.shared.f32 %1, [%5+4];\n\t"
+        "ld.shared.f32 %2, [%5+8];\n\t"
+        "ld.shared.f32 %3, [%5+12];\n\t"
+        "ld.shared.f32 %4, [%5+16];"
+        : "=f"(r.y0), "=f"(r.y1), "=f"(r.y2), "=f"(r.y3), "=f"(r.y4)
+        : "r"(a));
   } else if (i < scan_M<RG>(P, sS)) {
     const ScanDesc S = *sS;
     r.y0 = sample_at(S, P.dtype, i, off);
@@ -354,9 +365,12 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
-      if (STAGED) n0 = min(max(n0, cl_lo), cl_hi) - nlo + i * P.span;
+      if (STAGED)
+        n0 = static_cast<int>(smem_u32(sTr)) +
+             4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
     } else if (STAGED) {
-      n0 = i * P.span;  // rows M..MMAX-1 of the staged window are zero
+      // rows M..MMAX-1 of the staged window are zero
+      n0 = static_cast<int>(smem_u32(sTr)) + 4 * i * P.span;
     }
     sNF[i * T + tid] = make_float2(__int_as_float(n0), f);
   }
