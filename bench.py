@@ -37,6 +37,8 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # Derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz max SM clock.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+# Derived shared-load peak: one 128-byte wavefront per clock per SM.
+LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 
 # DRAM traffic of the final-region literal-DMAS kernel per scan, from an ncu
 # capture of the kernel sources whose hash is stored alongside (dmas2d_512,
@@ -655,10 +657,16 @@ def main():
     if NCU_TRAFFIC["sha"] == sha and bf == 2:
         # scaled from a 256-scan capture by scans: the staged windows dominate
         traffic = NCU_TRAFFIC["bytes_per_scan"] * B
+    # the same GPU's measured ceilings (paired-FMA chains; conflict-free shared loads)
+    fma_meas, lds_meas = uwb.uwb_measure_peaks()
     roofline = {
         "bound": "alu",
         "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (achieved_tflops / FP32_PEAK_TFLOPS) if achieved_tflops else None,
+        "measured_peak": fma_meas,
+        "frac_of_measured": (achieved_tflops / fma_meas) if achieved_tflops else None,
+        "measured_peak_source": "uwb_measure_peaks: independent __ffma2_rn chains, "
+                                "8 CTAs x 256 threads per SM",
         "traffic": traffic,
         "kernel": f"k_image<{['DAS', 'DMAS', 'DMAS_LITERAL'][bf]}> final-region pass",
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
@@ -667,6 +675,22 @@ def main():
         "phase_ms_per_step": [p / max(calls, 1) for p in phase_ms],
         "kernel_sha": sha,
     }
+    if bf != 2:
+        # DAS and identity DMAS: bound by shared-memory loads. Algorithmic
+        # wavefronts per focal point: M (W + 1) conflict-free word loads per
+        # warp of 32 points, i.e. M (W + 1) / 32 per point.
+        wf = float(roi_points.sum()) * M * (cfg.window + 1) / 32.0
+        achieved_gwf = wf / (final_ms / 1e3) / 1e9 if final_ms > 0 else None
+        roofline.update({
+            "bound": "smem", "achieved": achieved_gwf, "peak": LDS_PEAK_GWF,
+            "unit": "G wavefronts/s",
+            "frac": achieved_gwf / LDS_PEAK_GWF if achieved_gwf else None,
+            "measured_peak": lds_meas / 1e9,
+            "frac_of_measured": achieved_gwf / (lds_meas / 1e9) if achieved_gwf else None,
+            "measured_peak_source": "uwb_measure_peaks: conflict-free 32-bit shared loads",
+            "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz",
+            "wavefronts_per_launch": wf, "traffic": None,
+            "tflops_achieved": achieved_tflops})
 
     # ---- full-resolution GPU images of the same scans (same beamformer) ----
     P = int(np.prod(grid["n"]))

@@ -362,6 +362,14 @@ int uwb_device_status(int clear);
 /* Text of the last error of the calling thread ("" if none). */
 const char* uwb_last_error(void);
 
+/* Measurement aid for roofline fractions (no counterpart in the paper):
+ * microbenchmarks of the two on-chip peaks the image kernels are bound by, on
+ * the current device, synchronously. fp32_tflops: independent chains of paired
+ * FP32 FMAs (2 FLOP per FMA); shared_wavefronts_per_s: conflict-free 32-bit
+ * shared-memory loads, one 128-byte wavefront per warp instruction. Returns
+ * UWB_OK or UWB_ERR_CUDA. */
+int uwb_measure_peaks(double* fp32_tflops, double* shared_wavefronts_per_s);
+
 /* Progressive re-evaluation: a variant of uwb_localize_batch (the paper's
  * selection loop reads only the decimated profile). Iteration 1 is the
  * paper's. Every later iteration first images again the region being split on

@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
             "uwb_phase_timing": (i, [i]),
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
             "uwb_last_error": (ctypes.c_char_p, []),
+            "uwb_measure_peaks": (i, [ctypes.POINTER(ctypes.c_double)] * 2),
             "uwb_cnn_selftest": (i, [ctypes.POINTER(ctypes.c_int)]),
             "uwb_cnn_pack": (i, [vp, vp, vp]),
             "uwb_cnn_forward": (i, [vp, vp, i, vp, vp]),
@@ -642,4 +643,11 @@ def uwb_localize_learned(traces, antennas, grid, v, fs, window, beamformer, rule
                                       _ptr(packed, "packed"), float(threshold), int(levels),
                                       _ptr(workspace, "workspace"), _nbytes(workspace),
                                       _ptr(out, "out"), _stream(stream)), "uwb_localize_learned")
+
+
+def uwb_measure_peaks():
+    """(FP32 TFLOP/s of paired-FMA chains, conflict-free shared-load wavefronts/s)."""
+    t, w = ctypes.c_double(), ctypes.c_double()
+    _check(lib().uwb_measure_peaks(ctypes.byref(t), ctypes.byref(w)), "uwb_measure_peaks")
+    return t.value, w.value
 

@@ -14,7 +14,7 @@ INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libuwb.so"
 SOURCES = ["uwb_api.cu", "select_kernels.cu", "image_das.cu", "image_dmas.cu",
-           "image_literal.cu", "cnn.cu"]
+           "image_literal.cu", "cnn.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}",
                 f"-I{CSRC}"]

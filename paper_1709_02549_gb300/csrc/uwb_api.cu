@@ -2226,3 +2226,16 @@ int uwb_localize_progressive(int batch, const float* traces, int M, int N,
 }
 
 }  // extern "C"
+
+extern "C" {
+
+int uwb_measure_peaks(double* fp32_tflops, double* shared_wavefronts_per_s) {
+  if (!fp32_tflops || !shared_wavefronts_per_s) return fail(UWB_ERR_ARG, "null output");
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  cudaError_t e = measure_peaks(dev->sms, fp32_tflops, shared_wavefronts_per_s);
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "peak microbenchmarks");
+}
+
+}  // extern "C"
