@@ -38,11 +38,25 @@ namespace uwb {
 // Bounded waits: a staging wait gives up after this many try_wait probes.
 constexpr long kWaitProbes = 1L << 24;
 
+// Antenna-to-focal-point distance with the hardware square-root
+// approximation (sqrt.approx.f32, relative error about one float ulp): the
+// IEEE-rounded sqrtf adds a branch and several instructions per antenna, and
+// one ulp of distance is 1e-5 samples of delay at these scales, far below the
+// image tolerance.
+__device__ __forceinline__ float dist3(float dx, float dy, float dz) {
+  const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float d;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(d) : "f"(q));
+  return d;
+}
+
 template <int BF, int V>
 struct KernelShape {
   static constexpr int threads = (BF == BF_DMAS_LIT) ? 128 : 256;
-  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas
-  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : (BF == BF_DAS ? (V <= 20 ? 4 : 3) : (V <= 20 ? 3 : 2));
+  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas; DAS
+  // 3 and identity DMAS 2, where their window accumulators fit registers
+  // without spilling (measured faster than one more CTA with spills)
+  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : (BF == BF_DAS ? 3 : 2);
 };
 
 // Per-scan quantities: ragged instances (RG) read the scan's descriptor in
@@ -109,7 +123,7 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* 
     for (int i = 0; i < M; ++i) {
       const float4 a = sAnt[i];
       const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
-      sD[i * T + tid] = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      sD[i * T + tid] = dist3(dx, dy, dz);
     }
   }
   const float half_k = 0.5f * kscale;
@@ -131,7 +145,7 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* 
         const float dx = px - a.x;
         const float dy = py - a.y;
         const float dz = pz - a.z;
-        const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        const float d = dist3(dx, dy, dz);
         t = fmaf(d, kscale, -hoff);
       }
       const float fl = floorf(t);
@@ -257,7 +271,7 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
       const float dx = px - a.x;
       const float dy = py - a.y;
       const float dz = pz - a.z;
-      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float d = dist3(dx, dy, dz);
       const float t = fmaf(d, kscale, -hf);
       const float fl = floorf(t);
       f = t - fl;
@@ -360,7 +374,7 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
       const float dx = px - a.x;
       const float dy = py - a.y;
       const float dz = pz - a.z;
-      const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      const float d = dist3(dx, dy, dz);
       const float t = fmaf(d, kscale, -hf);
       const float fl = floorf(t);
       f = t - fl;
