@@ -276,7 +276,8 @@ def run_ragged(args, uwb, torch):
     oracle.build()
     B = args.batch
     bf = BEAMFORMERS[args.beamformer] if args.beamformer != "literal" else 1
-    cfgs = phantom.ragged_configs(B)
+    dim = args.ragged_dim
+    cfgs = phantom.ragged_configs(B, dim=dim)
     scans = [phantom.make_scan(c, phantom.BASE_SEED + 200000 + k) for k, c in enumerate(cfgs)]
     dev_tr = [torch.from_numpy(sc["traces"]).cuda() for sc in scans]
     dev_an = [torch.from_numpy(sc["antennas"]).cuda() for sc in scans]
@@ -287,8 +288,9 @@ def run_ragged(args, uwb, torch):
     out = {"metric": "localised scans/s, ragged batches (plan API)", "unit": "scans/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "data": "synthetic", "beamformer": args.beamformer if bf else "das",
-           "config": {"workload": f"{B} uneven scans: 16-96 antennas, 1024-4096 samples, "
-                                  "128^2-1024^2 grids over 12 cm, 50 clutter, 15 dB",
+           "config": {"workload": f"{B} uneven scans: 16-96 antennas, 1024-4096 samples, " +
+                                  ("128^2-1024^2 grids over 12 cm, 50 clutter, 15 dB" if dim == 2
+                                   else "128^3 grids over 10 cm, 100 clutter, 15 dB"),
                       "points_total": int(sum(np.prod(c.grid_n) for c in cfgs))},
            "by_dtype": {}}
     for name, tdt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
@@ -324,9 +326,12 @@ def run_ragged(args, uwb, torch):
         img_ms = timed(lambda: plan.images(imgs, peak))
         recs = uwb.results_from_device(res)
         pk = peak.cpu().numpy()
-        agree = float(np.mean([list(recs["loc_idx"][k][:2]) ==
-                               [int(pk[k] % cfgs[k].grid_n[0]), int(pk[k] // cfgs[k].grid_n[0])]
-                               for k in range(B)]))
+
+        def unravel(k, lin):
+            n = list(cfgs[k].grid_n) + [1] * (3 - len(cfgs[k].grid_n))
+            return [int(lin % n[0]), int((lin // n[0]) % n[1]), int(lin // (n[0] * n[1]))]
+
+        agree = float(np.mean([list(recs["loc_idx"][k]) == unravel(k, pk[k]) for k in range(B)]))
         # error per image against the FP64 oracle on the float32 traces, at 64
         # sampled focal points and the argmax of each of the first 8 scans
         errs = []
@@ -334,13 +339,13 @@ def run_ragged(args, uwb, torch):
         for k in range(min(8, B)):
             c, sc = cfgs[k], scans[k]
             g = c.grid()
-            gx, gy = c.grid_n[0], c.grid_n[1]
-            pts = rng.integers(0, [gx, gy], size=(64, 2)).tolist() + [[int(pk[k] % gx),
-                                                                       int(pk[k] // gx)]]
-            got = np.array([im[plan.image_offset(k) + x + gx * y] for x, y in pts])
+            n = list(c.grid_n) + [1] * (3 - len(c.grid_n))
+            pts = rng.integers(0, n, size=(64, 3)).tolist() + [unravel(k, pk[k])]
+            got = np.array([im[plan.image_offset(k) + x + n[0] * (y + n[1] * z)]
+                            for x, y, z in pts])
             ref = np.array([oracle.image(sc["traces"], sc["antennas"], g, c.v, c.fs, c.window,
-                                         oracle.DAS if bf == 0 else oracle.DMAS, lo=[x, y, 0],
-                                         cnt=[1, 1, 1])[0, 0, 0] for x, y in pts])
+                                         oracle.DAS if bf == 0 else oracle.DMAS, lo=[x, y, z],
+                                         cnt=[1, 1, 1])[0, 0, 0] for x, y, z in pts])
             errs.append(float(np.max(np.abs(got - ref)) / max(ref.max(), 1e-300)))
         out["by_dtype"][name] = {
             "value": B / (loc_ms / 1e3), "ms_per_step": loc_ms, "tile": tile,
@@ -351,7 +356,7 @@ def run_ragged(args, uwb, torch):
         }
         plan.close()
     out["value"] = out["by_dtype"]["f32"]["value"]
-    uwb.uwb_set_tile_shape(bf, 2, None)
+    uwb.uwb_set_tile_shape(bf, dim, None)
     return out
 
 
@@ -562,6 +567,8 @@ def main():
                     help="presence: the two-decimation tumour-presence test; ragged: a batch "
                          "of uneven scans through the plan API; learned: the learned segment "
                          "proposal against the plain framework")
+    ap.add_argument("--ragged-dim", type=int, default=2, choices=[2, 3],
+                    help="ragged mode: 2-D grids (128^2-1024^2) or 128^3 cubes")
     ap.add_argument("--decimation2", type=int, default=0,
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()

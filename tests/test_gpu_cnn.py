@@ -333,3 +333,34 @@ def test_trained_network_gains_over_the_framework(gpu):
     t_l = timed(lambda: wl.learned(tr, pk, th, gpu.UWB_DMAS_LITERAL))
     t_f = timed(lambda: wl.framework(tr, gpu.UWB_DMAS_LITERAL))
     assert t_l * 2.0 < t_f, (t_l, t_f)
+
+
+def test_learned_localisation_replays_in_a_cuda_graph(gpu):
+    from paper_1709_02549_gb300 import proposal
+    theta, record = proposal.load()
+    wl = proposal.Workload("dmas2d_512")
+    _, pk = packed_of(gpu, theta)
+    b = phantom.make_batch(wl.cfg, 6, proposal.EVAL_FIRST_SCAN + 90_000)
+    tr = dev(b["traces"])
+    B = tr.shape[0]
+    ws = torch.empty(gpu.uwb_localize_learned_workspace(B, wl.grid, wl.rule), dtype=torch.uint8,
+                     device="cuda")
+    direct = torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+
+    def run(out, stream=None):
+        gpu.uwb_localize_learned(tr, wl.ants, wl.grid, wl.cfg.v, wl.cfg.fs, wl.cfg.window,
+                                 gpu.UWB_DMAS_LITERAL, wl.rule, pk, record["threshold"], 2, ws,
+                                 out, stream)
+
+    run(direct)
+    torch.cuda.synchronize()
+    graphed = torch.zeros_like(direct)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        run(graphed, s)
+    for _ in range(2):
+        graphed.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(graphed, direct)

@@ -74,3 +74,31 @@ def test_progressive_edge_cases(gpu):
     assert res[1]["stop_reason"] == gpu.UWB_STOP_NO_TARGET and res[1]["loc_idx"] == [-1, -1, -1]
     assert res[2]["status"] == gpu.UWB_ERR_NONFINITE
     gpu.uwb_device_status(clear=True)
+
+
+def test_progressive_replays_in_a_cuda_graph(gpu):
+    cfg = phantom.CONFIGS["dmas2d_512"]
+    b = phantom.make_batch(cfg, 5, 70)
+    tr, ants = dev(b["traces"]), dev(b["antennas"].astype(np.float32))
+    g, rule = cfg.grid(), gpu.uwb_default_rule()
+    B, M, N = b["traces"].shape
+    ws = torch.empty(gpu.uwb_localize_progressive_workspace(B, M, N, g, 2, rule),
+                     dtype=torch.uint8, device="cuda")
+    direct = torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+
+    def run(out, stream=None):
+        gpu.uwb_localize_progressive(tr, ants, g, cfg.v, cfg.fs, cfg.window, 2, rule, ws, out,
+                                     stream)
+
+    run(direct)
+    torch.cuda.synchronize()
+    graphed = torch.zeros_like(direct)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        run(graphed, s)
+    for _ in range(2):
+        graphed.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(graphed, direct)
