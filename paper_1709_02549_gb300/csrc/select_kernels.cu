@@ -112,6 +112,102 @@ __device__ double decision_metric(int metric, double mu, double var, double var_
   return (1.0 - a) * mu + a * var;
 }
 
+// Child choice of one iteration (Eq. 5 over the 2^dim children of the region
+// [Rlo, Rhi)), all children at once: lane group c = lane / G (G = 32 / 2^dim
+// lanes) sums child c's lattice points, the group's sums are reduced within
+// the group, and every lane then runs the choice over the children in index
+// order (first maximum wins; the runner-up is kept for the margin).
+struct Choice {
+  int best, nvalid;
+  double best_m, second_m;
+  int blo[3], bhi[3];
+};
+
+__device__ Choice choose_child(const SelScan& Q, const float* vals, double pmax, const int Rlo[3],
+                               const int Rhi[3], int dim, const uwb_rule& rule,
+                               double var_prev) {
+  const int lane = threadIdx.x & 31;
+  const int nchild = 1 << dim;
+  const int G = 32 / nchild;
+  const int c = lane / G, r = lane % G;
+  int mid[3], clo[3], chi[3];
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mid[a] = Rlo[a] + (Rhi[a] - Rlo[a]) / 2;
+    if (a < dim) {
+      const int bit = (c >> a) & 1;
+      clo[a] = bit ? mid[a] : Rlo[a];
+      chi[a] = bit ? Rhi[a] : mid[a];
+      if (chi[a] - clo[a] < rule.min_segment) ok = false;
+    } else {
+      clo[a] = Rlo[a];
+      chi[a] = Rhi[a];
+    }
+  }
+  const KBox kb = lattice_in_box(Q, clo, chi);
+  // this group's partial sums over child c
+  double s1 = 0.0, s2 = 0.0;
+  if (ok) {
+    const int nx = kb.khi[0] - kb.klo[0], ny = kb.khi[1] - kb.klo[1];
+    for (long long j = r; j < kb.n; j += G) {
+      const int kx = kb.klo[0] + static_cast<int>(j % nx);
+      const int ky = kb.klo[1] + static_cast<int>((j / nx) % ny);
+      const int kz = kb.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
+      const double v = static_cast<double>(
+          vals[kx + static_cast<long long>(Q.cnt[0]) * (ky + static_cast<long long>(Q.cnt[1]) * kz)]);
+      s1 += v;
+      s2 = fma(v, v, s2);
+    }
+  }
+  for (int o = G >> 1; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+  }
+  double m = 0.0;
+  const bool valid = ok && kb.n > 0;
+  if (valid) {
+    const double n = static_cast<double>(kb.n);
+    const double inv = 1.0 / pmax;
+    const double sum = s1 * inv;
+    const double mean = sum / n;
+    const double scatter = fmax(s2 * inv * inv - sum * sum / n, 0.0);
+    m = decision_metric(rule.metric, mean, scatter / n, var_prev);
+  }
+  Choice ch;
+  ch.best = -1;
+  ch.nvalid = 0;
+  ch.best_m = ch.second_m = 0.0;
+  for (int a = 0; a < 3; ++a) ch.blo[a] = ch.bhi[a] = 0;
+  for (int cc = 0; cc < nchild; ++cc) {
+    const double mc = __shfl_sync(0xFFFFFFFFu, m, cc * G);
+    const int vc = __shfl_sync(0xFFFFFFFFu, valid ? 1 : 0, cc * G);
+    if (!vc) continue;
+    if (ch.nvalid == 0 || mc > ch.best_m) {
+      if (ch.nvalid > 0) ch.second_m = ch.best_m;
+      ch.best_m = mc;
+      ch.best = cc;
+    } else if (ch.nvalid == 1 || mc > ch.second_m) {
+      ch.second_m = mc;
+    }
+    ++ch.nvalid;
+  }
+  if (ch.best >= 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a < dim) {
+        const int bit = (ch.best >> a) & 1;
+        ch.blo[a] = bit ? mid[a] : Rlo[a];
+        ch.bhi[a] = bit ? Rhi[a] : mid[a];
+      } else {
+        ch.blo[a] = Rlo[a];
+        ch.bhi[a] = Rhi[a];
+      }
+    }
+  }
+  return ch;
+}
+
 __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   const int lane = threadIdx.x & 31;
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -178,7 +274,6 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
   }
   const double pmax = static_cast<double>(fmx);
   const int dim = P.dim;
-  const int nchild = 1 << dim;
   const uwb_rule& rule = P.rule;
 
   int Rlo[3] = {0, 0, 0}, Rhi[3] = {Q.gn[0], Q.gn[1], Q.gn[2]};
@@ -189,46 +284,14 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
 
   for (int i = 1; i <= Q.max_iters; ++i) {
     const int li = i - 1;
-    int mid[3];
+    const Choice ch = choose_child(Q, prof, pmax, Rlo, Rhi, dim, rule, var_prev);
+    const int best = ch.best, nvalid = ch.nvalid;
+    const double best_m = ch.best_m, second_m = ch.second_m;
+    int blo[3], bhi[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) mid[a] = Rlo[a] + (Rhi[a] - Rlo[a]) / 2;
-    int best = -1, nvalid = 0;
-    double best_m = 0.0, second_m = 0.0;
-    int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
-    for (int c = 0; c < nchild; ++c) {
-      int clo[3], chi[3];
-      bool ok = true;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (a < dim) {
-          const int bit = (c >> a) & 1;
-          clo[a] = bit ? mid[a] : Rlo[a];
-          chi[a] = bit ? Rhi[a] : mid[a];
-          if (chi[a] - clo[a] < rule.min_segment) ok = false;
-        } else {
-          clo[a] = Rlo[a];
-          chi[a] = Rhi[a];
-        }
-      }
-      if (!ok) continue;
-      const KBox kb = lattice_in_box(Q, clo, chi);
-      if (kb.n == 0) continue;
-      const Stats sc = box_stats(Q, prof, pmax, kb);
-      const double m =
-          decision_metric(rule.metric, sc.mean, sc.scatter / static_cast<double>(sc.n), var_prev);
-      if (nvalid == 0 || m > best_m) {
-        if (nvalid > 0) second_m = best_m;
-        best_m = m;
-        best = c;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          blo[a] = clo[a];
-          bhi[a] = chi[a];
-        }
-      } else if (nvalid == 1 || m > second_m) {
-        second_m = m;
-      }
-      ++nvalid;
+    for (int a = 0; a < 3; ++a) {
+      blo[a] = ch.blo[a];
+      bhi[a] = ch.bhi[a];
     }
     if (nvalid == 0) {
       stop = UWB_STOP_MINSIZE;
@@ -452,47 +515,14 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
   }
   const Stats sr = box_stats(Qc, cv, pmax, lattice_in_box(Qc, Rlo, Rhi));
   const double var_prev = sr.n > 0 ? sr.scatter / static_cast<double>(sr.n) : 0.0;
-  const int nchild = 1 << dim;
-  int mid[3];
+  const Choice ch = choose_child(Qc, cv, pmax, Rlo, Rhi, dim, rule, var_prev);
+  const int best = ch.best, nvalid = ch.nvalid;
+  const double best_m = ch.best_m, second_m = ch.second_m;
+  int blo[3], bhi[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) mid[a] = Rlo[a] + (Rhi[a] - Rlo[a]) / 2;
-  int best = -1, nvalid = 0;
-  double best_m = 0.0, second_m = 0.0;
-  int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
-  for (int c = 0; c < nchild; ++c) {
-    int clo[3], chi[3];
-    bool ok = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a < dim) {
-        const int bit = (c >> a) & 1;
-        clo[a] = bit ? mid[a] : Rlo[a];
-        chi[a] = bit ? Rhi[a] : mid[a];
-        if (chi[a] - clo[a] < rule.min_segment) ok = false;
-      } else {
-        clo[a] = Rlo[a];
-        chi[a] = Rhi[a];
-      }
-    }
-    if (!ok) continue;
-    const KBox kb = lattice_in_box(Qc, clo, chi);
-    if (kb.n == 0) continue;
-    const Stats sc = box_stats(Qc, cv, pmax, kb);
-    const double m =
-        decision_metric(rule.metric, sc.mean, sc.scatter / static_cast<double>(sc.n), var_prev);
-    if (nvalid == 0 || m > best_m) {
-      if (nvalid > 0) second_m = best_m;
-      best_m = m;
-      best = c;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        blo[a] = clo[a];
-        bhi[a] = chi[a];
-      }
-    } else if (nvalid == 1 || m > second_m) {
-      second_m = m;
-    }
-    ++nvalid;
+  for (int a = 0; a < 3; ++a) {
+    blo[a] = ch.blo[a];
+    bhi[a] = ch.bhi[a];
   }
   const int li = it - 1;
   bool stopped = false;
