@@ -543,6 +543,9 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   int staged = -1;
   bool fits = false;
   int nlo = 0, cl_lo = 0, cl_hi = 0;
+  // this thread's best argmax key over the CTA's tiles of the current scan;
+  // the CTA reduces it once per scan, not once per tile
+  unsigned long long run_key = 0ull;
 
   for (long long g = g_begin; g < g_end; ++g) {
     long long t;
@@ -710,23 +713,33 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
     }
     if (P.keys) {
       // larger energy wins; equal energies -> lower linear index wins
-      unsigned long long key =
+      const unsigned long long key =
           valid ? (static_cast<unsigned long long>(__float_as_uint(energy)) << 32) |
                       (0xFFFFFFFFull - static_cast<unsigned long long>(lin))
                 : 0ull;
+      run_key = key > run_key ? key : run_key;
+      // the CTA's tiles are contiguous: reduce when its last tile of this
+      // scan is done (uniform across the CTA)
+      const bool scan_ends =
+          g + 1 == g_end || (P.boxes ? P.prefix[scan + 1] <= g + 1
+                                     : (g + 1) % P.uni.tiles == 0);
+      if (scan_ends) {
+        unsigned long long k = run_key;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, key, o);
-        key = other > key ? other : key;
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, k, o);
+          k = other > k ? other : k;
+        }
+        if (lane == 0) sKey[warp] = k;
+        __syncthreads();
+        if (tid == 0) {
+          unsigned long long best = 0;
+          for (int w = 0; w < (T >> 5); ++w) best = sKey[w] > best ? sKey[w] : best;
+          if (best) atomicMax(P.keys + scan, best);
+        }
+        __syncthreads();
+        run_key = 0ull;
       }
-      if (lane == 0) sKey[warp] = key;
-      __syncthreads();
-      if (tid == 0) {
-        unsigned long long best = 0;
-        for (int w = 0; w < (T >> 5); ++w) best = sKey[w] > best ? sKey[w] : best;
-        if (best) atomicMax(P.keys + scan, best);
-      }
-      __syncthreads();
     }
   }
 }
