@@ -50,13 +50,19 @@ __device__ __forceinline__ float dist3(float dx, float dy, float dz) {
   return d;
 }
 
-template <int BF, int V>
+// Launch shape of an instance. pp = focal points per thread: monostatic DAS
+// and identity DMAS evaluate two points per thread as the two lanes of
+// paired (float2) instructions; a tile always holds threads * pp points.
+template <int BF, int V, bool MS>
 struct KernelShape {
-  static constexpr int threads = (BF == BF_DMAS_LIT) ? 128 : 256;
-  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas; DAS
-  // 3 and identity DMAS 2, where their window accumulators fit registers
-  // without spilling (measured faster than one more CTA with spills)
-  static constexpr int min_blocks = (BF == BF_DMAS_LIT) ? (V <= 32 ? 4 : 2) : (BF == BF_DAS ? 3 : 2);
+  static constexpr bool lit = BF == BF_DMAS_LIT;
+  static constexpr int pp = (!lit && !MS) ? 2 : 1;
+  static constexpr int threads = (lit || !MS) ? 128 : 256;
+  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas.
+  // Point pairs: DAS 4 and identity DMAS 3, where the paired window
+  // accumulators fit registers; multistatic: DAS 3, identity DMAS 2.
+  static constexpr int min_blocks =
+      lit ? (V <= 32 ? 4 : 2) : (MS ? (BF == BF_DAS ? 3 : 2) : (BF == BF_DAS ? 4 : 3));
 };
 
 // Per-scan quantities: ragged instances (RG) read the scan's descriptor in
@@ -196,6 +202,85 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* 
   return energy;
 }
 
+// Two focal points per thread (monostatic rows, staged window): the lanes of
+// every float2 are the two points, so each per-sample multiply-add of the
+// window sums is half of one paired instruction. Lane by lane the operations
+// and their order are those of energy_sum (a - b is formed as the fused
+// b * (-1) + a, which rounds the same), so both give identical energies.
+template <int BF, int WT, bool RG>
+__device__ __forceinline__ float2 energy_sum_pair(const ImgParams& P,
+                                                  const ScanDesc* __restrict__ sS,
+                                                  const float* __restrict__ sTr,
+                                                  const float4* __restrict__ sAnt, int nlo,
+                                                  int cl_lo, int cl_hi, float2 px, float2 py,
+                                                  float2 pz) {
+  const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
+  float2 energy = make_float2(0.f, 0.f);
+  const int R = scan_R<RG>(P, sS);
+  const float kscale = scan_kscale<RG>(P, sS);
+  const float2 ks = make_float2(kscale, kscale);
+  for (int k0 = 0; k0 < P.W; k0 += WT) {
+    float2 s1[WT], s2[WT];
+#pragma unroll
+    for (int k = 0; k < WT; ++k) {
+      s1[k] = make_float2(0.f, 0.f);
+      s2[k] = make_float2(0.f, 0.f);
+    }
+    const float hoff = static_cast<float>(P.h - k0);
+    const float2 nh = make_float2(-hoff, -hoff);
+    for (int i = 0; i < R; ++i) {
+      const float4 a = sAnt[i];
+      const float2 dx = make_float2(px.x - a.x, px.y - a.x);
+      const float2 dy = make_float2(py.x - a.y, py.y - a.y);
+      const float2 dz = make_float2(pz.x - a.z, pz.y - a.z);
+      // dist3 lane by lane: dx^2 + (dy^2 + dz^2), then the approximate root
+      const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float2 d;
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(d.x) : "f"(q.x));
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(d.y) : "f"(q.y));
+      const float2 t = __ffma2_rn(d, ks, nh);
+      const float2 fl = make_float2(floorf(t.x), floorf(t.y));
+      const float2 f = __ffma2_rn(fl, m1, t);
+      const int nx = min(max(static_cast<int>(fl.x), cl_lo), cl_hi);
+      const int ny = min(max(static_cast<int>(fl.y), cl_lo), cl_hi);
+      const float* rx = sTr + i * P.span + (nx - nlo);
+      const float* ry = sTr + i * P.span + (ny - nlo);
+      float2 y[WT + 1];
+#pragma unroll
+      for (int k = 0; k <= WT; ++k) y[k] = make_float2(rx[k], ry[k]);
+      if (BF == BF_DAS) {
+        const float2 g = __ffma2_rn(f, m1, one);
+#pragma unroll
+        for (int k = 0; k < WT; ++k) {
+          s1[k] = __ffma2_rn(g, y[k], s1[k]);
+          s1[k] = __ffma2_rn(f, y[k + 1], s1[k]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < WT; ++k) {
+          const float2 x = __ffma2_rn(f, __ffma2_rn(y[k], m1, y[k + 1]), y[k]);
+          s1[k] = __fadd2_rn(s1[k], x);
+          s2[k] = __ffma2_rn(x, x, s2[k]);
+        }
+      }
+    }
+    const int kend = min(WT, P.W - k0);
+#pragma unroll
+    for (int k = 0; k < WT; ++k) {
+      if (k < kend) {
+        if (BF == BF_DAS) {
+          energy = __ffma2_rn(s1[k], s1[k], energy);
+        } else {
+          const float2 sq = __fmul2_rn(s1[k], s1[k]);
+          const float2 p = __fmul2_rn(make_float2(0.5f, 0.5f), __ffma2_rn(s2[k], m1, sq));
+          energy = __ffma2_rn(p, p, energy);
+        }
+      }
+    }
+  }
+  return energy;
+}
+
 // ------------------------------------------------------------------ literal DMAS
 // Two window samples (k, k+1) travel together as a float2, so every antenna
 // pair costs one paired FMA for both samples. The pair sum
@@ -257,7 +342,7 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
                                                 int cl_hi, float px, float py, float pz) {
   // the literal kernel always runs 128 threads: a constant T turns the
   // per-antenna (offset, fraction) addresses into immediate offsets
-  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX>::threads;
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false>::threads;
   const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
@@ -361,7 +446,7 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
                                                  int cl_hi, float px, float py, float pz) {
   // the literal kernel always runs 128 threads: a constant T turns the
   // per-antenna (offset, fraction) addresses into immediate offsets
-  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX>::threads;
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false>::threads;
   const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
@@ -479,7 +564,8 @@ __device__ __forceinline__ void make_desc(const ImgParams& P, int scan, ScanDesc
 // (literal DMAS); MS = multistatic rows. Dynamic shared memory as laid out by
 // image_smem_layout.
 template <int BF, int V, bool MS, bool RG>
-__global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V>::min_blocks)
+__global__ void __launch_bounds__(KernelShape<BF, V, MS>::threads,
+                                   KernelShape<BF, V, MS>::min_blocks)
     k_image(const __grid_constant__ CUtensorMap tmap, const ImgParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
@@ -497,12 +583,19 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
   unsigned long long* sKey = reinterpret_cast<unsigned long long*>(smem_raw + Lay.key);
   int* sInt = reinterpret_cast<int*>(smem_raw + Lay.ints);
 
-  // thread -> point of the tile (warp sub-blocks of wdim points)
+  // thread -> points of the tile (warp sub-blocks of wdim points): point q of
+  // a thread is the tile's point number tid + q * T
+  constexpr int PP = KernelShape<BF, V, MS>::pp;
   const int lane = tid & 31, warp = tid >> 5;
   const int nbx = P.tdim[0] / P.wdim[0], nby = P.tdim[1] / P.wdim[1];
-  const int lx = (warp % nbx) * P.wdim[0] + lane % P.wdim[0];
-  const int ly = ((warp / nbx) % nby) * P.wdim[1] + (lane / P.wdim[0]) % P.wdim[1];
-  const int lz = (warp / (nbx * nby)) * P.wdim[2] + lane / (P.wdim[0] * P.wdim[1]);
+  int lx[PP], ly[PP], lz[PP];
+#pragma unroll
+  for (int q = 0; q < PP; ++q) {
+    const int vw = warp + q * (T >> 5);
+    lx[q] = (vw % nbx) * P.wdim[0] + lane % P.wdim[0];
+    ly[q] = ((vw / nbx) % nby) * P.wdim[1] + (lane / P.wdim[0]) % P.wdim[1];
+    lz[q] = (vw / (nbx * nby)) * P.wdim[2] + lane / (P.wdim[0] * P.wdim[1]);
+  }
 
   // where a TMA copy of the window lands: the float32 window itself, or the
   // raw 16-bit area that is widened afterwards
@@ -677,47 +770,80 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
     const int tix = static_cast<int>(t % ntx);
     const int tiy = static_cast<int>((t / ntx) % nty);
     const int tiz = static_cast<int>(t / (static_cast<long long>(ntx) * nty));
-    const int kx = tix * P.tdim[0] + lx, ky = tiy * P.tdim[1] + ly, kz = tiz * P.tdim[2] + lz;
-    const bool valid = kx < L.cnt[0] && ky < L.cnt[1] && kz < L.cnt[2];
-    const int gx = L.lo[0] + L.step[0] * kx;
-    const int gy = L.lo[1] + L.step[1] * ky;
-    const int gz = L.lo[2] + L.step[2] * kz;
-    const long long lin = gx + static_cast<long long>(scan_gn<RG>(P, sS, 0)) *
-                                   (gy + static_cast<long long>(scan_gn<RG>(P, sS, 1)) * gz);
-    float energy = 0.f;
-    if (valid) {
-      const float px = fmaf(static_cast<float>(gx), scan_pit<RG>(P, sS, 0), scan_org<RG>(P, sS, 0));
-      const float py = fmaf(static_cast<float>(gy), scan_pit<RG>(P, sS, 1), scan_org<RG>(P, sS, 1));
-      const float pz = fmaf(static_cast<float>(gz), scan_pit<RG>(P, sS, 2), scan_org<RG>(P, sS, 2));
+    int kx[PP], ky[PP], kz[PP];
+    bool valid[PP];
+    long long lin[PP];
+    float px[PP], py[PP], pz[PP], energy[PP];
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+      kx[q] = tix * P.tdim[0] + lx[q];
+      ky[q] = tiy * P.tdim[1] + ly[q];
+      kz[q] = tiz * P.tdim[2] + lz[q];
+      valid[q] = kx[q] < L.cnt[0] && ky[q] < L.cnt[1] && kz[q] < L.cnt[2];
+      const int gx = L.lo[0] + L.step[0] * kx[q];
+      const int gy = L.lo[1] + L.step[1] * ky[q];
+      const int gz = L.lo[2] + L.step[2] * kz[q];
+      lin[q] = gx + static_cast<long long>(scan_gn<RG>(P, sS, 0)) *
+                        (gy + static_cast<long long>(scan_gn<RG>(P, sS, 1)) * gz);
+      px[q] = fmaf(static_cast<float>(gx), scan_pit<RG>(P, sS, 0), scan_org<RG>(P, sS, 0));
+      py[q] = fmaf(static_cast<float>(gy), scan_pit<RG>(P, sS, 1), scan_org<RG>(P, sS, 1));
+      pz[q] = fmaf(static_cast<float>(gz), scan_pit<RG>(P, sS, 2), scan_org<RG>(P, sS, 2));
+      energy[q] = 0.f;
+    }
+    if constexpr (PP == 2) {
+      // both points together (an invalid one is evaluated at its in-range
+      // clamped samples and discarded)
+      if (valid[0] || valid[1]) {
+        if (fits) {
+          const float2 e = energy_sum_pair<BF, V, RG>(
+              P, sS, sTr, sAnt, nlo, cl_lo, cl_hi, make_float2(px[0], px[1]),
+              make_float2(py[0], py[1]), make_float2(pz[0], pz[1]));
+          energy[0] = e.x;
+          energy[1] = e.y;
+        } else {
+#pragma unroll
+          for (int q = 0; q < PP; ++q)
+            if (valid[q])
+              energy[q] = energy_sum_global<BF, V, MS>(P, sS, sAnt, sCh, sD, px[q], py[q], pz[q]);
+        }
+      }
+    } else if (valid[0]) {
       if constexpr (BF == BF_DMAS_LIT) {
         if constexpr (V <= 16)
-          energy = fits ? energy_literal4<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
-                                                       px, py, pz)
-                        : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
+          energy[0] = fits ? energy_literal4<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                          px[0], py[0], pz[0])
+                           : energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);
         else
-          energy = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
-                                                      px, py, pz)
-                        : energy_literal_global<V>(P, sS, sAnt, sNF, px, py, pz);
+          energy[0] = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                         px[0], py[0], pz[0])
+                           : energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);
       } else {
-        energy = fits ? energy_sum<BF, V, true, MS, RG>(P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo,
-                                                        cl_hi, px, py, pz)
-                      : energy_sum_global<BF, V, MS>(P, sS, sAnt, sCh, sD, px, py, pz);
+        energy[0] = fits ? energy_sum<BF, V, true, MS, RG>(P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo,
+                                                           cl_hi, px[0], py[0], pz[0])
+                         : energy_sum_global<BF, V, MS>(P, sS, sAnt, sCh, sD, px[0], py[0], pz[0]);
       }
-      const long long img_off = RG ? sS->img_off : static_cast<long long>(scan) * P.gP;
-      const long long cmp_off = RG ? sS->cmp_off : static_cast<long long>(scan) * P.compact_stride;
-      if (P.image) P.image[img_off + lin] = energy;
+    }
+    const long long img_off = RG ? sS->img_off : static_cast<long long>(scan) * P.gP;
+    const long long cmp_off = RG ? sS->cmp_off : static_cast<long long>(scan) * P.compact_stride;
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+      if (!valid[q]) continue;
+      if (P.image) P.image[img_off + lin[q]] = energy[q];
       if (P.compact)
-        P.compact[cmp_off + kx +
-                  static_cast<long long>(L.cnt[0]) * (ky + static_cast<long long>(L.cnt[1]) * kz)] =
-            energy;
+        P.compact[cmp_off + kx[q] +
+                  static_cast<long long>(L.cnt[0]) *
+                      (ky[q] + static_cast<long long>(L.cnt[1]) * kz[q])] = energy[q];
     }
     if (P.keys) {
       // larger energy wins; equal energies -> lower linear index wins
-      const unsigned long long key =
-          valid ? (static_cast<unsigned long long>(__float_as_uint(energy)) << 32) |
-                      (0xFFFFFFFFull - static_cast<unsigned long long>(lin))
-                : 0ull;
-      run_key = key > run_key ? key : run_key;
+#pragma unroll
+      for (int q = 0; q < PP; ++q) {
+        const unsigned long long key =
+            valid[q] ? (static_cast<unsigned long long>(__float_as_uint(energy[q])) << 32) |
+                           (0xFFFFFFFFull - static_cast<unsigned long long>(lin[q]))
+                     : 0ull;
+        run_key = key > run_key ? key : run_key;
+      }
       // the CTA's tiles are contiguous: reduce when its last tile of this
       // scan is done (uniform across the CTA)
       const bool scan_ends =
@@ -749,10 +875,13 @@ __global__ void __launch_bounds__(KernelShape<BF, V>::threads, KernelShape<BF, V
 template <int BF, int V, bool MS>
 cudaError_t launch_variant(const ImgParams& p, const CUtensorMap* tmap, int ctas, int threads,
                            size_t smem, cudaStream_t st) {
-  if (p.descs && !MS)
-    k_image<BF, V, false, true><<<ctas, threads, smem, st>>>(*tmap, p);
-  else
-    k_image<BF, V, MS, false><<<ctas, threads, smem, st>>>(*tmap, p);
+  if constexpr (!MS) {
+    if (p.descs) {
+      k_image<BF, V, false, true><<<ctas, threads, smem, st>>>(*tmap, p);
+      return cudaGetLastError();
+    }
+  }
+  k_image<BF, V, MS, false><<<ctas, threads, smem, st>>>(*tmap, p);
   return cudaGetLastError();
 }
 
@@ -781,9 +910,12 @@ int occupancy_instance(int threads, size_t smem) {
 template <int BF, int V, bool MS>
 int occupancy_variant(int threads, size_t smem) {
   const int a = occupancy_instance<BF, V, MS, false>(threads, smem);
-  if (MS) return a;
-  const int b = occupancy_instance<BF, V, false, true>(threads, smem);
-  return a < b ? a : b;
+  if constexpr (MS) {
+    return a;
+  } else {
+    const int b = occupancy_instance<BF, V, false, true>(threads, smem);
+    return a < b ? a : b;
+  }
 }
 
 }  // namespace uwb

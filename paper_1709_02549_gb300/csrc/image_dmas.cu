@@ -21,9 +21,9 @@ cudaError_t launch_image_dmas(int v, bool ms, const ImgParams& p, const CUtensor
     case 20:
       return ms ? launch_variant<BF_DMAS_ID, 20, true>(p, tmap, ctas, threads, smem, st)
                 : launch_variant<BF_DMAS_ID, 20, false>(p, tmap, ctas, threads, smem, st);
-    case 32:
+    case 32:  // multistatic only (monostatic windows over 20 go in chunks of 16)
       return ms ? launch_variant<BF_DMAS_ID, 32, true>(p, tmap, ctas, threads, smem, st)
-                : launch_variant<BF_DMAS_ID, 32, false>(p, tmap, ctas, threads, smem, st);
+                : cudaErrorInvalidValue;
     default:
       return cudaErrorInvalidValue;
   }
@@ -44,8 +44,7 @@ int occupancy_image_dmas(int v, bool ms, int threads, size_t smem) {
       return ms ? occupancy_variant<BF_DMAS_ID, 20, true>(threads, smem)
                 : occupancy_variant<BF_DMAS_ID, 20, false>(threads, smem);
     case 32:
-      return ms ? occupancy_variant<BF_DMAS_ID, 32, true>(threads, smem)
-                : occupancy_variant<BF_DMAS_ID, 32, false>(threads, smem);
+      return ms ? occupancy_variant<BF_DMAS_ID, 32, true>(threads, smem) : 0;
     default:
       return 0;
   }

@@ -196,10 +196,10 @@ std::mutex g_tile_mu;
 int g_tile[3][4][3] = {};
 
 bool tile_ok(int bf, const int t[3]) {
-  const int threads = bf == BF_DMAS_LIT ? 128 : 256;
+  const int points = bf == BF_DMAS_LIT ? 128 : 256;  // focal points per tile
   for (int a = 0; a < 3; ++a)
     if (t[a] < 1 || (t[a] & (t[a] - 1))) return false;  // powers of two
-  return t[0] * t[1] * t[2] == threads;
+  return t[0] * t[1] * t[2] == points;
 }
 
 int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
@@ -226,9 +226,12 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
       var.tdim[0] = 8; var.tdim[1] = 4; var.tdim[2] = 4;
     }
   } else {
-    var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : 32;
+    // window chunk: the whole window up to 20 samples; longer windows go in
+    // chunks of 16 (two focal points per thread) or 32 (multistatic)
+    var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : (var.ms ? 32 : 16);
     var.wpad = (W + var.v - 1) / var.v * var.v;
-    var.threads = 256;
+    // monostatic: 128 threads of two focal points each; multistatic: 256 of one
+    var.threads = var.ms ? 256 : 128;
     var.rows = var.R;
     // multistatic rows are M^2 channels: a larger window budget per CTA
     var.smem_budget = var.ms ? 120 * 1024 : 56 * 1024;
