@@ -40,10 +40,15 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 # Derived shared-load peak: one 128-byte wavefront per clock per SM.
 LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 
-# DRAM traffic of the final-region literal-DMAS kernel per scan, from an ncu
-# capture of the kernel sources whose hash is stored alongside (dmas2d_512,
-# 256 scans); reported as null once the sources change.
-NCU_TRAFFIC = {"sha": "96ce06cfd329a34d", "bytes_per_scan": 6721280 / 256}
+# DRAM traffic of the final-region kernel per scan, per beamformer (0 DAS,
+# 1 identity DMAS, 2 literal DMAS), from ncu captures (dmas2d_512, 256 scans)
+# of the kernel sources whose hash is stored alongside; reported as null once
+# the sources change.
+NCU_TRAFFIC = {
+    0: {"sha": "af45abd9711ae751", "bytes_per_scan": 9006592 / 256},
+    1: {"sha": "af45abd9711ae751", "bytes_per_scan": 9320960 / 256},
+    2: {"sha": "96ce06cfd329a34d", "bytes_per_scan": 6721280 / 256},
+}
 
 
 def kernel_sha() -> str:
@@ -661,9 +666,9 @@ def main():
     achieved_tflops = final_flops / (final_ms / 1e3) / 1e12 if final_ms > 0 else None
     sha = kernel_sha()
     traffic = None
-    if NCU_TRAFFIC["sha"] == sha and bf == 2:
+    if NCU_TRAFFIC[bf]["sha"] == sha:
         # scaled from a 256-scan capture by scans: the staged windows dominate
-        traffic = NCU_TRAFFIC["bytes_per_scan"] * B
+        traffic = NCU_TRAFFIC[bf]["bytes_per_scan"] * B
     # the same GPU's measured ceilings (paired-FMA chains; conflict-free shared loads)
     fma_meas, lds_meas = uwb.uwb_measure_peaks()
     roofline = {
@@ -696,7 +701,7 @@ def main():
             "frac_of_measured": achieved_gwf / (lds_meas / 1e9) if achieved_gwf else None,
             "measured_peak_source": "uwb_measure_peaks: conflict-free 32-bit shared loads",
             "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz",
-            "wavefronts_per_launch": wf, "traffic": None,
+            "wavefronts_per_launch": wf,
             "tflops_achieved": achieved_tflops})
 
     # ---- full-resolution GPU images of the same scans (same beamformer) ----
