@@ -50,19 +50,24 @@ __device__ __forceinline__ float dist3(float dx, float dy, float dz) {
   return d;
 }
 
-// Launch shape of an instance. pp = focal points per thread: monostatic DAS
-// and identity DMAS evaluate two points per thread as the two lanes of
-// paired (float2) instructions; a tile always holds threads * pp points.
-template <int BF, int V, bool MS>
+// Launch shape of an instance. pp = focal points per thread: uniform
+// monostatic DAS and identity DMAS evaluate two points per thread as the two
+// lanes of paired (float2) instructions; a tile always holds threads * pp
+// points. Multistatic and ragged (per-scan descriptor) instances keep one
+// point per thread: their windows (up to 96 rows, or channel rows) often
+// exceed the staged span, and on the global-load path 256 threads of one
+// point measured faster than 128 of two.
+template <int BF, int V, bool MS, bool RG>
 struct KernelShape {
   static constexpr bool lit = BF == BF_DMAS_LIT;
-  static constexpr int pp = (!lit && !MS) ? 2 : 1;
-  static constexpr int threads = (lit || !MS) ? 128 : 256;
+  static constexpr bool pair = !lit && !MS && !RG;
+  static constexpr int pp = pair ? 2 : 1;
+  static constexpr int threads = (lit || pair) ? 128 : 256;
   // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas.
   // Point pairs: DAS 4 and identity DMAS 3, where the paired window
-  // accumulators fit registers; multistatic: DAS 3, identity DMAS 2.
+  // accumulators fit registers; one point per thread: DAS 3, identity DMAS 2.
   static constexpr int min_blocks =
-      lit ? (V <= 32 ? 4 : 2) : (MS ? (BF == BF_DAS ? 3 : 2) : (BF == BF_DAS ? 4 : 3));
+      lit ? (V <= 32 ? 4 : 2) : (pair ? (BF == BF_DAS ? 4 : 3) : (BF == BF_DAS ? 3 : 2));
 };
 
 // Per-scan quantities: ragged instances (RG) read the scan's descriptor in
@@ -342,7 +347,7 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
                                                 int cl_hi, float px, float py, float pz) {
   // the literal kernel always runs 128 threads: a constant T turns the
   // per-antenna (offset, fraction) addresses into immediate offsets
-  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false>::threads;
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false, false>::threads;
   const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
@@ -446,7 +451,7 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
                                                  int cl_hi, float px, float py, float pz) {
   // the literal kernel always runs 128 threads: a constant T turns the
   // per-antenna (offset, fraction) addresses into immediate offsets
-  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false>::threads;
+  constexpr int T = KernelShape<BF_DMAS_LIT, MMAX, false, false>::threads;
   const int tid = threadIdx.x;
   const int M = scan_M<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
@@ -564,8 +569,8 @@ __device__ __forceinline__ void make_desc(const ImgParams& P, int scan, ScanDesc
 // (literal DMAS); MS = multistatic rows. Dynamic shared memory as laid out by
 // image_smem_layout.
 template <int BF, int V, bool MS, bool RG>
-__global__ void __launch_bounds__(KernelShape<BF, V, MS>::threads,
-                                   KernelShape<BF, V, MS>::min_blocks)
+__global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
+                                   KernelShape<BF, V, MS, RG>::min_blocks)
     k_image(const __grid_constant__ CUtensorMap tmap, const ImgParams P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS>::threads,
 
   // thread -> points of the tile (warp sub-blocks of wdim points): point q of
   // a thread is the tile's point number tid + q * T
-  constexpr int PP = KernelShape<BF, V, MS>::pp;
+  constexpr int PP = KernelShape<BF, V, MS, RG>::pp;
   const int lane = tid & 31, warp = tid >> 5;
   const int nbx = P.tdim[0] / P.wdim[0], nby = P.tdim[1] / P.wdim[1];
   int lx[PP], ly[PP], lz[PP];
@@ -905,17 +910,14 @@ int occupancy_instance(int threads, size_t smem) {
   return blocks;
 }
 
-// Resident CTAs of the uniform instance; the ragged instance shares its shape
-// and gets the same dynamic shared-memory limit.
+// Resident CTAs of the instance a launch will use: the ragged one (per-scan
+// descriptors, monostatic only) or the uniform one.
 template <int BF, int V, bool MS>
-int occupancy_variant(int threads, size_t smem) {
-  const int a = occupancy_instance<BF, V, MS, false>(threads, smem);
-  if constexpr (MS) {
-    return a;
-  } else {
-    const int b = occupancy_instance<BF, V, false, true>(threads, smem);
-    return a < b ? a : b;
+int occupancy_variant(bool rg, int threads, size_t smem) {
+  if constexpr (!MS) {
+    if (rg) return occupancy_instance<BF, V, false, true>(threads, smem);
   }
+  return occupancy_instance<BF, V, MS, false>(threads, smem);
 }
 
 }  // namespace uwb

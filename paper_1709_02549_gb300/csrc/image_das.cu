@@ -27,22 +27,22 @@ cudaError_t launch_image_das(int v, bool ms, const ImgParams& p, const CUtensorM
   }
 }
 
-int occupancy_image_das(int v, bool ms, int threads, size_t smem) {
+int occupancy_image_das(int v, bool ms, bool rg, int threads, size_t smem) {
   switch (v) {
     case 4:
-      return ms ? occupancy_variant<BF_DAS, 4, true>(threads, smem)
-                : occupancy_variant<BF_DAS, 4, false>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 4, true>(rg, threads, smem)
+                : occupancy_variant<BF_DAS, 4, false>(rg, threads, smem);
     case 8:
-      return ms ? occupancy_variant<BF_DAS, 8, true>(threads, smem)
-                : occupancy_variant<BF_DAS, 8, false>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 8, true>(rg, threads, smem)
+                : occupancy_variant<BF_DAS, 8, false>(rg, threads, smem);
     case 16:
-      return ms ? occupancy_variant<BF_DAS, 16, true>(threads, smem)
-                : occupancy_variant<BF_DAS, 16, false>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 16, true>(rg, threads, smem)
+                : occupancy_variant<BF_DAS, 16, false>(rg, threads, smem);
     case 20:
-      return ms ? occupancy_variant<BF_DAS, 20, true>(threads, smem)
-                : occupancy_variant<BF_DAS, 20, false>(threads, smem);
+      return ms ? occupancy_variant<BF_DAS, 20, true>(rg, threads, smem)
+                : occupancy_variant<BF_DAS, 20, false>(rg, threads, smem);
     case 32:
-      return ms ? occupancy_variant<BF_DAS, 32, true>(threads, smem) : 0;
+      return ms ? occupancy_variant<BF_DAS, 32, true>(rg, threads, smem) : 0;
     default:
       return 0;
   }

@@ -19,14 +19,14 @@ cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* t
   }
 }
 
-int occupancy_image_literal(int v, int threads, size_t smem) {
+int occupancy_image_literal(int v, bool rg, int threads, size_t smem) {
   switch (v) {
     case 16:
-      return occupancy_variant<BF_DMAS_LIT, 16, false>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 16, false>(rg, threads, smem);
     case 32:
-      return occupancy_variant<BF_DMAS_LIT, 32, false>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 32, false>(rg, threads, smem);
     case 64:
-      return occupancy_variant<BF_DMAS_LIT, 64, false>(threads, smem);
+      return occupancy_variant<BF_DMAS_LIT, 64, false>(rg, threads, smem);
     default:
       return 0;
   }

@@ -187,6 +187,7 @@ struct Variant {
   int rows;           // trace rows in shared memory
   size_t smem_budget; // shared memory per CTA the span is sized for
   bool ms;            // multistatic rows (channels)
+  bool rg;            // launched with per-scan descriptors (ragged plans)
   int M, R;           // antennas, trace rows per scan
 };
 
@@ -206,6 +207,7 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   Variant var;
   var.bf = bf;
   var.ms = R >= 0;
+  var.rg = false;
   var.M = M;
   var.R = R >= 0 ? R : M;
   if (var.ms && bf == BF_DMAS_LIT)
@@ -230,7 +232,8 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     // chunks of 16 (two focal points per thread) or 32 (multistatic)
     var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : (var.ms ? 32 : 16);
     var.wpad = (W + var.v - 1) / var.v * var.v;
-    // monostatic: 128 threads of two focal points each; multistatic: 256 of one
+    // uniform monostatic: 128 threads of two focal points each; multistatic
+    // (and ragged plans, see use_ragged_shape): 256 threads of one
     var.threads = var.ms ? 256 : 128;
     var.rows = var.R;
     // multistatic rows are M^2 channels: a larger window budget per CTA
@@ -249,6 +252,13 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   }
   *out = var;
   return UWB_OK;
+}
+
+// Ragged plans launch the per-scan-descriptor instances, which evaluate one
+// focal point per thread (DAS and identity DMAS at 256 threads).
+void use_ragged_shape(Variant* var) {
+  var->rg = true;
+  if (var->bf != BF_DMAS_LIT) var->threads = 256;
 }
 
 // Warp sub-block shape: the one whose 32 focal points span the fewest delay
@@ -315,11 +325,11 @@ int encode_traces(const Geo& geo, const float* traces, int span, CUtensorMap* ma
 // per device, so that calls after the first (for example inside a CUDA-graph
 // capture) query nothing and change no attribute.
 struct OccKey {
-  int dev, bf, v, ms, threads;
+  int dev, bf, v, ms, rg, threads;
   size_t smem;
   bool operator==(const OccKey& o) const {
-    return dev == o.dev && bf == o.bf && v == o.v && ms == o.ms && threads == o.threads &&
-           smem == o.smem;
+    return dev == o.dev && bf == o.bf && v == o.v && ms == o.ms && rg == o.rg &&
+           threads == o.threads && smem == o.smem;
   }
 };
 std::mutex g_occ_mu;
@@ -328,7 +338,7 @@ std::vector<std::pair<OccKey, int>> g_occ;
 int occupancy(const Variant& var, size_t smem) {
   int d = 0;
   cudaGetDevice(&d);
-  const OccKey key{d, var.bf, var.v, var.ms ? 1 : 0, var.threads, smem};
+  const OccKey key{d, var.bf, var.v, var.ms ? 1 : 0, var.rg ? 1 : 0, var.threads, smem};
   {
     std::lock_guard<std::mutex> lk(g_occ_mu);
     for (const auto& kv : g_occ)
@@ -336,9 +346,9 @@ int occupancy(const Variant& var, size_t smem) {
   }
   int occ;
   switch (var.bf) {
-    case BF_DAS: occ = occupancy_image_das(var.v, var.ms, var.threads, smem); break;
-    case BF_DMAS_ID: occ = occupancy_image_dmas(var.v, var.ms, var.threads, smem); break;
-    default: occ = occupancy_image_literal(var.v, var.threads, smem); break;
+    case BF_DAS: occ = occupancy_image_das(var.v, var.ms, var.rg, var.threads, smem); break;
+    case BF_DMAS_ID: occ = occupancy_image_dmas(var.v, var.ms, var.rg, var.threads, smem); break;
+    default: occ = occupancy_image_literal(var.v, var.rg, var.threads, smem); break;
   }
   if (occ > 0) {
     std::lock_guard<std::mutex> lk(g_occ_mu);
@@ -1179,6 +1189,7 @@ uwb_plan* uwb_plan_create(int batch, const uwb_scan* scans, int dtype, int windo
       max_delta = std::fmax(max_delta, sc.grid.pitch[a] * geos[b].kscale);
   }
   if ((st = pick_variant(bf, Mcap, window, pl->dim, &pl->var))) return bad(st);
+  use_ragged_shape(&pl->var);
   pl->span = pick_span(pl->var, Mcap, dtype);
   const double d1[3] = {max_delta, max_delta, pl->dim == 3 ? max_delta : 1e9};
   pick_warp(pl->var.tdim, d1, pl->wdim_full);

@@ -213,9 +213,9 @@ cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* t
                                  int threads, size_t smem, cudaStream_t st);
 // Sets the dynamic shared-memory limit of the instance and returns its
 // resident CTAs per SM (0 on error).
-int occupancy_image_das(int v, bool ms, int threads, size_t smem);
-int occupancy_image_dmas(int v, bool ms, int threads, size_t smem);
-int occupancy_image_literal(int v, int threads, size_t smem);
+int occupancy_image_das(int v, bool ms, bool rg, int threads, size_t smem);
+int occupancy_image_dmas(int v, bool ms, bool rg, int threads, size_t smem);
+int occupancy_image_literal(int v, bool rg, int threads, size_t smem);
 
 cudaError_t launch_select(const SelParams& p, cudaStream_t st);
 cudaError_t launch_prog_step(const ProgParams& p, int iteration, cudaStream_t st);
