@@ -112,6 +112,36 @@ def test_ragged_plan_of_equal_scans_equals_the_uniform_batch(gpu):
     plan.close()
 
 
+@pytest.mark.parametrize("bf", [0, 1])
+@pytest.mark.parametrize("window,grid_n", [(20, (45, 37, 1)), (33, (31, 26, 1)),
+                                           (20, (18, 14, 11))])
+def test_two_points_per_thread_equal_one_point_per_thread(gpu, bf, window, grid_n):
+    """Uniform DAS / identity-DMAS batches evaluate two focal points per thread
+    as float2 lanes; ragged plans evaluate one per thread. Each lane performs
+    the scalar operations in the scalar order, so the images of the same scans
+    are bit-identical (ragged tiles, window chunks and a 3-D grid included)."""
+    base = phantom.CONFIGS["das2d_64"] if grid_n[2] == 1 else phantom.CONFIGS["hemi3d_256"]
+    cfg = phantom.with_changes(base, grid_n=grid_n, window=window, n_antennas=16,
+                               n_samples=1024, extent=0.09)
+    batch = phantom.make_batch(cfg, 3, 77)
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    P = int(np.prod(grid_n))
+    uni = torch.full((3, P), -1.0, device="cuda")
+    gpu.uwb_image_batch(bf, traces, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, uni)
+    g_rule, _ = rule_pair(gpu)
+    specs = [{"traces": traces[k], "antennas": ants, "grid": cfg.grid(), "v": cfg.v,
+              "fs": cfg.fs} for k in range(3)]
+    plan = gpu.UwbPlan(specs, cfg.window, bf, g_rule)
+    plan.upload(torch.empty(plan.workspace_bytes(), dtype=torch.uint8, device="cuda"))
+    rag = torch.full((plan.image_offset(3),), -2.0, device="cuda")
+    plan.images(rag)
+    torch.cuda.synchronize()
+    assert torch.equal(rag.view(3, P), uni)
+    assert bool((uni >= 0).all())
+    plan.close()
+
+
 def test_ragged_localisation_replays_in_a_cuda_graph(gpu):
     scans = ragged_scans(4, seed=2)
     g_rule, _ = rule_pair(gpu)
