@@ -663,12 +663,6 @@ __global__ void k_cnn_adam(float* __restrict__ theta, float* __restrict__ m,
 }
 
 // ---------------------------------------------------------------- decisions
-__device__ __forceinline__ int tiles_for(const int cnt[3], const int tdim[3]) {
-  int t = 1;
-  for (int a = 0; a < 3; ++a) t *= cnt[a] > 0 ? (cnt[a] + tdim[a] - 1) / tdim[a] : 0;
-  return t;
-}
-
 __device__ __forceinline__ void set_box(LatBox& L, const int lo[3], const int step[3],
                                         const int cnt[3], const int tdim[3]) {
   for (int a = 0; a < 3; ++a) {
@@ -676,7 +670,7 @@ __device__ __forceinline__ void set_box(LatBox& L, const int lo[3], const int st
     L.step[a] = step[a];
     L.cnt[a] = cnt[a];
   }
-  L.tiles = tiles_for(cnt, tdim);
+  L.tiles = lattice_tiles(cnt, step, tdim);
 }
 
 __device__ __forceinline__ void empty_box(LatBox& L) {

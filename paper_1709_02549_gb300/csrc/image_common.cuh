@@ -769,22 +769,34 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
       staged = scan;
     }
 
-    // ---- one tile of the lattice ----
+    // ---- one tile of the lattice: linear (unit step) or tdim-shaped ----
+    const bool linear = lattice_linear(L.step);
     const int ntx = (L.cnt[0] + P.tdim[0] - 1) / P.tdim[0];
     const int nty = (L.cnt[1] + P.tdim[1] - 1) / P.tdim[1];
     const int tix = static_cast<int>(t % ntx);
     const int tiy = static_cast<int>((t / ntx) % nty);
     const int tiz = static_cast<int>(t / (static_cast<long long>(ntx) * nty));
+    const int cxy = L.cnt[0] * L.cnt[1];
     int kx[PP], ky[PP], kz[PP];
     bool valid[PP];
     long long lin[PP];
     float px[PP], py[PP], pz[PP], energy[PP];
 #pragma unroll
     for (int q = 0; q < PP; ++q) {
-      kx[q] = tix * P.tdim[0] + lx[q];
-      ky[q] = tiy * P.tdim[1] + ly[q];
-      kz[q] = tiz * P.tdim[2] + lz[q];
-      valid[q] = kx[q] < L.cnt[0] && ky[q] < L.cnt[1] && kz[q] < L.cnt[2];
+      if (linear) {
+        // point t * (T * PP) + tid + q * T of the box, x fastest
+        const int idx = static_cast<int>(t) * (T * PP) + tid + q * T;
+        kz[q] = idx / cxy;
+        const int r = idx - kz[q] * cxy;
+        ky[q] = r / L.cnt[0];
+        kx[q] = r - ky[q] * L.cnt[0];
+        valid[q] = kz[q] < L.cnt[2];
+      } else {
+        kx[q] = tix * P.tdim[0] + lx[q];
+        ky[q] = tiy * P.tdim[1] + ly[q];
+        kz[q] = tiz * P.tdim[2] + lz[q];
+        valid[q] = kx[q] < L.cnt[0] && ky[q] < L.cnt[1] && kz[q] < L.cnt[2];
+      }
       const int gx = L.lo[0] + L.step[0] * kx[q];
       const int gy = L.lo[1] + L.step[1] * ky[q];
       const int gz = L.lo[2] + L.step[2] * kz[q];

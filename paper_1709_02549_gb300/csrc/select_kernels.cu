@@ -364,16 +364,14 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     R->iters = iters;
     R->n_logged = n_logged;
     R->stop_reason = stop;
-    int tiles = 1;
     for (int a = 0; a < 3; ++a) {
       R->roi_lo[a] = Rlo[a];
       R->roi_hi[a] = Rhi[a];
       box->lo[a] = Rlo[a];
       box->step[a] = 1;
       box->cnt[a] = Rhi[a] - Rlo[a];
-      tiles *= (box->cnt[a] + P.tdim[a] - 1) / P.tdim[a];
     }
-    box->tiles = tiles;
+    box->tiles = lattice_tiles(box->cnt, box->step, P.tdim);
   }
 }
 
@@ -400,14 +398,12 @@ __host__ __device__ inline void region_lattice(int lo, int hi, int c0, int& firs
 }
 
 __device__ void set_full_box(LatBox* box, const int lo[3], const int hi[3], const int tdim[3]) {
-  int tiles = 1;
   for (int a = 0; a < 3; ++a) {
     box->lo[a] = lo[a];
     box->step[a] = 1;
     box->cnt[a] = hi[a] - lo[a];
-    tiles *= (box->cnt[a] + tdim[a] - 1) / tdim[a];
   }
-  box->tiles = tiles;
+  box->tiles = lattice_tiles(box->cnt, box->step, tdim);
 }
 
 __device__ void set_empty_box(LatBox* box) {
@@ -625,14 +621,12 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
         }
         n *= cn[a];
       }
-      int tiles = 1;
       for (int a = 0; a < 3; ++a) {
         next->lo[a] = lo[a];
         next->step[a] = st[a];
         next->cnt[a] = cn[a];
-        tiles *= (cn[a] + P.tdim[a] - 1) / P.tdim[a];
       }
-      next->tiles = tiles;
+      next->tiles = lattice_tiles(cn, st, P.tdim);
       S->points += n;
     }
   }

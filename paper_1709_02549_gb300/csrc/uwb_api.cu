@@ -367,6 +367,8 @@ cudaError_t launch(const Variant& var, const ImgParams& p, const CUtensorMap* ma
   }
 }
 
+// Tiles of tdim points per axis covering cnt points: an upper bound of the
+// tiles of any lattice of that count (lattice_tiles), used to size grids.
 int tiles_of(const int cnt[3], const int tdim[3]) {
   long long t = 1;
   for (int a = 0; a < 3; ++a) t *= (cnt[a] + tdim[a] - 1) / tdim[a];
@@ -466,7 +468,7 @@ int image_impl(int batch, int beamformer, const float* traces, int M, int N, con
     p.uni.step[a] = 1;
     p.uni.cnt[a] = geo.g.n[a];
   }
-  p.uni.tiles = tiles_of(p.uni.cnt, var.tdim);
+  p.uni.tiles = lattice_tiles(p.uni.cnt, p.uni.step, var.tdim);
   p.image = image;
   p.keys = reinterpret_cast<unsigned long long*>(peak_index);
   cudaError_t e;
@@ -637,7 +639,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
     p1.uni.step[a] = dc.step[a];
     p1.uni.cnt[a] = dc.cnt[a];
   }
-  p1.uni.tiles = tiles_of(p1.uni.cnt, var.tdim);
+  p1.uni.tiles = lattice_tiles(p1.uni.cnt, p1.uni.step, var.tdim);
   p1.compact = profile;
   p1.compact_stride = dc.Pd;
   p1.image = image;
@@ -1239,8 +1241,8 @@ uwb_plan* uwb_plan_create(int batch, const uwb_scan* scans, int dtype, int windo
       fb.cnt[a] = g.g.n[a];
       max_dec = std::fmax(max_dec, dc.step[a] * g.g.pitch[a] * g.kscale * (a < pl->dim));
     }
-    pb.tiles = tiles_of(pb.cnt, pl->var.tdim);
-    fb.tiles = tiles_of(fb.cnt, pl->var.tdim);
+    pb.tiles = lattice_tiles(pb.cnt, pb.step, pl->var.tdim);
+    fb.tiles = lattice_tiles(fb.cnt, fb.step, pl->var.tdim);
     pl->pprefix[b + 1] = pl->pprefix[b] + pb.tiles;
     pl->fprefix[b + 1] = pl->fprefix[b] + fb.tiles;
     SelScan& q = pl->sel[b];
@@ -1855,7 +1857,7 @@ int uwb_coarse_maps(int batch, const float* traces, int M, int N, const float* a
       uni.step[a] = stp[a];
       uni.cnt[a] = cnt[a];
     }
-    uni.tiles = tiles_of(uni.cnt, vm.tdim);
+    uni.tiles = lattice_tiles(uni.cnt, uni.step, vm.tdim);
     return run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span, use_tma, &map, &uni,
                         nullptr, nullptr, maps, dev->status, step, cs);
   }
@@ -1967,7 +1969,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
       uni.lo[2] = 0;
       uni.step[2] = 1;
       uni.cnt[2] = 1;
-      uni.tiles = tiles_of(uni.cnt, vm.tdim);
+      uni.tiles = lattice_tiles(uni.cnt, uni.step, vm.tdim);
       st = run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span_m, tma_m, &map_m,
                         &uni, nullptr, nullptr, maps, status, step, cs);
     } else {
@@ -2158,7 +2160,7 @@ int uwb_localize_progressive(int batch, const float* traces, int M, int N,
       p1.uni.step[a] = dc.step[a];
       p1.uni.cnt[a] = dc.cnt[a];
     }
-    p1.uni.tiles = tiles_of(p1.uni.cnt, var.tdim);
+    p1.uni.tiles = lattice_tiles(p1.uni.cnt, p1.uni.step, var.tdim);
     p1.compact = profile;
     p1.compact_stride = dc.Pd;
     if ((st = run_image_kernel(*dev, var, p1, &map, lattice_work, dstep, cs))) return st;

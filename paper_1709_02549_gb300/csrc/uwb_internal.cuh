@@ -34,13 +34,35 @@ struct ScanDesc {
 
 // A box lattice of the focal grid: lattice point k (per axis) is grid index
 // lo + step * k, for 0 <= k < cnt. `tiles` = tiles of the image kernel's tile
-// shape needed to cover it.
+// shape needed to cover it (lattice_tiles).
 struct LatBox {
   int lo[3];
   int step[3];
   int cnt[3];
   int tiles;
 };
+
+// Unit-step lattices (full-resolution regions and images) are covered by
+// linear tiles: tile t holds the points t * P .. t * P + P - 1 (P = points per
+// tile, x fastest), so a region whose sides are not multiples of the tile's
+// sides leaves no partly empty warps but the last. Coarser lattices use tiles
+// of tdim points per axis, whose warps span fewer delay samples.
+__host__ __device__ inline bool lattice_linear(const int step[3]) {
+  return step[0] == 1 && step[1] == 1 && step[2] == 1;
+}
+
+__host__ __device__ inline int lattice_tiles(const int cnt[3], const int step[3],
+                                             const int tdim[3]) {
+  if (cnt[0] <= 0 || cnt[1] <= 0 || cnt[2] <= 0) return 0;
+  if (lattice_linear(step)) {
+    const long long n = static_cast<long long>(cnt[0]) * cnt[1] * cnt[2];
+    const long long pts = static_cast<long long>(tdim[0]) * tdim[1] * tdim[2];
+    return static_cast<int>((n + pts - 1) / pts);
+  }
+  long long t = 1;
+  for (int a = 0; a < 3; ++a) t *= (cnt[a] + tdim[a] - 1) / tdim[a];
+  return static_cast<int>(t);
+}
 
 // Everything the image kernels read. Scans of one launch share M, N, the grid
 // and the lattice shape (uniform lattice) or each has its own box (per-scan
