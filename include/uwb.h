@@ -205,8 +205,12 @@ int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* 
 int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream);
 void uwb_plan_destroy(uwb_plan* plan);
 
-/* Tile shapes of the image kernel (focal points per CTA along x, y, z; powers
- * of two multiplying to 256, or 128 for UWB_DMAS_LITERAL; z = 1 for 2-D).
+/* Tile shapes of the image kernel. {0, 0, 0} = linear tiles (the default):
+ * tile t of a lattice holds its points t*P .. t*P + P - 1 in x-fastest order
+ * (P = 256 focal points per CTA, 128 for UWB_DMAS_LITERAL), so lattices whose
+ * sides are not multiples of a tile leave no partly empty warps. Otherwise a
+ * shaped tile: focal points per CTA along x, y, z, powers of two multiplying
+ * to P, z = 1 for 2-D.
  * uwb_autotune runs the given batch through uwb_plan_localize once per
  * candidate shape (timed with CUDA events after a warm-up run), keeps the
  * fastest for this beamformer and dimensionality in a process-wide table

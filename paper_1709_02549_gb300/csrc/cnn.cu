@@ -670,7 +670,7 @@ __device__ __forceinline__ void set_box(LatBox& L, const int lo[3], const int st
     L.step[a] = step[a];
     L.cnt[a] = cnt[a];
   }
-  L.tiles = lattice_tiles(cnt, step, tdim);
+  L.tiles = lattice_tiles(cnt, tdim);
 }
 
 __device__ __forceinline__ void empty_box(LatBox& L) {

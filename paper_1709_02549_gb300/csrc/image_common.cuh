@@ -588,18 +588,22 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
   unsigned long long* sKey = reinterpret_cast<unsigned long long*>(smem_raw + Lay.key);
   int* sInt = reinterpret_cast<int*>(smem_raw + Lay.ints);
 
-  // thread -> points of the tile (warp sub-blocks of wdim points): point q of
-  // a thread is the tile's point number tid + q * T
-  constexpr int PP = KernelShape<BF, V, MS, RG>::pp;
+  // point q of a thread is the tile's point number tid + q * T; shaped tiles
+  // place it by warp sub-blocks of wdim points
   const int lane = tid & 31, warp = tid >> 5;
-  const int nbx = P.tdim[0] / P.wdim[0], nby = P.tdim[1] / P.wdim[1];
+  constexpr int PP = KernelShape<BF, V, MS, RG>::pp;
+  const bool linear = tile_linear(P.tdim);
   int lx[PP], ly[PP], lz[PP];
 #pragma unroll
   for (int q = 0; q < PP; ++q) {
-    const int vw = warp + q * (T >> 5);
-    lx[q] = (vw % nbx) * P.wdim[0] + lane % P.wdim[0];
-    ly[q] = ((vw / nbx) % nby) * P.wdim[1] + (lane / P.wdim[0]) % P.wdim[1];
-    lz[q] = (vw / (nbx * nby)) * P.wdim[2] + lane / (P.wdim[0] * P.wdim[1]);
+    lx[q] = ly[q] = lz[q] = 0;
+    if (!linear) {
+      const int nbx = P.tdim[0] / P.wdim[0], nby = P.tdim[1] / P.wdim[1];
+      const int vw = warp + q * (T >> 5);
+      lx[q] = (vw % nbx) * P.wdim[0] + lane % P.wdim[0];
+      ly[q] = ((vw / nbx) % nby) * P.wdim[1] + (lane / P.wdim[0]) % P.wdim[1];
+      lz[q] = (vw / (nbx * nby)) * P.wdim[2] + lane / (P.wdim[0] * P.wdim[1]);
+    }
   }
 
   // where a TMA copy of the window lands: the float32 window itself, or the
@@ -769,13 +773,15 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
       staged = scan;
     }
 
-    // ---- one tile of the lattice: linear (unit step) or tdim-shaped ----
-    const bool linear = lattice_linear(L.step);
-    const int ntx = (L.cnt[0] + P.tdim[0] - 1) / P.tdim[0];
-    const int nty = (L.cnt[1] + P.tdim[1] - 1) / P.tdim[1];
-    const int tix = static_cast<int>(t % ntx);
-    const int tiy = static_cast<int>((t / ntx) % nty);
-    const int tiz = static_cast<int>(t / (static_cast<long long>(ntx) * nty));
+    // ---- one tile of the lattice: linear or shaped ----
+    int tix = 0, tiy = 0, tiz = 0;
+    if (!linear) {
+      const int ntx = (L.cnt[0] + P.tdim[0] - 1) / P.tdim[0];
+      const int nty = (L.cnt[1] + P.tdim[1] - 1) / P.tdim[1];
+      tix = static_cast<int>(t % ntx);
+      tiy = static_cast<int>((t / ntx) % nty);
+      tiz = static_cast<int>(t / (static_cast<long long>(ntx) * nty));
+    }
     const int cxy = L.cnt[0] * L.cnt[1];
     int kx[PP], ky[PP], kz[PP];
     bool valid[PP];

@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       box->step[a] = 1;
       box->cnt[a] = Rhi[a] - Rlo[a];
     }
-    box->tiles = lattice_tiles(box->cnt, box->step, P.tdim);
+    box->tiles = lattice_tiles(box->cnt, P.tdim);
   }
 }
 
@@ -403,7 +403,7 @@ __device__ void set_full_box(LatBox* box, const int lo[3], const int hi[3], cons
     box->step[a] = 1;
     box->cnt[a] = hi[a] - lo[a];
   }
-  box->tiles = lattice_tiles(box->cnt, box->step, tdim);
+  box->tiles = lattice_tiles(box->cnt, tdim);
 }
 
 __device__ void set_empty_box(LatBox* box) {
@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
         next->step[a] = st[a];
         next->cnt[a] = cn[a];
       }
-      next->tiles = lattice_tiles(cn, st, P.tdim);
+      next->tiles = lattice_tiles(cn, P.tdim);
       S->points += n;
     }
   }

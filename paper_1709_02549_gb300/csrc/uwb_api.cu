@@ -197,6 +197,7 @@ std::mutex g_tile_mu;
 int g_tile[3][4][3] = {};
 
 bool tile_ok(int bf, const int t[3]) {
+  if (t[0] == 0 && t[1] == 0 && t[2] == 0) return true;  // linear tiles
   const int points = bf == BF_DMAS_LIT ? 128 : 256;  // focal points per tile
   for (int a = 0; a < 3; ++a)
     if (t[a] < 1 || (t[a] & (t[a] - 1))) return false;  // powers of two
@@ -222,11 +223,7 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     // 4 CTAs (2 for the 64-antenna block) per SM, each with the 1 KB the
     // runtime reserves per CTA, fill the SM's 228 KB
     var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
-    if (dim == 2) {
-      var.tdim[0] = 16; var.tdim[1] = 8; var.tdim[2] = 1;
-    } else {
-      var.tdim[0] = 8; var.tdim[1] = 4; var.tdim[2] = 4;
-    }
+    var.tdim[0] = 128; var.tdim[1] = 0; var.tdim[2] = 0;  // linear tiles
   } else {
     // window chunk: the whole window up to 20 samples; longer windows go in
     // chunks of 16 (two focal points per thread) or 32 (multistatic)
@@ -238,20 +235,28 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     var.rows = var.R;
     // multistatic rows are M^2 channels: a larger window budget per CTA
     var.smem_budget = var.ms ? 120 * 1024 : 56 * 1024;
-    if (dim == 2) {
-      var.tdim[0] = 32; var.tdim[1] = 8; var.tdim[2] = 1;
-    } else {
-      var.tdim[0] = 16; var.tdim[1] = 4; var.tdim[2] = 4;
-    }
+    var.tdim[0] = 256; var.tdim[1] = 0; var.tdim[2] = 0;  // linear tiles
   }
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
-    const int* t = g_tile[bf][dim];
+    const int* t = g_tile[bf][dim];  // {0, 0, 0}: the default, linear tiles
     if (t[0] && (dim == 3 || t[2] == 1))
       for (int a = 0; a < 3; ++a) var.tdim[a] = t[a];
   }
   *out = var;
   return UWB_OK;
+}
+
+// The coarse DAS maps of the learned proposal: 32 x 32 lattices with steps of
+// 4 to 16 grid points. Shaped 32 x 8 tiles divide them exactly and keep each
+// warp's delay samples compact (fewer shared-memory bank conflicts than rows
+// of 32 points), so they are used unless a shape was set for 2-D DAS.
+int pick_map_variant(int M, int window, Variant* vm) {
+  const int st = pick_variant(BF_DAS, M, window, 2, vm);
+  if (st == UWB_OK && tile_linear(vm->tdim)) {
+    vm->tdim[0] = 32; vm->tdim[1] = 8; vm->tdim[2] = 1;
+  }
+  return st;
 }
 
 // Ragged plans launch the per-scan-descriptor instances, which evaluate one
@@ -264,6 +269,10 @@ void use_ragged_shape(Variant* var) {
 // Warp sub-block shape: the one whose 32 focal points span the fewest delay
 // samples (fewest shared-memory bank collisions), preferring wide x.
 void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
+  if (tile_linear(tdim)) {  // a warp is 32 consecutive points
+    wdim[0] = 32; wdim[1] = 1; wdim[2] = 1;
+    return;
+  }
   double best = 1e300;
   for (int wx = 32; wx >= 1; wx >>= 1)
     for (int wy = 32 / wx; wy >= 1; wy >>= 1) {
@@ -367,13 +376,6 @@ cudaError_t launch(const Variant& var, const ImgParams& p, const CUtensorMap* ma
   }
 }
 
-// Tiles of tdim points per axis covering cnt points: an upper bound of the
-// tiles of any lattice of that count (lattice_tiles), used to size grids.
-int tiles_of(const int cnt[3], const int tdim[3]) {
-  long long t = 1;
-  for (int a = 0; a < 3; ++a) t *= (cnt[a] + tdim[a] - 1) / tdim[a];
-  return static_cast<int>(t);
-}
 
 ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
                       long long ant_stride, const Variant& var, int span, int use_tma,
@@ -468,7 +470,7 @@ int image_impl(int batch, int beamformer, const float* traces, int M, int N, con
     p.uni.step[a] = 1;
     p.uni.cnt[a] = geo.g.n[a];
   }
-  p.uni.tiles = lattice_tiles(p.uni.cnt, p.uni.step, var.tdim);
+  p.uni.tiles = lattice_tiles(p.uni.cnt, var.tdim);
   p.image = image;
   p.keys = reinterpret_cast<unsigned long long*>(peak_index);
   cudaError_t e;
@@ -639,7 +641,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
     p1.uni.step[a] = dc.step[a];
     p1.uni.cnt[a] = dc.cnt[a];
   }
-  p1.uni.tiles = lattice_tiles(p1.uni.cnt, p1.uni.step, var.tdim);
+  p1.uni.tiles = lattice_tiles(p1.uni.cnt, var.tdim);
   p1.compact = profile;
   p1.compact_stride = dc.Pd;
   p1.image = image;
@@ -685,7 +687,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
   int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
   const double step1[3] = {1, 1, 1};
   if ((st = run_image_kernel(*dev, var, p2, &map,
-                             static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                             static_cast<long long>(batch) * lattice_tiles(full_cnt, var.tdim), step1,
                              cs)))
     return st;
 
@@ -1241,8 +1243,8 @@ uwb_plan* uwb_plan_create(int batch, const uwb_scan* scans, int dtype, int windo
       fb.cnt[a] = g.g.n[a];
       max_dec = std::fmax(max_dec, dc.step[a] * g.g.pitch[a] * g.kscale * (a < pl->dim));
     }
-    pb.tiles = lattice_tiles(pb.cnt, pb.step, pl->var.tdim);
-    fb.tiles = lattice_tiles(fb.cnt, fb.step, pl->var.tdim);
+    pb.tiles = lattice_tiles(pb.cnt, pl->var.tdim);
+    fb.tiles = lattice_tiles(fb.cnt, pl->var.tdim);
     pl->pprefix[b + 1] = pl->pprefix[b] + pb.tiles;
     pl->fprefix[b + 1] = pl->fprefix[b] + fb.tiles;
     SelScan& q = pl->sel[b];
@@ -1405,7 +1407,7 @@ int uwb_tile_shape(int beamformer, int dim, int tile[3]) {
   Variant v;
   int st = pick_variant(bf, 16, 20, dim, &v);
   if (st) return st;
-  for (int a = 0; a < 3; ++a) tile[a] = v.tdim[a];
+  for (int a = 0; a < 3; ++a) tile[a] = tile_linear(v.tdim) ? 0 : v.tdim[a];
   return UWB_OK;
 }
 
@@ -1417,8 +1419,10 @@ int uwb_set_tile_shape(int beamformer, int dim, const int tile[3]) {
     for (int a = 0; a < 3; ++a) g_tile[bf][dim][a] = 0;
     return UWB_OK;
   }
-  if (!tile_ok(bf, tile) || (dim == 2 && tile[2] != 1))
-    return fail(UWB_ERR_ARG, "tile must be powers of two multiplying to the CTA size");
+  const bool linear = tile[0] == 0 && tile[1] == 0 && tile[2] == 0;
+  if (!tile_ok(bf, tile) || (dim == 2 && tile[2] != 1 && !linear))
+    return fail(UWB_ERR_ARG,
+                "tile must be {0, 0, 0} (linear) or powers of two multiplying to the CTA size");
   for (int a = 0; a < 3; ++a) g_tile[bf][dim][a] = tile[a];
   return UWB_OK;
 }
@@ -1430,10 +1434,12 @@ int uwb_autotune(int batch, const uwb_scan* scans, int dtype, int window, int be
   if (bf < 0 || !scans || batch < 1) return fail(UWB_ERR_ARG, "bad autotune arguments");
   const int dim = scans[0].grid.dim;
   if (dim != 2 && dim != 3) return fail(UWB_ERR_ARG, "grid dim must be 2 or 3");
-  static const int c256_2[][3] = {{32, 8, 1}, {16, 16, 1}, {64, 4, 1}, {8, 32, 1}};
-  static const int c128_2[][3] = {{16, 8, 1}, {32, 4, 1}, {8, 16, 1}, {64, 2, 1}};
-  static const int c256_3[][3] = {{16, 4, 4}, {8, 8, 4}, {32, 4, 2}, {8, 4, 8}};
-  static const int c128_3[][3] = {{8, 4, 4}, {16, 4, 2}, {4, 8, 4}, {8, 8, 2}};
+  // linear tiles ({0, 0, 0}) and four shaped ones
+  static const int c256_2[][3] = {{0, 0, 0}, {32, 8, 1}, {16, 16, 1}, {64, 4, 1}, {8, 32, 1}};
+  static const int c128_2[][3] = {{0, 0, 0}, {16, 8, 1}, {32, 4, 1}, {8, 16, 1}, {64, 2, 1}};
+  static const int c256_3[][3] = {{0, 0, 0}, {16, 4, 4}, {8, 8, 4}, {32, 4, 2}, {8, 4, 8}};
+  static const int c128_3[][3] = {{0, 0, 0}, {8, 4, 4}, {16, 4, 2}, {4, 8, 4}, {8, 8, 2}};
+  const int n_cand = 5;
   const int(*cand)[3] = bf == BF_DMAS_LIT ? (dim == 2 ? c128_2 : c128_3)
                                           : (dim == 2 ? c256_2 : c256_3);
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -1447,7 +1453,7 @@ int uwb_autotune(int batch, const uwb_scan* scans, int dtype, int window, int be
     std::lock_guard<std::mutex> lk(g_tile_mu);
     for (int a = 0; a < 3; ++a) saved[a] = g_tile[bf][dim][a];
   }
-  for (int c = 0; c < 4 && st == UWB_OK; ++c) {
+  for (int c = 0; c < n_cand && st == UWB_OK; ++c) {
     st = uwb_set_tile_shape(beamformer, dim, cand[c]);
     if (st) break;
     uwb_plan* plan = uwb_plan_create(batch, scans, dtype, window, beamformer, rule, &st);
@@ -1806,7 +1812,7 @@ int run_map_pass(const Device& dev, const Geo& geo, const float* traces, const f
   p.compact_stride = cnn::MAP * cnn::MAP;
   const double dstep[3] = {static_cast<double>(step), static_cast<double>(step), 1.0};
   int cnt[3] = {cnn::MAP, cnn::MAP, 1};
-  return run_image_kernel(dev, vm, p, map, static_cast<long long>(geo.B) * tiles_of(cnt, vm.tdim),
+  return run_image_kernel(dev, vm, p, map, static_cast<long long>(geo.B) * lattice_tiles(cnt, vm.tdim),
                           dstep, cs);
 }
 
@@ -1842,7 +1848,7 @@ int uwb_coarse_maps(int batch, const float* traces, int M, int N, const float* a
   if ((st = device(&dev))) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   Variant vm;
-  if ((st = pick_variant(BF_DAS, M, window, 2, &vm))) return st;
+  if ((st = pick_map_variant(M, window, &vm))) return st;
   const int span = pick_span(vm, M);
   CUtensorMap map;
   const int use_tma = encode_traces(geo, traces, span, &map);
@@ -1857,7 +1863,7 @@ int uwb_coarse_maps(int batch, const float* traces, int M, int N, const float* a
       uni.step[a] = stp[a];
       uni.cnt[a] = cnt[a];
     }
-    uni.tiles = lattice_tiles(uni.cnt, uni.step, vm.tdim);
+    uni.tiles = lattice_tiles(uni.cnt, vm.tdim);
     return run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span, use_tma, &map, &uni,
                         nullptr, nullptr, maps, dev->status, step, cs);
   }
@@ -1903,7 +1909,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
   Device* dev;
   if ((st = device(&dev))) return st;
   Variant vm, var;
-  if ((st = pick_variant(BF_DAS, M, window, 2, &vm))) return st;
+  if ((st = pick_map_variant(M, window, &vm))) return st;
   if ((st = pick_variant(bf, M, window, 2, &var))) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
@@ -1969,7 +1975,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
       uni.lo[2] = 0;
       uni.step[2] = 1;
       uni.cnt[2] = 1;
-      uni.tiles = lattice_tiles(uni.cnt, uni.step, vm.tdim);
+      uni.tiles = lattice_tiles(uni.cnt, vm.tdim);
       st = run_map_pass(*dev, geo, traces, antennas, antenna_stride, vm, span_m, tma_m, &map_m,
                         &uni, nullptr, nullptr, maps, status, step, cs);
     } else {
@@ -2002,7 +2008,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
                              static_cast<double>(dc.step[2])};
     const int pc[3] = {dc.cnt[0], dc.cnt[1], dc.cnt[2]};
     if ((st = run_image_kernel(*dev, var, p1, &map_f,
-                               static_cast<long long>(batch) * tiles_of(pc, var.tdim), dstep, cs)))
+                               static_cast<long long>(batch) * lattice_tiles(pc, var.tdim), dstep, cs)))
       return st;
   }
   SelParams sp;
@@ -2039,7 +2045,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
     int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
     const double step1[3] = {1, 1, 1};
     if ((st = run_image_kernel(*dev, var, p2, &map_f,
-                               static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                               static_cast<long long>(batch) * lattice_tiles(full_cnt, var.tdim), step1,
                                cs)))
       return st;
   }
@@ -2152,7 +2158,7 @@ int uwb_localize_progressive(int batch, const float* traces, int M, int N,
   const double dstep[3] = {static_cast<double>(dc.step[0]), static_cast<double>(dc.step[1]),
                            static_cast<double>(dc.step[2])};
   const int pc[3] = {dc.cnt[0], dc.cnt[1], dc.cnt[2]};
-  const long long lattice_work = static_cast<long long>(batch) * tiles_of(pc, var.tdim);
+  const long long lattice_work = static_cast<long long>(batch) * lattice_tiles(pc, var.tdim);
   {
     ImgParams p1 = base_params(geo, traces, antennas, antenna_stride, var, span, use_tma, status);
     for (int a = 0; a < 3; ++a) {
@@ -2160,7 +2166,7 @@ int uwb_localize_progressive(int batch, const float* traces, int M, int N,
       p1.uni.step[a] = dc.step[a];
       p1.uni.cnt[a] = dc.cnt[a];
     }
-    p1.uni.tiles = lattice_tiles(p1.uni.cnt, p1.uni.step, var.tdim);
+    p1.uni.tiles = lattice_tiles(p1.uni.cnt, var.tdim);
     p1.compact = profile;
     p1.compact_stride = dc.Pd;
     if ((st = run_image_kernel(*dev, var, p1, &map, lattice_work, dstep, cs))) return st;
@@ -2217,7 +2223,7 @@ int uwb_localize_progressive(int batch, const float* traces, int M, int N,
     int full_cnt[3] = {geo.g.n[0], geo.g.n[1], geo.g.n[2]};
     const double step1[3] = {1, 1, 1};
     if ((st = run_image_kernel(*dev, var, p2, &map,
-                               static_cast<long long>(batch) * tiles_of(full_cnt, var.tdim), step1,
+                               static_cast<long long>(batch) * lattice_tiles(full_cnt, var.tdim), step1,
                                cs)))
       return st;
   }

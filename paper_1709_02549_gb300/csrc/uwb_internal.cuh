@@ -42,22 +42,20 @@ struct LatBox {
   int tiles;
 };
 
-// Unit-step lattices (full-resolution regions and images) are covered by
-// linear tiles: tile t holds the points t * P .. t * P + P - 1 (P = points per
-// tile, x fastest), so a region whose sides are not multiples of the tile's
-// sides leaves no partly empty warps but the last. Coarser lattices use tiles
-// of tdim points per axis, whose warps span fewer delay samples.
-__host__ __device__ inline bool lattice_linear(const int step[3]) {
-  return step[0] == 1 && step[1] == 1 && step[2] == 1;
-}
+// Tiles of the image kernel, one launch-wide kind. Linear tiles (tdim = {P,
+// 0, 0}, P = focal points per CTA; the default): tile t holds the lattice's
+// points t * P .. t * P + P - 1 in x-fastest order, so lattices whose sides
+// are not multiples of a tile leave no partly empty warps but the last.
+// Shaped tiles (tdim = powers of two per axis multiplying to P): tdim points
+// per axis, warps of compact wdim blocks, which span fewer delay samples on
+// coarse lattices.
+__host__ __device__ inline bool tile_linear(const int tdim[3]) { return tdim[1] == 0; }
 
-__host__ __device__ inline int lattice_tiles(const int cnt[3], const int step[3],
-                                             const int tdim[3]) {
+__host__ __device__ inline int lattice_tiles(const int cnt[3], const int tdim[3]) {
   if (cnt[0] <= 0 || cnt[1] <= 0 || cnt[2] <= 0) return 0;
-  if (lattice_linear(step)) {
+  if (tile_linear(tdim)) {
     const long long n = static_cast<long long>(cnt[0]) * cnt[1] * cnt[2];
-    const long long pts = static_cast<long long>(tdim[0]) * tdim[1] * tdim[2];
-    return static_cast<int>((n + pts - 1) / pts);
+    return static_cast<int>((n + tdim[0] - 1) / tdim[0]);
   }
   long long t = 1;
   for (int a = 0; a < 3; ++a) t *= (cnt[a] + tdim[a] - 1) / tdim[a];

@@ -93,12 +93,17 @@ def test_bad_rule_and_workspace_are_rejected(uwb):
 
 
 def test_tile_shape_table(uwb):
-    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [32, 8, 1]
-    assert uwb.uwb_tile_shape(uwb.UWB_DMAS_LITERAL, 3) == [8, 4, 4]
+    # linear tiles by default, reported as {0, 0, 0}
+    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [0, 0, 0]
+    assert uwb.uwb_tile_shape(uwb.UWB_DMAS_LITERAL, 3) == [0, 0, 0]
     uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, [16, 16, 1])
     assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [16, 16, 1]
-    uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, None)
-    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [32, 8, 1]
+    uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, [0, 0, 0])
+    assert uwb.uwb_tile_shape(uwb.UWB_DAS, 2) == [0, 0, 0]
+    uwb.uwb_set_tile_shape(uwb.UWB_DMAS_LITERAL, 3, [8, 4, 4])
+    assert uwb.uwb_tile_shape(uwb.UWB_DMAS_LITERAL, 3) == [8, 4, 4]
+    uwb.uwb_set_tile_shape(uwb.UWB_DMAS_LITERAL, 3, None)
+    assert uwb.uwb_tile_shape(uwb.UWB_DMAS_LITERAL, 3) == [0, 0, 0]
     for bad in ([16, 8, 1], [24, 8, 1], [16, 4, 4]):   # wrong size, not a power of 2, z in 2-D
         with pytest.raises(uwb.UwbError):
             uwb.uwb_set_tile_shape(uwb.UWB_DAS, 2, bad)

@@ -142,6 +142,51 @@ def test_two_points_per_thread_equal_one_point_per_thread(gpu, bf, window, grid_
     plan.close()
 
 
+@pytest.mark.parametrize("bf", [0, 1, 2])
+@pytest.mark.parametrize("grid_n", [(45, 37, 1), (64, 32, 1), (18, 14, 11), (16, 8, 8)])
+def test_linear_and_shaped_tiles_give_identical_results(gpu, bf, grid_n):
+    """The tiling only decides which thread evaluates which focal point:
+    images, decimated profiles and localisations are identical with linear
+    tiles (the default) and with shaped tiles, exact or ragged on the grid."""
+    base = phantom.CONFIGS["das2d_64"] if grid_n[2] == 1 else phantom.CONFIGS["hemi3d_256"]
+    cfg = phantom.with_changes(base, grid_n=grid_n, n_antennas=16, n_samples=1024,
+                               extent=0.09)
+    batch = phantom.make_batch(cfg, 3, 78)
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    dim = 2 if grid_n[2] == 1 else 3
+    shaped = {(2, 2): [16, 8, 1], (2, 3): [8, 4, 4]}.get((bf, dim), [32, 8, 1] if dim == 2
+                                                          else [16, 4, 4])
+    other = {(2, 2): [32, 4, 1], (2, 3): [16, 4, 2]}.get((bf, dim), [16, 16, 1] if dim == 2
+                                                         else [8, 8, 4])
+    assert gpu.uwb_tile_shape(bf, dim) == [0, 0, 0]
+    g_rule, _ = rule_pair(gpu)
+    P = int(np.prod(grid_n))
+
+    def run():
+        img = torch.full((3, P), -1.0, device="cuda")
+        gpu.uwb_image_batch(bf, traces, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, img)
+        ws = torch.empty(gpu.uwb_localize_workspace(3, cfg.n_antennas, cfg.n_samples,
+                                                    cfg.grid(), bf, g_rule),
+                         dtype=torch.uint8, device="cuda")
+        out = torch.empty(3 * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+        gpu.uwb_localize_batch(traces, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, bf, g_rule,
+                               ws, out)
+        torch.cuda.synchronize()
+        return img, out
+
+    img0, out0 = run()
+    try:
+        for tile in (shaped, other):
+            gpu.uwb_set_tile_shape(bf, dim, tile)
+            img1, out1 = run()
+            assert torch.equal(img0, img1), tile
+            assert torch.equal(out0, out1), tile
+    finally:
+        gpu.uwb_set_tile_shape(bf, dim, None)
+    assert bool((img0 >= 0).all())
+
+
 def test_ragged_localisation_replays_in_a_cuda_graph(gpu):
     scans = ragged_scans(4, seed=2)
     g_rule, _ = rule_pair(gpu)
@@ -192,7 +237,7 @@ def test_autotune_picks_a_valid_tile_and_keeps_the_results(gpu):
     out1 = torch.empty_like(out0)
     try:
         tile, ms = plan.autotune(ws, out1)
-        assert tile in ([32, 8, 1], [16, 16, 1], [64, 4, 1], [8, 32, 1]) and ms > 0
+        assert tile in ([0, 0, 0], [32, 8, 1], [16, 16, 1], [64, 4, 1], [8, 32, 1]) and ms > 0
         assert gpu.uwb_tile_shape(1, 2) == tile
         plan2, _ = plan_for(gpu, scans, "f32", 1, g_rule)
         out2 = torch.empty_like(out0)
