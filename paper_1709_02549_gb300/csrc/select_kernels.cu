@@ -52,7 +52,9 @@ __device__ KBox lattice_in_box(const SelScan& P, const int lo[3], const int hi[3
 
 struct Stats {
   long long n;
-  double sum, mean, scatter;  // of the normalised energies; scatter = sum of squared deviations
+  // of the normalised energies; scatter = sum of squared deviations,
+  // var = scatter / n (population variance)
+  double sum, mean, scatter, var;
 };
 
 // Lane-partial sum and sum of squares of the raw energies of the decimated
@@ -74,14 +76,16 @@ __device__ __forceinline__ void lane_sums(const SelScan& P, const float* prof, c
   }
 }
 
-// Statistics of the normalised energies e = I / pmax inside a box: count, sum,
-// mean and scatter (sum of squared deviations, as sum e^2 - (sum e)^2 / n; the
-// energies are non-negative and bounded, so float64 keeps ~14 digits even for
-// nearly flat segments). float64 is this GPU's slow path, so one pass.
-__device__ Stats box_stats(const SelScan& P, const float* prof, double pmax, const KBox& b) {
+// Statistics of the normalised energies e = I * inv (inv = 1 / the profile
+// maximum) inside a box: count, sum, mean, scatter (sum of squared
+// deviations, as sum e^2 - (sum e) mean; the energies are non-negative and
+// bounded, so float64 keeps ~14 digits even for nearly flat segments) and
+// variance. float64 is this GPU's slow path (about two lanes per clock per
+// SM): one pass, and one division (1 / n) per box.
+__device__ Stats box_stats(const SelScan& P, const float* prof, double inv, const KBox& b) {
   Stats st;
   st.n = b.n;
-  st.sum = st.mean = st.scatter = 0.0;
+  st.sum = st.mean = st.scatter = st.var = 0.0;
   if (b.n == 0) return st;
   double s1, s2;
   lane_sums(P, prof, b, s1, s2);
@@ -90,11 +94,11 @@ __device__ Stats box_stats(const SelScan& P, const float* prof, double pmax, con
     s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
     s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
   }
-  const double n = static_cast<double>(b.n);
-  const double inv = 1.0 / pmax;
+  const double rn = 1.0 / static_cast<double>(b.n);
   st.sum = s1 * inv;
-  st.mean = st.sum / n;
-  st.scatter = fmax(s2 * inv * inv - st.sum * st.sum / n, 0.0);
+  st.mean = st.sum * rn;
+  st.scatter = fmax(s2 * inv * inv - st.sum * st.mean, 0.0);
+  st.var = st.scatter * rn;
   return st;
 }
 
@@ -123,7 +127,7 @@ struct Choice {
   int blo[3], bhi[3];
 };
 
-__device__ Choice choose_child(const SelScan& Q, const float* vals, double pmax, const int Rlo[3],
+__device__ Choice choose_child(const SelScan& Q, const float* vals, double inv, const int Rlo[3],
                                const int Rhi[3], int dim, const uwb_rule& rule,
                                double var_prev) {
   const int lane = threadIdx.x & 31;
@@ -167,12 +171,11 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, double pmax,
   double m = 0.0;
   const bool valid = ok && kb.n > 0;
   if (valid) {
-    const double n = static_cast<double>(kb.n);
-    const double inv = 1.0 / pmax;
+    const double rn = 1.0 / static_cast<double>(kb.n);
     const double sum = s1 * inv;
-    const double mean = sum / n;
-    const double scatter = fmax(s2 * inv * inv - sum * sum / n, 0.0);
-    m = decision_metric(rule.metric, mean, scatter / n, var_prev);
+    const double mean = sum * rn;
+    const double scatter = fmax(s2 * inv * inv - sum * mean, 0.0);
+    m = decision_metric(rule.metric, mean, scatter * rn, var_prev);
   }
   Choice ch;
   ch.best = -1;
@@ -272,19 +275,19 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     }
     return;
   }
-  const double pmax = static_cast<double>(fmx);
+  const double inv = 1.0 / static_cast<double>(fmx);
   const int dim = P.dim;
   const uwb_rule& rule = P.rule;
 
   int Rlo[3] = {0, 0, 0}, Rhi[3] = {Q.gn[0], Q.gn[1], Q.gn[2]};
-  Stats sa = box_stats(Q, prof, pmax, lattice_in_box(Q, Rlo, Rhi));
-  double var_prev = sa.scatter / static_cast<double>(sa.n);
+  Stats sa = box_stats(Q, prof, inv, lattice_in_box(Q, Rlo, Rhi));
+  double var_prev = sa.var;
   double B_prev = 0.0, W_prev = 0.0;
   int iters = 0, n_logged = 0, stop = UWB_STOP_NONE;
 
   for (int i = 1; i <= Q.max_iters; ++i) {
     const int li = i - 1;
-    const Choice ch = choose_child(Q, prof, pmax, Rlo, Rhi, dim, rule, var_prev);
+    const Choice ch = choose_child(Q, prof, inv, Rlo, Rhi, dim, rule, var_prev);
     const int best = ch.best, nvalid = ch.nvalid;
     const double best_m = ch.best_m, second_m = ch.second_m;
     int blo[3], bhi[3];
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       }
     }
     // Eq. 6-7 between the regions of consecutive iterations
-    const Stats sb = box_stats(Q, prof, pmax, lattice_in_box(Q, Nlo, Nhi));
+    const Stats sb = box_stats(Q, prof, inv, lattice_in_box(Q, Nlo, Nhi));
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       Rhi[a] = Nhi[a];
     }
     sa = sb;
-    var_prev = sa.scatter / static_cast<double>(sa.n);
+    var_prev = sa.var;
     B_prev = Bi;
     W_prev = Wi;
     iters = i;
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
     return;
   }
   const uwb_rule& rule = P.rule;
-  const double pmax = S->pmax;
+  const double inv = 1.0 / static_cast<double>(S->pmax);
   int Rlo[3], Rhi[3];
   for (int a = 0; a < 3; ++a) {
     Rlo[a] = S->Rlo[a];
@@ -509,9 +512,9 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       return;
     }
   }
-  const Stats sr = box_stats(Qc, cv, pmax, lattice_in_box(Qc, Rlo, Rhi));
-  const double var_prev = sr.n > 0 ? sr.scatter / static_cast<double>(sr.n) : 0.0;
-  const Choice ch = choose_child(Qc, cv, pmax, Rlo, Rhi, dim, rule, var_prev);
+  const Stats sr = box_stats(Qc, cv, inv, lattice_in_box(Qc, Rlo, Rhi));
+  const double var_prev = sr.var;
+  const Choice ch = choose_child(Qc, cv, inv, Rlo, Rhi, dim, rule, var_prev);
   const int best = ch.best, nvalid = ch.nvalid;
   const double best_m = ch.best_m, second_m = ch.second_m;
   int blo[3], bhi[3];
@@ -542,8 +545,8 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       }
     }
     // Eq. 6-7 on the decimated profile between the region and the framed child
-    const Stats sa = box_stats(Q0, prof, pmax, lattice_in_box(Q0, Rlo, Rhi));
-    const Stats sb = box_stats(Q0, prof, pmax, lattice_in_box(Q0, Nlo, Nhi));
+    const Stats sa = box_stats(Q0, prof, inv, lattice_in_box(Q0, Rlo, Rhi));
+    const Stats sb = box_stats(Q0, prof, inv, lattice_in_box(Q0, Nlo, Nhi));
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
