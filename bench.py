@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "af45abd9711ae751", "bytes_per_scan": 9006592 / 256},
-    1: {"sha": "af45abd9711ae751", "bytes_per_scan": 9320960 / 256},
-    2: {"sha": "af45abd9711ae751", "bytes_per_scan": 6721024 / 256},
+    0: {"sha": "2009db500c676d4f", "bytes_per_scan": 9007872 / 256},
+    1: {"sha": "2009db500c676d4f", "bytes_per_scan": 9321984 / 256},
+    2: {"sha": "2009db500c676d4f", "bytes_per_scan": 6720768 / 256},
 }
 
 
