@@ -14,10 +14,14 @@
 //    bounding box) is copied to shared memory by one 3-D TMA box
 //    (x = sample, y = antenna, z = scan) whose out-of-range elements arrive as
 //    zeros -- exactly the "samples outside the trace are 0" convention;
-//  * one thread per focal point; the delay is computed in registers, the
-//    W+1 samples of the window are read from shared memory and interpolated;
-//  * fused epilogue: image store, compact-profile store, and a block-reduced
-//    64-bit (energy, -index) key folded into the scan's argmax with atomicMax.
+//  * tiles of a lattice are linear (points in x-fastest order) or shaped
+//    (tdim points per axis); one focal point per thread (two as float2 lanes
+//    for uniform DAS and identity DMAS); the delay is computed in registers,
+//    the W+1 samples of the window are read from shared memory and
+//    interpolated;
+//  * fused epilogue: image store, compact-profile store, and a 64-bit
+//    (energy, -index) key per thread, reduced by the CTA once per scan and
+//    folded into the scan's argmax with atomicMax.
 // Scans whose window does not fit the staged span fall back to bounds-checked
 // global loads (same arithmetic). Traces may be stored as float32, float16 or
 // bfloat16; the staged window is always float32 (16-bit traces land in a raw

@@ -85,8 +85,8 @@ struct ImgParams {
   LatBox uni;                // the lattice of every scan when boxes == nullptr
   const LatBox* boxes;       // per-scan lattices (device) or nullptr
   const int* prefix;         // [B+1] exclusive tile prefix when boxes != nullptr
-  int tdim[3];               // tile extent in lattice points
-  int wdim[3];               // warp sub-block extent (product 32)
+  int tdim[3];               // tile shape, or {P, 0, 0} for linear tiles (tile_linear)
+  int wdim[3];               // warp sub-block extent of shaped tiles (product 32)
   int span;                  // samples staged per antenna (multiple of 4)
   int wpad;                  // window samples a thread may read (>= W, chunk multiple)
   int use_tma;               // stage with cp.async.bulk.tensor (else plain loads)
