@@ -426,3 +426,13 @@ def test_multistatic_localize_matches_oracle(gpu, bf):
             return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
                                                   BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
         compare_localize(res[s], o, energy_at)
+
+
+def test_measured_peaks_are_plausible(gpu):
+    """uwb_measure_peaks (the denominators of the bench's measured roofline
+    fractions): paired-FMA TFLOP/s and conflict-free shared-load wavefronts/s
+    on this GPU, between a third of and a little above the derived peaks
+    (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz; 1 wavefront per clock per SM)."""
+    tflops, wavefronts = gpu.uwb_measure_peaks()
+    assert 80.5 / 3 < tflops < 80.5 * 1.1
+    assert 314.6e9 / 3 < wavefronts < 314.6e9 * 1.1
