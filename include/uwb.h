@@ -83,8 +83,9 @@ extern "C" {
 
 #define UWB_MAX_ITERS 32
 
-/* Focal-point lattice (Section II.A: "the breast tissue is divided into
- * several focal points according to the desired resolution"). */
+/* Focal-point lattice (Section II.A: the imaged region is sampled at focal
+ * points spaced by the target resolution). n[0] * n[1] * n[2] must stay below
+ * 2^31 - 4096 (UWB_ERR_ARG). */
 typedef struct uwb_grid {
   int dim;           /* 2 or 3 */
   int n[3];          /* points per axis; n[2] == 1 when dim == 2 */

@@ -159,7 +159,9 @@ int check_common(int batch, const float* traces, int M, int N, const float* ant,
     P *= grid->n[a];
   }
   if (grid->dim == 2 && grid->n[2] != 1) return fail(UWB_ERR_ARG, "2-D grid needs n[2] == 1");
-  if (P > 0x7FFFFFFELL) return fail(UWB_ERR_ARG, "grid of %lld points exceeds 2^31 - 2", P);
+  // below 2^31 by more than a tile, so that every focal-point index of a
+  // linear tile (tile * 256 + thread) stays a non-negative int
+  if (P > 0x7FFFF000LL) return fail(UWB_ERR_ARG, "grid of %lld points exceeds 2^31 - 4096", P);
   const double ks = 2.0 * fs / v;
   if (!std::isfinite(static_cast<float>(ks))) return fail(UWB_ERR_ARG, "2 fs / v overflows float");
   geo->B = batch;
