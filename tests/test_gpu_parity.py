@@ -312,9 +312,16 @@ def test_host_entry_point_matches_device_entry_point(gpu, name, bf, N, per_scan)
 
 # ------------------------------------------------------------------ tumour-presence test
 
-@pytest.mark.parametrize("name,bf,D2", [("das2d_64", 0, 3), ("dmas2d_512", 2, 20)])
+def _small_cube(**kw):
+    """A 32^3 version of the hemispherical 3-D workload (16 antennas)."""
+    return phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(32, 32, 32),
+                                n_antennas=16, n_samples=1024, n_clutter=10, **kw)
+
+
+@pytest.mark.parametrize("name,bf,D2", [("das2d_64", 0, 3), ("dmas2d_512", 2, 20),
+                                        ("cube32", 0, 3), ("cube32", 2, 3)])
 def test_presence_matches_oracle(gpu, name, bf, D2):
-    base = phantom.CONFIGS[name]
+    base = _small_cube() if name == "cube32" else phantom.CONFIGS[name]
     scans, truth = [], []
     for tumor in (True, False):
         cfg = base if tumor else phantom.with_changes(base, n_tumors=(0, 0))
@@ -436,3 +443,40 @@ def test_measured_peaks_are_plausible(gpu):
     tflops, wavefronts = gpu.uwb_measure_peaks()
     assert 80.5 / 3 < tflops < 80.5 * 1.1
     assert 314.6e9 / 3 < wavefronts < 314.6e9 * 1.1
+
+
+
+@pytest.mark.parametrize("bf", [0, 1])
+def test_multistatic_three_d_matches_oracle(gpu, bf):
+    """Multistatic (Eq. 2 delays, Eq. 4 over every channel) on a small cube:
+    the image and the octree localisation against the oracle."""
+    cfg = phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(24, 20, 16),
+                               n_antennas=8, n_samples=1024, n_clutter=5)
+    ch = phantom.all_channels(cfg.n_antennas)
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + 40 + s, ch) for s in range(2)]
+    traces = np.stack([sc["traces"] for sc in scans])
+    ants = scans[0]["antennas"]
+    grid = cfg.grid()
+    img, _ = _ms_gpu_image(gpu, bf, traces, ch, ants, grid, cfg.v, cfg.fs, cfg.window)
+    for s, sc in enumerate(scans):
+        ref = oracle.image_multistatic(sc["traces"], ch, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                       BF_ORACLE[bf])
+        assert_image_close(img[s], ref, what=f"3-D multistatic scan {s}")
+    g_rule, o_rule = rule_pair(gpu, min_segment=2)
+    B = len(scans)
+    ws = torch.empty(gpu.uwb_localize_multistatic_workspace(B, len(ch), cfg.n_samples, grid, bf,
+                                                            g_rule), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    gpu.uwb_localize_multistatic_batch(dev(traces), torch.from_numpy(ch).cuda(), dev(ants), grid,
+                                       cfg.v, cfg.fs, cfg.window, bf, g_rule, ws, out)
+    torch.cuda.synchronize()
+    res = [record_to_dict(r) for r in gpu.results_from_device(out)]
+    for s, sc in enumerate(scans):
+        o = oracle.localize_multistatic(sc["traces"], ch, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                        BF_ORACLE[bf], o_rule)
+
+        def energy_at(idx, t=sc["traces"]):
+            return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
+                                                  BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
+        compare_localize(res[s], o, energy_at)

@@ -25,10 +25,18 @@ def gpu_progressive(uwb, bf, traces, ants, grid, v, fs, W, rule):
     return [record_to_dict(r) for r in uwb.results_from_device(out)]
 
 
+def _config(name):
+    if name == "cube32":   # a 32^3 version of the hemispherical 3-D workload (octree)
+        return phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(32, 32, 32),
+                                    n_antennas=16, n_samples=1024, n_clutter=10)
+    return phantom.CONFIGS[name]
+
+
 @pytest.mark.parametrize("name,bf,n_scans", [("das2d_64", 0, 6), ("dmas2d_512", 0, 4),
-                                             ("dmas2d_512", 2, 3)])
+                                             ("dmas2d_512", 2, 3), ("cube32", 0, 3),
+                                             ("cube32", 2, 2)])
 def test_progressive_matches_oracle(gpu, name, bf, n_scans):
-    cfg = phantom.CONFIGS[name]
+    cfg = _config(name)
     b = phantom.make_batch(cfg, n_scans, 40)
     g = cfg.grid()
     ants = b["antennas"].astype(np.float32)
