@@ -50,6 +50,31 @@ __device__ KBox lattice_in_box(const SelScan& P, const int lo[3], const int hi[3
   return b;
 }
 
+// Visits the decimated points j = start, start + stride, ... of a box (x
+// fastest) without dividing per point: the index is decomposed once and then
+// advanced by the stride with carries (stride <= 32).
+template <class F>
+__device__ __forceinline__ void for_box_points(const KBox& b, int start, int stride, F&& f) {
+  const int n = static_cast<int>(b.n);
+  if (start >= n) return;
+  const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
+  int kx = start % nx, ky = (start / nx) % ny, kz = start / (nx * ny);
+  const int sx = stride % nx, sy = stride / nx;
+  for (int j = start; j < n; j += stride) {
+    f(b.klo[0] + kx, b.klo[1] + ky, b.klo[2] + kz);
+    kx += sx;
+    ky += sy;
+    if (kx >= nx) {
+      kx -= nx;
+      ++ky;
+    }
+    while (ky >= ny) {
+      ky -= ny;
+      ++kz;
+    }
+  }
+}
+
 struct Stats {
   long long n;
   // of the normalised energies; scatter = sum of squared deviations,
@@ -62,18 +87,14 @@ struct Stats {
 __device__ __forceinline__ void lane_sums(const SelScan& P, const float* prof, const KBox& b,
                                           double& s1, double& s2) {
   const int lane = threadIdx.x & 31;
-  const int nx = b.khi[0] - b.klo[0], ny = b.khi[1] - b.klo[1];
-  s1 = 0.0;
-  s2 = 0.0;
-  for (long long j = lane; j < b.n; j += 32) {
-    const int kx = b.klo[0] + static_cast<int>(j % nx);
-    const int ky = b.klo[1] + static_cast<int>((j / nx) % ny);
-    const int kz = b.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
-    const double v = static_cast<double>(
-        prof[kx + static_cast<long long>(P.cnt[0]) * (ky + static_cast<long long>(P.cnt[1]) * kz)]);
-    s1 += v;
-    s2 = fma(v, v, s2);
-  }
+  double a1 = 0.0, a2 = 0.0;
+  for_box_points(b, lane, 32, [&](int kx, int ky, int kz) {
+    const double v = static_cast<double>(prof[kx + P.cnt[0] * (ky + P.cnt[1] * kz)]);
+    a1 += v;
+    a2 = fma(v, v, a2);
+  });
+  s1 = a1;
+  s2 = a2;
 }
 
 // Statistics of the normalised energies e = I * inv (inv = 1 / the profile
@@ -153,16 +174,11 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, double inv, 
   // this group's partial sums over child c
   double s1 = 0.0, s2 = 0.0;
   if (ok) {
-    const int nx = kb.khi[0] - kb.klo[0], ny = kb.khi[1] - kb.klo[1];
-    for (long long j = r; j < kb.n; j += G) {
-      const int kx = kb.klo[0] + static_cast<int>(j % nx);
-      const int ky = kb.klo[1] + static_cast<int>((j / nx) % ny);
-      const int kz = kb.klo[2] + static_cast<int>(j / (static_cast<long long>(nx) * ny));
-      const double v = static_cast<double>(
-          vals[kx + static_cast<long long>(Q.cnt[0]) * (ky + static_cast<long long>(Q.cnt[1]) * kz)]);
+    for_box_points(kb, r, G, [&](int kx, int ky, int kz) {
+      const double v = static_cast<double>(vals[kx + Q.cnt[0] * (ky + Q.cnt[1] * kz)]);
       s1 += v;
       s2 = fma(v, v, s2);
-    }
+    });
   }
   for (int o = G >> 1; o > 0; o >>= 1) {
     s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
