@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "ab09062424ef5a5b", "bytes_per_scan": 9007872 / 256},
-    1: {"sha": "ab09062424ef5a5b", "bytes_per_scan": 9321984 / 256},
-    2: {"sha": "ab09062424ef5a5b", "bytes_per_scan": 6720768 / 256},
+    0: {"sha": "14bb30dad4fc1aa5", "bytes_per_scan": 9007104 / 256},
+    1: {"sha": "14bb30dad4fc1aa5", "bytes_per_scan": 9323008 / 256},
+    2: {"sha": "14bb30dad4fc1aa5", "bytes_per_scan": 6720000 / 256},
 }
 
 
