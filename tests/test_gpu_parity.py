@@ -480,3 +480,68 @@ def test_multistatic_three_d_matches_oracle(gpu, bf):
             return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
                                                   BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
         compare_localize(res[s], o, energy_at)
+
+
+@pytest.mark.parametrize("entry", ["localize_das", "localize_literal", "presence",
+                                   "multistatic"])
+def test_device_entry_points_replay_in_a_cuda_graph(gpu, entry):
+    """The device-resident entry points launch kernels only (no host round
+    trip, allocation or synchronisation), so a captured CUDA graph replays
+    them with byte-identical results."""
+    g_rule, _ = rule_pair(gpu)
+    if entry == "multistatic":
+        cfg = phantom.CONFIGS["ms2d_12"]
+        ch = phantom.all_channels(cfg.n_antennas)
+        scans = [phantom.make_scan(cfg, phantom.BASE_SEED + 60 + s, ch) for s in range(3)]
+        tr = dev(np.stack([sc["traces"] for sc in scans]))
+        chd = torch.from_numpy(ch).cuda()
+        ants = dev(scans[0]["antennas"])
+        bf = 1
+        ws = torch.empty(gpu.uwb_localize_multistatic_workspace(3, len(ch), cfg.n_samples,
+                                                                cfg.grid(), bf, g_rule),
+                         dtype=torch.uint8, device="cuda")
+        outs = [torch.empty(3 * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")]
+
+        def run(o, stream=None):
+            gpu.uwb_localize_multistatic_batch(tr, chd, ants, cfg.grid(), cfg.v, cfg.fs,
+                                               cfg.window, bf, g_rule, ws, o[0],
+                                               stream=stream)
+    else:
+        cfg = phantom.CONFIGS["das2d_64" if entry == "localize_das" else "dmas2d_512"]
+        b = phantom.make_batch(cfg, 3, 61)
+        tr, ants = dev(b["traces"]), dev(b["antennas"].astype(np.float32))
+        bf = 0 if entry == "localize_das" else 2
+        B, M, N = b["traces"].shape
+        if entry == "presence":
+            D2 = 20
+            ws = torch.empty(gpu.uwb_presence_workspace(B, M, N, cfg.grid(), bf, g_rule, D2),
+                             dtype=torch.uint8, device="cuda")
+            outs = [torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda"),
+                    torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda"),
+                    torch.empty(B, dtype=torch.int32, device="cuda")]
+
+            def run(o, stream=None):
+                gpu.uwb_presence_batch(tr, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, bf,
+                                       g_rule, D2, ws, o[0], o[1], o[2], stream=stream)
+        else:
+            ws = torch.empty(gpu.uwb_localize_workspace(B, M, N, cfg.grid(), bf, g_rule),
+                             dtype=torch.uint8, device="cuda")
+            outs = [torch.empty(B * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")]
+
+            def run(o, stream=None):
+                gpu.uwb_localize_batch(tr, ants, cfg.grid(), cfg.v, cfg.fs, cfg.window, bf,
+                                       g_rule, ws, o[0], stream=stream)
+    run(outs)
+    torch.cuda.synchronize()
+    graphed = [torch.zeros_like(o) for o in outs]
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        run(graphed, s)
+    for _ in range(2):
+        for g in graphed:
+            g.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for g, o in zip(graphed, outs):
+            assert torch.equal(g, o)
