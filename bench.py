@@ -315,9 +315,14 @@ def run_ragged(args, uwb, torch):
     import oracle
     oracle.build()
     B = args.batch
-    bf = BEAMFORMERS[args.beamformer] if args.beamformer != "literal" else 1
+    # literal-pair DMAS is built for up to 64 antennas: --ragged-literal draws
+    # 16-64 antennas per scan; otherwise a DMAS request runs the identity form
+    # on the 16-96 antenna batches
+    max_m = 64 if args.ragged_literal else 96
+    bf = 2 if args.ragged_literal else (BEAMFORMERS[args.beamformer]
+                                        if args.beamformer != "literal" else 1)
     dim = args.ragged_dim
-    cfgs = phantom.ragged_configs(B, dim=dim)
+    cfgs = phantom.ragged_configs(B, dim=dim, max_antennas=max_m)
     scans = [phantom.make_scan(c, phantom.BASE_SEED + 200000 + k) for k, c in enumerate(cfgs)]
     dev_tr = [torch.from_numpy(sc["traces"]).cuda() for sc in scans]
     dev_an = [torch.from_numpy(sc["antennas"]).cuda() for sc in scans]
@@ -328,10 +333,8 @@ def run_ragged(args, uwb, torch):
     out = {"metric": "localised scans/s, ragged batches (plan API)", "unit": "scans/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
            "data": "synthetic",
-           # literal-pair DMAS is built for up to 64 antennas and these scans reach 96,
-           # so a DMAS request runs the identity form
-           "beamformer": ["das", "dmas (identity)", "dmas (identity)"][bf],
-           "config": {"workload": f"{B} uneven scans: 16-96 antennas, 1024-4096 samples, " +
+           "beamformer": ["das", "dmas (identity)", "dmas (literal pairs)"][bf],
+           "config": {"workload": f"{B} uneven scans: 16-{max_m} antennas, 1024-4096 samples, " +
                                   ("128^2-1024^2 grids over 12 cm, 50 clutter, 15 dB" if dim == 2
                                    else "128^3 grids over 10 cm, 100 clutter, 15 dB"),
                       "points_total": int(sum(np.prod(c.grid_n) for c in cfgs))},
@@ -612,6 +615,8 @@ def main():
                          "proposal against the plain framework")
     ap.add_argument("--ragged-dim", type=int, default=2, choices=[2, 3],
                     help="ragged mode: 2-D grids (128^2-1024^2) or 128^3 cubes")
+    ap.add_argument("--ragged-literal", action="store_true",
+                    help="ragged mode: literal-pair DMAS on scans of 16-64 antennas")
     ap.add_argument("--decimation2", type=int, default=0,
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()

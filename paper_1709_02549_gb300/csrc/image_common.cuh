@@ -666,6 +666,11 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
 
     if (scan != staged) {
       // ---- stage scan `scan`: descriptor, antennas, reachable sample window ----
+      // literal DMAS lands a 16-bit window (ragged plans; uniform batches are
+      // float32) in the (offset, fraction) table: order this thread's table
+      // stores before the copy's async-proxy writes
+      if constexpr (BF == BF_DMAS_LIT && RG)
+        if (P.dtype != DT_F32) fence_proxy_async_smem();
       __syncthreads();  // every read of the previous window is complete
       if (tid == 0) {
         make_desc(P, scan, *sS);
@@ -836,14 +841,31 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
       }
     } else if (valid[0]) {
       if constexpr (BF == BF_DMAS_LIT) {
-        if constexpr (V <= 16)
+        if constexpr (V <= 16) {
           energy[0] = fits ? energy_literal4<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
                                                           px[0], py[0], pz[0])
                            : energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);
-        else
+        } else if constexpr (RG) {
+          // ragged plans size the block for their largest scan: each scan takes
+          // the smallest pair-sample block that holds its own antennas, so a
+          // small scan forms no products with zero rows beyond that block
+          const int Ms = scan_M<RG>(P, sS);
+          if (!fits)
+            energy[0] = energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);
+          else if (Ms <= 16)
+            energy[0] = energy_literal<16, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                     px[0], py[0], pz[0]);
+          else if (V > 32 && Ms <= 32)
+            energy[0] = energy_literal<32, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                     px[0], py[0], pz[0]);
+          else
+            energy[0] = energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
+                                                    px[0], py[0], pz[0]);
+        } else {
           energy[0] = fits ? energy_literal<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
                                                          px[0], py[0], pz[0])
                            : energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);
+        }
       } else {
         energy[0] = fits ? energy_sum<BF, V, true, MS, RG>(P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo,
                                                            cl_hi, px[0], py[0], pz[0])

@@ -120,11 +120,20 @@ inline __host__ __device__ SmemLayout image_smem_layout(int bf, int Mcap, int Rc
   size_t off = static_cast<size_t>(rows) * span * 4;
   off = align_up(off, 128);
   L.raw = off;
-  if (dtype != DT_F32) off = align_up(off + static_cast<size_t>(rows) * span * 2, 128);
+  if (dtype != DT_F32 && bf != BF_DMAS_LIT)
+    off = align_up(off + static_cast<size_t>(rows) * span * 2, 128);
   L.ant = off;
   off += static_cast<size_t>(Mcap) * 16;
   L.ch = off;
   if (ms) off += static_cast<size_t>(Rcap) * 8;
+  if (bf == BF_DMAS_LIT && dtype != DT_F32) {
+    // literal DMAS writes its per-thread (offset, fraction) table only after a
+    // staged window has been widened, so a 16-bit window lands in the table
+    // (rows * span * 2 <= rows * threads * 8 bytes: span <= 256 <= 4 * threads;
+    // 128-byte aligned for the copy)
+    off = align_up(off, 128);
+    L.raw = off;
+  }
   L.nf = off;
   if (bf == BF_DMAS_LIT) off += static_cast<size_t>(rows) * threads * 8;
   L.d = off;

@@ -103,16 +103,17 @@ CONFIGS["ms2d_12"] = ScanConfig(
     clutter_amp=(0.05, 0.2), eps_jitter=0.10)
 
 
-def ragged_configs(n_scans: int, seed: int = BASE_SEED, dim: int = 2) -> list:
-    """Per-scan workloads of a batch of uneven scans: each draws 16-96 antennas,
-    1024-4096 samples and a 2-D grid side of 128-1024 points (or a 128^3 cube
-    when dim == 3) over a 12 cm region, with the clutter, permittivity jitter
-    and 15 dB noise of the 512 x 512 workload."""
+def ragged_configs(n_scans: int, seed: int = BASE_SEED, dim: int = 2,
+                   max_antennas: int = 96) -> list:
+    """Per-scan workloads of a batch of uneven scans: each draws 16-96 antennas
+    (16-max_antennas), 1024-4096 samples and a 2-D grid side of 128-1024 points
+    (or a 128^3 cube when dim == 3) over a 12 cm region, with the clutter,
+    permittivity jitter and 15 dB noise of the 512 x 512 workload."""
     rng = np.random.Generator(np.random.Philox(seed))
     out = []
     base = CONFIGS["dmas2d_512"]
     for _ in range(n_scans):
-        m = int(rng.integers(16, 97))
+        m = int(rng.integers(16, max_antennas + 1))
         n = int(rng.integers(1024, 4097))
         if dim == 2:
             g = int(rng.integers(128, 1025))

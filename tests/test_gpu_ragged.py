@@ -187,6 +187,40 @@ def test_linear_and_shaped_tiles_give_identical_results(gpu, bf, grid_n):
     assert bool((img0 >= 0).all())
 
 
+def test_ragged_literal_blocks_per_scan_match_oracle(gpu):
+    """A literal-DMAS plan holds scans of 8 to 60 antennas (the 64-antenna
+    register block); each scan runs the smallest block that holds it (16, 32
+    or 64 antennas), and images and localisations match the oracle."""
+    base = phantom.CONFIGS["das2d_64"]
+    scans = []
+    for k, m in enumerate((8, 20, 40, 60)):
+        cfg = phantom.with_changes(base, n_antennas=m, grid_n=(40 + 3 * k, 36, 1),
+                                   n_samples=1024, n_clutter=5)
+        scans.append((cfg, phantom.make_scan(cfg, phantom.BASE_SEED + 950 + k)))
+    g_rule, o_rule = rule_pair(gpu)
+    plan, host = plan_for(gpu, scans, "f32", 2, g_rule)
+    imgs = torch.full((plan.image_offset(len(scans)),), -1.0, device="cuda")
+    plan.images(imgs)
+    out = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(out)
+    torch.cuda.synchronize()
+    imgs = imgs.cpu().numpy()
+    res = [record_to_dict(r) for r in gpu.results_from_device(out)]
+    for k, (cfg, sc) in enumerate(scans):
+        g = cfg.grid()
+        ref = oracle.image(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DMAS)
+        got = imgs[plan.image_offset(k):plan.image_offset(k + 1)].reshape(ref.shape)
+        assert_image_close(got, ref, what=f"scan {k} ({cfg.n_antennas} antennas)")
+        o = oracle.localize(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DMAS,
+                            o_rule)
+
+        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
+            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, oracle.DMAS, lo=idx,
+                                      step=[1, 1, 1], cnt=[1, 1, 1])[0, 0, 0])
+        compare_localize(res[k], o, energy_at)
+    plan.close()
+
+
 def test_ragged_localisation_replays_in_a_cuda_graph(gpu):
     scans = ragged_scans(4, seed=2)
     g_rule, _ = rule_pair(gpu)
