@@ -235,24 +235,26 @@ def run_reference(args, cfg, bf):
     }
 
 
-def cpu_baseline(cfg, bf, seconds):
-    """The oracle as it stands, on the host cores: scans localised until about
-    `seconds` of oracle time (scan synthesis not timed)."""
+def cpu_baseline(cfg, bf, seconds, pool=32):
+    """The oracle as it stands, on the host cores: a pool of scans is synthesised
+    first (not timed), then localised in turn until about `seconds` of oracle
+    time."""
     import oracle
     oracle.build()
     grid = cfg.grid()
     obf = oracle.DAS if bf == 0 else oracle.DMAS
     rule = oracle.make_rule()
+    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + 100000 + k) for k in range(pool)]
     n, busy = 0, 0.0
     while busy < seconds:
-        sc = phantom.make_scan(cfg, phantom.BASE_SEED + 100000 + n)
+        sc = scans[n % pool]
         t1 = time.perf_counter()
         oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf, rule)
         busy += time.perf_counter() - t1
         n += 1
     return {"value": n / busy, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} scans of the same workload localised by the FP64 oracle "
-                      f"({busy:.1f} s of oracle time)"}
+            "sample": f"{n} localisations of {pool} scans of the same workload by the FP64 "
+                      f"oracle ({busy:.1f} s of oracle time)"}
 
 
 def run_presence(args, cfg, bf, uwb, torch):
