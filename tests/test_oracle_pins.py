@@ -94,6 +94,46 @@ def test_dmas_single_sample_equals_pair_identity_of_das(M):
     np.testing.assert_allclose(dmas, expect, rtol=1e-9, atol=1e-12 * expect.max())
 
 
+def _brute_force_image(tr, ants, grid, window, literal_pairs):
+    """Eq. 1 and Eq. 3 (DAS) or the Section II.B pair sum (DMAS) written out in
+    plain Python loops: round-trip delay 2|r - a_i| fs / v in samples, the
+    window centred on it, linear interpolation with zero outside the trace."""
+    nx, ny = grid["n"][0], grid["n"][1]
+    h = window // 2
+    out = np.zeros((1, ny, nx))
+    for iy in range(ny):
+        for ix in range(nx):
+            r = (grid["origin"][0] + ix * grid["pitch"][0], grid["origin"][1] + iy * grid["pitch"][1],
+                 grid["origin"][2])
+            energy = 0.0
+            for k in range(window):
+                xs = []
+                for i in range(len(ants)):
+                    d = math.dist(r, [float(c) for c in ants[i]])
+                    t = 2.0 * d * FS / V - h + k
+                    n0 = math.floor(t)
+                    f = t - n0
+                    y0 = float(tr[i][n0]) if 0 <= n0 < tr.shape[1] else 0.0
+                    y1 = float(tr[i][n0 + 1]) if 0 <= n0 + 1 < tr.shape[1] else 0.0
+                    xs.append((1.0 - f) * y0 + f * y1)
+                if literal_pairs:
+                    s = sum(xs[i] * xs[j] for i in range(len(xs)) for j in range(i + 1, len(xs)))
+                else:
+                    s = sum(xs)
+                energy += s * s
+            out[0, iy, ix] = energy
+    return out
+
+
+@pytest.mark.parametrize("bf", [oracle.DAS, oracle.DMAS])
+def test_image_matches_a_brute_force_of_the_definitions(bf):
+    # a tiny scene: 3 antennas, a 7 x 5 grid, a 3-sample window
+    tr, ants, grid = _random_scene(3, N=256, seed=21)
+    got = oracle.image(tr, ants, grid, V, FS, 3, bf)
+    want = _brute_force_image(tr, ants, grid, 3, literal_pairs=bf == oracle.DMAS)
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-12 * want.max())
+
+
 def test_dmas_two_antennas_is_product_of_single_antenna_energies():
     # M = 2, W = 1: (x_1 x_2)^2 = x_1^2 * x_2^2
     tr, ants, grid = _random_scene(2, seed=11)
