@@ -187,10 +187,12 @@ def test_linear_and_shaped_tiles_give_identical_results(gpu, bf, grid_n):
     assert bool((img0 >= 0).all())
 
 
-def test_ragged_literal_blocks_per_scan_match_oracle(gpu):
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_ragged_literal_blocks_per_scan_match_oracle(gpu, dtype):
     """A literal-DMAS plan holds scans of 8 to 60 antennas (the 64-antenna
     register block); each scan runs the smallest block that holds it (16, 32
-    or 64 antennas), and images and localisations match the oracle."""
+    or 64 antennas), and images and localisations match the oracle. 16-bit
+    windows land in the per-thread delay table before they are widened."""
     base = phantom.CONFIGS["das2d_64"]
     scans = []
     for k, m in enumerate((8, 20, 40, 60)):
@@ -198,7 +200,7 @@ def test_ragged_literal_blocks_per_scan_match_oracle(gpu):
                                    n_samples=1024, n_clutter=5)
         scans.append((cfg, phantom.make_scan(cfg, phantom.BASE_SEED + 950 + k)))
     g_rule, o_rule = rule_pair(gpu)
-    plan, host = plan_for(gpu, scans, "f32", 2, g_rule)
+    plan, host = plan_for(gpu, scans, dtype, 2, g_rule)
     imgs = torch.full((plan.image_offset(len(scans)),), -1.0, device="cuda")
     plan.images(imgs)
     out = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
