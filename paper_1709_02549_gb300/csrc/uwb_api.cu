@@ -265,7 +265,13 @@ int pick_map_variant(int M, int window, Variant* vm) {
 // focal point per thread (DAS and identity DMAS at 256 threads).
 void use_ragged_shape(Variant* var) {
   var->rg = true;
-  if (var->bf != BF_DMAS_LIT) var->threads = 256;
+  if (var->bf != BF_DMAS_LIT) {
+    var->threads = 256;
+    // those run 3 (DAS) or 2 (identity DMAS) CTAs per SM, each with the 1 KB
+    // the runtime reserves: the rest of the SM's 228 KB sizes the staged span
+    // of their (up to 96-row) windows
+    var->smem_budget = (var->bf == BF_DAS ? 74 : 112) * 1024;
+  }
 }
 
 // Warp sub-block shape: the one whose 32 focal points span the fewest delay
