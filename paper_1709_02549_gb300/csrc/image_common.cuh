@@ -762,10 +762,31 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
           phase ^= 1u;
           if (P.dtype != DT_F32) {  // widen the 16-bit window
             const int total_s = R * P.span;
-            for (int j = tid; j < total_s; j += T) {
+            const bool f16 = P.dtype == DT_F16;
+            auto widen = [&](int j) {
               const unsigned short b = sRaw[j];
-              sTr[j] = P.dtype == DT_F16 ? __half2float(__ushort_as_half(b))
-                                         : __bfloat162float(__ushort_as_bfloat16(b));
+              return f16 ? __half2float(__ushort_as_half(b))
+                         : __bfloat162float(__ushort_as_bfloat16(b));
+            };
+            if (BF == BF_DMAS_LIT) {  // the raw window sits in a separate area
+              for (int j = tid; j < total_s; j += T) sTr[j] = widen(j);
+            } else {
+              // in place: the raw window starts at byte >= 2 * total_s of the
+              // float window's area, so widening the elements [a, (total_s +
+              // a) / 2 - 1) writes below every raw element from a on. Stages
+              // of that size halve what remains; the last T or fewer elements
+              // are read before any of them is written.
+              int a = 0;
+              while (total_s - a > T) {
+                const int e = (total_s + a) / 2 - 1;
+                for (int j = a + tid; j < e; j += T) sTr[j] = widen(j);
+                __syncthreads();
+                a = e;
+              }
+              const int j = a + tid;
+              const float v = j < total_s ? widen(j) : 0.f;
+              __syncthreads();
+              if (j < total_s) sTr[j] = v;
             }
             __syncthreads();
           }

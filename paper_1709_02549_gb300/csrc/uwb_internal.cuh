@@ -117,11 +117,16 @@ inline __host__ __device__ SmemLayout image_smem_layout(int bf, int Mcap, int Rc
                                                         int span, int threads, bool ms,
                                                         int dtype) {
   SmemLayout L;
-  size_t off = static_cast<size_t>(rows) * span * 4;
-  off = align_up(off, 128);
+  const size_t window = static_cast<size_t>(rows) * span * 4;
+  size_t off = align_up(window, 128);
   L.raw = off;
-  if (dtype != DT_F32 && bf != BF_DMAS_LIT)
-    off = align_up(off + static_cast<size_t>(rows) * span * 2, 128);
+  if (dtype != DT_F32 && bf != BF_DMAS_LIT) {
+    // a 16-bit window lands in the upper half of the float window's area
+    // (128-byte aligned for the copy) and is widened in place, front to back
+    L.raw = align_up(static_cast<size_t>(rows) * span * 2, 128);
+    const size_t end = L.raw + static_cast<size_t>(rows) * span * 2;
+    off = align_up(end > window ? end : window, 128);
+  }
   L.ant = off;
   off += static_cast<size_t>(Mcap) * 16;
   L.ch = off;
