@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "c280ee09eaeb56b2", "bytes_per_scan": 9008640 / 256},
-    1: {"sha": "c280ee09eaeb56b2", "bytes_per_scan": 9322752 / 256},
-    2: {"sha": "c280ee09eaeb56b2", "bytes_per_scan": 6720256 / 256},
+    0: {"sha": "9a9ab4d873838212", "bytes_per_scan": 9008384 / 256},
+    1: {"sha": "9a9ab4d873838212", "bytes_per_scan": 9323520 / 256},
+    2: {"sha": "9a9ab4d873838212", "bytes_per_scan": 6721024 / 256},
 }
 
 
