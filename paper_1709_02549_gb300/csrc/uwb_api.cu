@@ -235,8 +235,10 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     // (and ragged plans, see use_ragged_shape): 256 threads of one
     var.threads = var.ms ? 256 : 128;
     var.rows = var.R;
-    // multistatic rows are M^2 channels: a larger window budget per CTA
-    var.smem_budget = var.ms ? 120 * 1024 : 56 * 1024;
+    // window budget per CTA: the CTAs per SM of the launch shape share the
+    // SM's 228 KB (point pairs: DAS 4, identity DMAS 3); multistatic rows are
+    // M^2 channels and take a larger budget
+    var.smem_budget = var.ms ? 120 * 1024 : (bf == BF_DAS ? 56 : 74) * 1024;
     var.tdim[0] = 256; var.tdim[1] = 0; var.tdim[2] = 0;  // linear tiles
   }
   {
