@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "9a9ab4d873838212", "bytes_per_scan": 9008384 / 256},
-    1: {"sha": "9a9ab4d873838212", "bytes_per_scan": 9323520 / 256},
-    2: {"sha": "9a9ab4d873838212", "bytes_per_scan": 6721024 / 256},
+    0: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 9008640 / 256},
+    1: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 9324800 / 256},
+    2: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 6720768 / 256},
 }
 
 
