@@ -64,14 +64,17 @@ __device__ __forceinline__ float dist3(float dx, float dy, float dz) {
 template <int BF, int V, bool MS, bool RG>
 struct KernelShape {
   static constexpr bool lit = BF == BF_DMAS_LIT;
-  static constexpr bool pair = !lit && !MS && !RG;
+  static constexpr bool pair = !lit && !RG;
   static constexpr int pp = pair ? 2 : 1;
-  static constexpr int threads = (lit || pair) ? 128 : 256;
+  static constexpr int threads = (lit || (pair && !MS)) ? 128 : 256;
   // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas.
-  // Point pairs: DAS 4 and identity DMAS 3, where the paired window
-  // accumulators fit registers; one point per thread: DAS 3, identity DMAS 2.
+  // Monostatic point pairs: DAS 4 and identity DMAS 3, where the paired
+  // window accumulators fit registers; ragged (one point per thread): DAS 3,
+  // identity DMAS 2. Multistatic: one CTA per SM (its channel window takes
+  // most of the shared memory), 256 threads of two points.
   static constexpr int min_blocks =
-      lit ? (V <= 32 ? 4 : 2) : (pair ? (BF == BF_DAS ? 4 : 3) : (BF == BF_DAS ? 3 : 2));
+      lit ? (V <= 32 ? 4 : 2)
+          : (MS ? 1 : (pair ? (BF == BF_DAS ? 4 : 3) : (BF == BF_DAS ? 3 : 2)));
 };
 
 // Per-scan quantities: ragged instances (RG) read the scan's descriptor in
@@ -216,18 +219,38 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* 
 // window sums is half of one paired instruction. Lane by lane the operations
 // and their order are those of energy_sum (a - b is formed as the fused
 // b * (-1) + a, which rounds the same), so both give identical energies.
-template <int BF, int WT, bool RG>
+template <int BF, int WT, bool RG, bool MS>
 __device__ __forceinline__ float2 energy_sum_pair(const ImgParams& P,
                                                   const ScanDesc* __restrict__ sS,
                                                   const float* __restrict__ sTr,
-                                                  const float4* __restrict__ sAnt, int nlo,
-                                                  int cl_lo, int cl_hi, float2 px, float2 py,
-                                                  float2 pz) {
+                                                  const float4* __restrict__ sAnt,
+                                                  const int2* __restrict__ sCh,
+                                                  float* __restrict__ sD, int nlo, int cl_lo,
+                                                  int cl_hi, float2 px, float2 py, float2 pz) {
   const float2 one = make_float2(1.f, 1.f), m1 = make_float2(-1.f, -1.f);
   float2 energy = make_float2(0.f, 0.f);
   const int R = scan_R<RG>(P, sS);
   const float kscale = scan_kscale<RG>(P, sS);
   const float2 ks = make_float2(kscale, kscale);
+  // multistatic: the distance of each of this thread's two points to every
+  // antenna, in sD[antenna][point of the CTA] (points v0 and v0 + blockDim)
+  const int TP = 2 * blockDim.x, v0 = threadIdx.x, v1 = threadIdx.x + blockDim.x;
+  if (MS) {
+    const int M = scan_M<RG>(P, sS);
+    for (int i = 0; i < M; ++i) {
+      const float4 a = sAnt[i];
+      const float2 dx = make_float2(px.x - a.x, px.y - a.x);
+      const float2 dy = make_float2(py.x - a.y, py.y - a.y);
+      const float2 dz = make_float2(pz.x - a.z, pz.y - a.z);
+      const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float dxv, dyv;
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(dxv) : "f"(q.x));
+      asm("sqrt.approx.f32 %0, %1;" : "=f"(dyv) : "f"(q.y));
+      sD[i * TP + v0] = dxv;
+      sD[i * TP + v1] = dyv;
+    }
+  }
+  const float half_k = 0.5f * kscale;
   for (int k0 = 0; k0 < P.W; k0 += WT) {
     float2 s1[WT], s2[WT];
 #pragma unroll
@@ -238,16 +261,24 @@ __device__ __forceinline__ float2 energy_sum_pair(const ImgParams& P,
     const float hoff = static_cast<float>(P.h - k0);
     const float2 nh = make_float2(-hoff, -hoff);
     for (int i = 0; i < R; ++i) {
-      const float4 a = sAnt[i];
-      const float2 dx = make_float2(px.x - a.x, px.y - a.x);
-      const float2 dy = make_float2(py.x - a.y, py.y - a.y);
-      const float2 dz = make_float2(pz.x - a.z, pz.y - a.z);
-      // dist3 lane by lane: dx^2 + (dy^2 + dz^2), then the approximate root
-      const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-      float2 d;
-      asm("sqrt.approx.f32 %0, %1;" : "=f"(d.x) : "f"(q.x));
-      asm("sqrt.approx.f32 %0, %1;" : "=f"(d.y) : "f"(q.y));
-      const float2 t = __ffma2_rn(d, ks, nh);
+      float2 t;  // u_i - h + k0 for both points
+      if (MS) {
+        // Eq. 2: (|r - a_tx| + |r - a_rx|) fs / v, lane by lane as energy_sum
+        const int2 c = sCh[i];
+        t.x = fmaf(sD[c.x * TP + v0] + sD[c.y * TP + v0], half_k, -hoff);
+        t.y = fmaf(sD[c.x * TP + v1] + sD[c.y * TP + v1], half_k, -hoff);
+      } else {
+        const float4 a = sAnt[i];
+        const float2 dx = make_float2(px.x - a.x, px.y - a.x);
+        const float2 dy = make_float2(py.x - a.y, py.y - a.y);
+        const float2 dz = make_float2(pz.x - a.z, pz.y - a.z);
+        // dist3 lane by lane: dx^2 + (dy^2 + dz^2), then the approximate root
+        const float2 q = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        float2 d;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(d.x) : "f"(q.x));
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(d.y) : "f"(q.y));
+        t = __ffma2_rn(d, ks, nh);
+      }
       const float2 fl = make_float2(floorf(t.x), floorf(t.y));
       const float2 f = __ffma2_rn(fl, m1, t);
       const int nx = min(max(static_cast<int>(fl.x), cl_lo), cl_hi);
@@ -580,7 +611,9 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
   const int T = blockDim.x, tid = threadIdx.x;
   // literal DMAS keeps V (>= M) trace rows; rows M..V-1 stay zero
   const int rows = (BF == BF_DMAS_LIT) ? V : P.Rcap;
-  const SmemLayout Lay = image_smem_layout(BF, P.Mcap, P.Rcap, rows, P.span, T, MS, P.dtype);
+  // per-point tables are sized by the CTA's focal points (threads x points per thread)
+  const SmemLayout Lay = image_smem_layout(BF, P.Mcap, P.Rcap, rows, P.span,
+                                           T * KernelShape<BF, V, MS, RG>::pp, MS, P.dtype);
   float* sTr = reinterpret_cast<float*>(smem_raw);
   unsigned short* sRaw = reinterpret_cast<unsigned short*>(smem_raw + Lay.raw);
   float4* sAnt = reinterpret_cast<float4*>(smem_raw + Lay.ant);  // (x, y, z, 0)
@@ -848,8 +881,8 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
       // clamped samples and discarded)
       if (valid[0] || valid[1]) {
         if (fits) {
-          const float2 e = energy_sum_pair<BF, V, RG>(
-              P, sS, sTr, sAnt, nlo, cl_lo, cl_hi, make_float2(px[0], px[1]),
+          const float2 e = energy_sum_pair<BF, V, RG, MS>(
+              P, sS, sTr, sAnt, sCh, sD, nlo, cl_lo, cl_hi, make_float2(px[0], px[1]),
               make_float2(py[0], py[1]), make_float2(pz[0], pz[1]));
           energy[0] = e.x;
           energy[1] = e.y;

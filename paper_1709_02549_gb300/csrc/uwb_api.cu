@@ -237,11 +237,12 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     var.rows = var.R;
     // window budget per CTA: the CTAs per SM of the launch shape share the
     // SM's 228 KB (point pairs: DAS 4, identity DMAS 3); multistatic rows are
-    // M^2 channels and take a larger budget
-    var.smem_budget = var.ms ? 120 * 1024 : (bf == BF_DAS ? 56 : 74) * 1024;
-    var.tdim[0] = 256; var.tdim[1] = 0; var.tdim[2] = 0;  // linear tiles
+    // M^2 channels: one CTA per SM with the span of up to 256 samples
+    var.smem_budget = (var.ms ? 180 : (bf == BF_DAS ? 56 : 74)) * 1024;
+    // linear tiles of the CTA's focal points (multistatic: 256 threads of two)
+    var.tdim[0] = var.ms ? 512 : 256; var.tdim[1] = 0; var.tdim[2] = 0;
   }
-  {
+  if (!var.ms) {  // tile shapes set by uwb_set_tile_shape / uwb_autotune (monostatic)
     std::lock_guard<std::mutex> lk(g_tile_mu);
     const int* t = g_tile[bf][dim];  // {0, 0, 0}: the default, linear tiles
     if (t[0] && (dim == 3 || t[2] == 1))
@@ -261,6 +262,12 @@ int pick_map_variant(int M, int window, Variant* vm) {
     vm->tdim[0] = 32; vm->tdim[1] = 8; vm->tdim[2] = 1;
   }
   return st;
+}
+
+// Focal points of one CTA: uniform DAS and identity DMAS (monostatic and
+// multistatic) evaluate two per thread; literal DMAS and ragged plans one.
+int var_points(const Variant& v) {
+  return v.threads * ((v.bf != BF_DMAS_LIT && !v.rg) ? 2 : 1);
 }
 
 // Ragged plans launch the per-scan-descriptor instances, which evaluate one
@@ -303,7 +310,7 @@ int pick_span(const Variant& var, int M, int dtype = DT_F32) {
   // the largest span (a multiple of 8: 16-byte TMA rows for 16-bit traces too)
   // whose whole layout fits the budget
   int span = 256;
-  while (span > 8 && image_smem_layout(var.bf, M, var.R, var.rows, span, var.threads, var.ms,
+  while (span > 8 && image_smem_layout(var.bf, M, var.R, var.rows, span, var_points(var), var.ms,
                                        dtype).total > var.smem_budget)
     span -= 8;
   const int floor_span = (var.wpad + 8 + 7) & ~7;
@@ -429,7 +436,7 @@ int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const 
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
   if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
   pick_warp(var.tdim, delta, p.wdim);
-  const size_t smem = image_smem_layout(var.bf, p.Mcap, p.Rcap, var.rows, p.span, var.threads,
+  const size_t smem = image_smem_layout(var.bf, p.Mcap, p.Rcap, var.rows, p.span, var_points(var),
                                         var.ms, p.dtype).total;
   const int occ = occupancy(var, smem);
   if (occ < 1) return fail(UWB_ERR_UNSUPPORTED, "image kernel cannot launch with %zu B of shared memory", smem);
@@ -891,7 +898,7 @@ int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const in
   if (st) return st;
   for (int a = 0; a < 3; ++a) p.wdim[a] = wdim[a];
   const size_t smem =
-      image_smem_layout(pl.var.bf, p.Mcap, p.Rcap, pl.var.rows, p.span, pl.var.threads, false,
+      image_smem_layout(pl.var.bf, p.Mcap, p.Rcap, pl.var.rows, p.span, var_points(pl.var), false,
                         p.dtype)
           .total;
   const int occ = occupancy(pl.var, smem);
