@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 9008640 / 256},
-    1: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 9324800 / 256},
-    2: {"sha": "ca8ef9b6a064f06a", "bytes_per_scan": 6720768 / 256},
+    0: {"sha": "cabc1fb47378795e", "bytes_per_scan": 9008896 / 256},
+    1: {"sha": "cabc1fb47378795e", "bytes_per_scan": 9324544 / 256},
+    2: {"sha": "cabc1fb47378795e", "bytes_per_scan": 6720768 / 256},
 }
 
 
@@ -597,24 +597,110 @@ def run_progressive(args, cfg, bf, uwb, torch):
             "clocks": clock_info}
 
 
+def run_multistatic(args, cfg, bf, uwb, torch):
+    """Multistatic imaging (Eq. 2, Eq. 4): every (transmit, receive) pair of
+    the ring is a channel row. The segment search against full-resolution
+    images of the same scans, both through the multistatic batch entry
+    points, with the final region's shared-load roofline."""
+    if bf == 2:
+        raise SystemExit("multistatic mode: literal-pair DMAS over channel rows is not built; "
+                         "use --beamformer das or dmas")
+    B = args.batch
+    ch = phantom.all_channels(cfg.n_antennas)
+    batch = phantom.make_batch(cfg, B, first_scan=0, channels=ch)
+    grid = cfg.grid()
+    C, N, W = len(ch), cfg.n_samples, cfg.window
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    chd = torch.from_numpy(np.ascontiguousarray(ch, dtype=np.int32)).cuda()
+    rule = uwb.uwb_default_rule()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(uwb.uwb_localize_multistatic_workspace(B, C, N, grid, bf, rule),
+                     dtype=torch.uint8, device="cuda")
+    out = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    P = int(np.prod(grid["n"]))
+    img = torch.empty(B, P, device="cuda")
+    peak = torch.empty(B, dtype=torch.int64, device="cuda")
+    fw = lambda: uwb.uwb_localize_multistatic_batch(traces, chd, ants, grid, cfg.v, cfg.fs, W,
+                                                    bf, rule, ws, out, stream=stream)
+    fr = lambda: uwb.uwb_image_multistatic_batch(bf, traces, chd, ants, grid, cfg.v, cfg.fs, W,
+                                                 img, peak, stream=stream)
+    for _ in range(args.warmup):
+        fw()
+    fr()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    uwb.uwb_phase_timing(True)
+    ms_f = _timed(torch, stream, flush, fw, args.steps)
+    calls, phase_ms = uwb.uwb_phase_times()
+    uwb.uwb_phase_timing(False)
+    ms_fr = _timed(torch, stream, flush, fr, args.fullres_steps)
+    clock_info = clocks.stop()
+    res = uwb.results_from_device(out)
+    pk = peak.cpu().numpy()
+    gx, gy = grid["n"][0], grid["n"][1]
+    full_idx = np.stack([pk % gx, (pk // gx) % gy, pk // (gx * gy)], 1)
+    per = [p / max(calls, 1) for p in phase_ms]
+    roi_points = np.prod(res["roi_hi"] - res["roi_lo"], axis=1).astype(np.float64)
+    # algorithmic wavefronts per focal point: C (W + 1) conflict-free word
+    # loads per warp of 32 points (the per-point distance table is not counted)
+    wf_final = float(roi_points.sum()) * C * (W + 1) / 32.0
+    wf_full = float(B) * P * C * (W + 1) / 32.0
+    gwf = lambda wf, ms: wf / (ms / 1e3) / 1e9 if ms > 0 else None
+    final_gwf = gwf(wf_final, per[2])
+    err = lambda xyz: float(np.mean([nearest_error_mm(xyz[k], batch["tumors"][k])
+                                     for k in range(B)]))
+    full_xyz = [[grid["origin"][a] + full_idx[k, a] * grid["pitch"][a] for a in range(3)]
+                for k in range(B)]
+    return {"metric": "localised scans/s, multistatic channels (variant, 1 GB300)",
+            "value": B / (ms_f / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_f, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(cfg, args.beamformer, B),
+                       "channels": f"all {C} (transmit, receive) pairs",
+                       "l2": "256 MB buffer written before every timed step (not timed)"},
+            "fullres": {"value": B / (ms_fr / 1e3), "unit": UNIT, "ms_per_step": ms_fr,
+                        "g_wavefronts_per_s": gwf(wf_full, ms_fr)},
+            "speedup_vs_fullres": ms_fr / ms_f,
+            "agreement_with_fullres": float(np.mean(np.all(full_idx == res["loc_idx"],
+                                                           axis=1))),
+            "loc_error_mm": {"framework": err(res["loc_xyz"]), "fullres": err(full_xyz)},
+            "points_per_scan": {"mean": float(res["points_evaluated"].mean()), "full": P},
+            "phase_ms_per_step": per,
+            "roofline": {"bound": "smem", "achieved": final_gwf, "peak": LDS_PEAK_GWF,
+                         "unit": "G wavefronts/s",
+                         "frac": final_gwf / LDS_PEAK_GWF if final_gwf else None,
+                         "kernel": "k_image multistatic final-region pass", "traffic": None,
+                         "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz"},
+            "status_ok": bool(np.all(res["status"] == 0)),
+            "clocks": clock_info}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="uwb", choices=["uwb", "reference"])
-    ap.add_argument("--config", default="dmas2d_512", choices=sorted(phantom.CONFIGS))
-    ap.add_argument("--beamformer", default="literal", choices=sorted(BEAMFORMERS))
-    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--config", default=None, choices=sorted(phantom.CONFIGS),
+                    help="workload (default dmas2d_512; ms2d_12 in multistatic mode)")
+    ap.add_argument("--beamformer", default=None, choices=sorted(BEAMFORMERS),
+                    help="default literal; dmas (identity form) in multistatic mode")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="scans per step (default 1024; 256 in multistatic mode)")
     ap.add_argument("--fullres-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-scans-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="localize",
-                    choices=["localize", "presence", "ragged", "learned", "progressive"],
+                    choices=["localize", "presence", "ragged", "learned", "progressive",
+                             "multistatic"],
                     help="presence: the two-decimation tumour-presence test; ragged: a batch "
                          "of uneven scans through the plan API; learned: the learned segment "
-                         "proposal against the plain framework")
+                         "proposal against the plain framework; multistatic: every "
+                         "(transmit, receive) pair of a ring as a channel row")
     ap.add_argument("--ragged-dim", type=int, default=2, choices=[2, 3],
                     help="ragged mode: 2-D grids (128^2-1024^2) or 128^3 cubes")
     ap.add_argument("--ragged-literal", action="store_true",
@@ -623,6 +709,13 @@ def main():
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    ms_mode = args.mode == "multistatic"
+    if args.config is None:
+        args.config = "ms2d_12" if ms_mode else "dmas2d_512"
+    if args.batch is None:
+        args.batch = 256 if ms_mode else 1024
+    if args.beamformer is None:
+        args.beamformer = "dmas" if ms_mode else "literal"
     cfg = phantom.CONFIGS[args.config]
     bf = BEAMFORMERS[args.beamformer]
     world, rank, local = dist_setup()
@@ -653,6 +746,9 @@ def main():
         return
     if args.mode == "progressive":
         print(json.dumps(run_progressive(args, cfg, bf, uwb, torch)), flush=True)
+        return
+    if args.mode == "multistatic":
+        print(json.dumps(run_multistatic(args, cfg, bf, uwb, torch)), flush=True)
         return
     batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
     grid = cfg.grid()
