@@ -38,6 +38,11 @@
  *    energies) are reported in uwb_result.status or by uwb_device_status().
  *  - Staging waits inside kernels are bounded; a kernel that gives up records
  *    UWB_ERR_TIMEOUT instead of hanging.
+ *  - Image launches with many tiles per CTA hand tiles out through a counter
+ *    taken from a per-device pool of 64 (a counter is reused only after the
+ *    launch that used it has completed). Launches captured into a CUDA graph,
+ *    or made while every counter is busy, split tiles into equal contiguous
+ *    ranges instead. Results do not depend on the split.
  */
 #ifndef UWB_H
 #define UWB_H
@@ -335,7 +340,9 @@ int uwb_localize_host(int batch, const float* traces_host, int M, int N,
  *    arguments) exceeds UWB_NOALLOC_SCRATCH_BYTES are rejected with
  *    UWB_ERR_WORKSPACE before any launch; split the batch instead.
  *  - The first call on a device looks up the address of that device's copy
- *    of the array; make that first call before any stream capture.
+ *    of the array and creates the library's events for that device (as the
+ *    first call of any entry point does); make that first call before any
+ *    stream capture.
  *  - Every call on a device uses the same array, and the array keeps the
  *    last call's contents (each call clears what it needs zeroed). Calls
  *    that overlap on the GPU (other streams, other host threads) race on

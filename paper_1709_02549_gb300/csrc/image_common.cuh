@@ -599,6 +599,22 @@ __device__ __forceinline__ void make_desc(const ImgParams& P, int scan, ScanDesc
   }
 }
 
+// A CTA takes a dynamic share of the tiles only when the launch has at least
+// this many per CTA; below it (the decimated profiles: about 3 tiles per scan)
+// a contiguous range stages each scan's window once, which costs less.
+constexpr long long kDynMinTiles = 16;
+
+// The scan that tile g of a ragged or boxed launch belongs to: the largest
+// scan with prefix[scan] <= g (empty scans share their successor's prefix).
+__device__ __forceinline__ int scan_of_tile(const ImgParams& P, long long g) {
+  int lo = 0, hi = P.B;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P.prefix[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------------------ the kernel
 // V = window chunk WT (DAS, DMAS identity) or antenna register block MMAX
 // (literal DMAS); MS = multistatic rows. Dynamic shared memory as laid out by
@@ -665,20 +681,26 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
 
   const long long total =
       P.boxes ? static_cast<long long>(P.prefix[P.B]) : static_cast<long long>(P.B) * P.uni.tiles;
-  const long long chunk = (total + gridDim.x - 1) / gridDim.x;
-  const long long g_begin = static_cast<long long>(blockIdx.x) * chunk;
-  const long long g_end = min(total, g_begin + chunk);
-  if (g_begin >= g_end) return;
-
-  int scan = 0;
-  if (P.boxes) {  // largest scan with prefix[scan] <= g_begin
-    int lo = 0, hi = P.B;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (P.prefix[mid] <= g_begin) lo = mid; else hi = mid;
-    }
-    scan = lo;
+  // Work split. The CTAs that share an SM do not advance at equal rates: its
+  // warp schedulers favour some of them. With equal contiguous ranges the
+  // favoured CTAs finish early and the last one runs alone: on the 512 x 512
+  // literal-DMAS final regions, the first CTA of every SM ended at 42 % of the
+  // kernel's time and 2.9 of 4 CTAs were resident on average. With a tile
+  // counter (P.work, zero at launch) and enough tiles per CTA, every CTA
+  // instead takes chunks of consecutive tiles as it frees up. Chunks shrink
+  // with the work left (guided self-scheduling: an eighth of an even share
+  // of it, at least 2 tiles), so scans are rarely staged twice and the CTAs
+  // end within a chunk of each other.
+  const bool dyn = P.work != nullptr && total >= kDynMinTiles * static_cast<long long>(gridDim.x);
+  long long g_begin = 0, g_end = 0;
+  if (!dyn) {
+    const long long chunk = (total + gridDim.x - 1) / gridDim.x;
+    g_begin = static_cast<long long>(blockIdx.x) * chunk;
+    g_end = min(total, g_begin + chunk);
+    if (g_begin >= g_end) return;
   }
+
+  int scan = P.boxes ? scan_of_tile(P, g_begin) : 0;
   int staged = -1;
   bool fits = false;
   int nlo = 0, cl_lo = 0, cl_hi = 0;
@@ -686,7 +708,24 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
   // the CTA reduces it once per scan, not once per tile
   unsigned long long run_key = 0ull;
 
-  for (long long g = g_begin; g < g_end; ++g) {
+  for (long long g = g_begin;; ++g) {
+    if (g >= g_end) {
+      if (!dyn) break;
+      // the next chunk; every thread reads it after the barrier, and the
+      // barrier before it keeps the previous chunk's values until all have
+      __syncthreads();
+      if (tid == 0) {
+        const long long left = total - *reinterpret_cast<volatile int*>(P.work);
+        const int c = static_cast<int>(max(2LL, left / (8LL * gridDim.x)));
+        sInt[2] = atomicAdd(P.work, c);
+        sInt[3] = c;
+      }
+      __syncthreads();
+      g = sInt[2];
+      if (g >= total) break;
+      g_end = min(total, g + sInt[3]);
+      if (P.boxes) scan = scan_of_tile(P, g);
+    }
     long long t;
     if (P.boxes) {
       while (P.prefix[scan + 1] <= g) ++scan;
@@ -947,8 +986,8 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
                      : 0ull;
         run_key = key > run_key ? key : run_key;
       }
-      // the CTA's tiles are contiguous: reduce when its last tile of this
-      // scan is done (uniform across the CTA)
+      // a range or chunk holds consecutive tiles: reduce when its last tile
+      // of this scan is done (uniform across the CTA)
       const bool scan_ends =
           g + 1 == g_end || (P.boxes ? P.prefix[scan + 1] <= g + 1
                                      : (g + 1) % P.uni.tiles == 0);

@@ -17,6 +17,11 @@
 // record UWB_ERR_TIMEOUT here when a bounded staging wait runs out.
 __device__ int g_uwb_status_word;
 
+// Tile counters of the image kernel's dynamic work split, one per launch in
+// flight (see take_counter).
+constexpr int kCounterSlots = 64;
+__device__ int g_uwb_tile_counters[kCounterSlots];
+
 namespace uwb {
 namespace {
 
@@ -38,6 +43,12 @@ struct Device {
   bool ready = false;
   int sms = 0;
   int* status = nullptr;
+  // tile counters: slot k is free once ev[k], recorded behind the last
+  // launch that used it, has completed
+  int* counters = nullptr;
+  cudaEvent_t ev[kCounterSlots] = {};
+  int next = 0;
+  std::mutex counter_mu;
 };
 
 std::mutex g_mu;
@@ -57,6 +68,14 @@ int device(Device** out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&dev.status), g_uwb_status_word);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&dev.counters), g_uwb_tile_counters);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    // a slot whose event cannot be created is never used
+    for (cudaEvent_t& ev : dev.ev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ev = nullptr;
+      }
     dev.ready = true;
   }
   if (!g_encode_tried) {
@@ -430,7 +449,54 @@ ImgParams base_params(const Geo& geo, const float* traces, const float* ant,
   return p;
 }
 
-int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
+// A free tile-counter slot of the device, or -1. Called with counter_mu held.
+// The caller zeroes the slot on its stream, launches, and records ev[slot]
+// behind the launch before releasing the lock, so a slot never serves two
+// launches at once. While `st` is being captured into a graph no slot is
+// taken (a captured launch would replay with one slot forever): the kernel
+// then splits its tiles statically.
+int take_counter(Device& dev, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return -1;
+  for (int k = 0; k < kCounterSlots; ++k) {
+    const int slot = (dev.next + k) % kCounterSlots;
+    if (!dev.ev[slot]) continue;
+    const cudaError_t q = cudaEventQuery(dev.ev[slot]);  // an unrecorded event is complete
+    if (q == cudaErrorNotReady) {
+      if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+      continue;
+    }
+    if (q != cudaSuccess) return -1;
+    dev.next = slot + 1;
+    return slot;
+  }
+  return -1;
+}
+
+// Launches the image kernel with a zeroed tile counter when one is free (the
+// kernel then balances its tiles dynamically where it has enough of them),
+// else with the static split. Tile counts near 2^31 keep the static split.
+cudaError_t launch_balanced(Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
+                            int ctas, size_t smem, long long work_bound, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(dev.counter_mu);
+  const int slot = work_bound < (1LL << 30) ? take_counter(dev, st) : -1;
+  p.work = nullptr;
+  if (slot >= 0) {
+    const cudaError_t e = cudaMemsetAsync(dev.counters + slot, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    p.work = dev.counters + slot;
+  }
+  const cudaError_t e = launch(var, p, map, ctas, smem, st);
+  if (e != cudaSuccess) return e;
+  if (slot >= 0) return cudaEventRecord(dev.ev[slot], st);
+  return cudaSuccess;
+}
+
+int run_image_kernel(Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
                      long long work_bound, const double step[3], cudaStream_t st) {
   double delta[3];
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
@@ -443,7 +509,7 @@ int run_image_kernel(const Device& dev, const Variant& var, ImgParams& p, const 
   long long ctas = static_cast<long long>(dev.sms) * occ;
   if (work_bound < ctas) ctas = work_bound;
   if (ctas < 1) return UWB_OK;
-  cudaError_t e = launch(var, p, map, static_cast<int>(ctas), smem, st);
+  cudaError_t e = launch_balanced(dev, var, p, map, static_cast<int>(ctas), smem, work_bound, st);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }
@@ -909,7 +975,8 @@ int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const in
   if (ctas < 1) return UWB_OK;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);
-  cudaError_t e = launch(pl.var, p, &dummy, static_cast<int>(ctas), smem, cs);
+  cudaError_t e =
+      launch_balanced(*dev, pl.var, p, &dummy, static_cast<int>(ctas), smem, work_bound, cs);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }
@@ -1813,7 +1880,7 @@ int check_learn_grid(const uwb_grid* g, int levels) {
 
 // One pass of the DAS image kernel over a 32 x 32 lattice per scan, written
 // compactly to maps[B][32][32]: the uniform lattice `uni`, or per-scan boxes.
-int run_map_pass(const Device& dev, const Geo& geo, const float* traces, const float* ant,
+int run_map_pass(Device& dev, const Geo& geo, const float* traces, const float* ant,
                  long long ant_stride, const Variant& vm, int span, int use_tma,
                  const CUtensorMap* map, const LatBox* uni, const LatBox* boxes,
                  const int* prefix, float* maps, int* status, int step, cudaStream_t cs) {

@@ -95,6 +95,7 @@ struct ImgParams {
   long long compact_stride;  // floats between scans in `compact`
   unsigned long long* keys;  // [B] argmax keys or nullptr
   int* status;               // device status word
+  int* work;                 // tile counter, zero at launch (dynamic split), or nullptr
   int dtype;                 // DT_* of the traces
   const ScanDesc* descs;     // ragged batches: [B] per-scan descriptors (device), else nullptr
   const CUtensorMap* tmaps;  // ragged batches: per-scan tensor maps (device), or nullptr
