@@ -45,9 +45,9 @@ LDS_PEAK_GWF = SMS * SM_MAX_GHZ
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "d8a403dca82f3e4e", "bytes_per_scan": 9012736 / 256},
-    1: {"sha": "d8a403dca82f3e4e", "bytes_per_scan": (9326592 + 256) / 256},
-    2: {"sha": "d8a403dca82f3e4e", "bytes_per_scan": 6724096 / 256},
+    0: {"sha": "2b7ae1fa39558a41", "bytes_per_scan": 9011456 / 256},
+    1: {"sha": "2b7ae1fa39558a41", "bytes_per_scan": 9327360 / 256},
+    2: {"sha": "2b7ae1fa39558a41", "bytes_per_scan": 6723328 / 256},
 }
 
 

@@ -38,11 +38,12 @@
  *    energies) are reported in uwb_result.status or by uwb_device_status().
  *  - Staging waits inside kernels are bounded; a kernel that gives up records
  *    UWB_ERR_TIMEOUT instead of hanging.
- *  - Image launches with many tiles per CTA hand tiles out through a counter
- *    taken from a per-device pool of 64 (a counter is reused only after the
- *    launch that used it has completed). Launches captured into a CUDA graph,
- *    or made while every counter is busy, split tiles into equal contiguous
- *    ranges instead. Results do not depend on the split.
+ *  - Image launches with at least 4 tiles per CTA and several CTAs per SM
+ *    hand tiles out through a counter taken from a per-device pool of 64 (a
+ *    counter is reused only after the launch that used it has completed).
+ *    Launches captured into a CUDA graph, or made while every counter is
+ *    busy, split tiles into equal contiguous ranges instead. Results do not
+ *    depend on the split.
  */
 #ifndef UWB_H
 #define UWB_H

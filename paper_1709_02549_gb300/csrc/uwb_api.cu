@@ -479,11 +479,14 @@ int take_counter(Device& dev, cudaStream_t st) {
 
 // Launches the image kernel with a zeroed tile counter when one is free (the
 // kernel then balances its tiles dynamically where it has enough of them),
-// else with the static split. Tile counts near 2^31 keep the static split.
+// else with the static split. The counter evens out CTAs that share an SM;
+// with one CTA per SM (per_sm == 1, the multistatic instances) the static
+// split measured 2-4 % faster. Tile counts near 2^31 keep the static split.
 cudaError_t launch_balanced(Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
-                            int ctas, size_t smem, long long work_bound, cudaStream_t st) {
+                            int ctas, int per_sm, size_t smem, long long work_bound,
+                            cudaStream_t st) {
   std::lock_guard<std::mutex> lk(dev.counter_mu);
-  const int slot = work_bound < (1LL << 30) ? take_counter(dev, st) : -1;
+  const int slot = (per_sm >= 2 && work_bound < (1LL << 30)) ? take_counter(dev, st) : -1;
   p.work = nullptr;
   if (slot >= 0) {
     const cudaError_t e = cudaMemsetAsync(dev.counters + slot, 0, sizeof(int), st);
@@ -509,7 +512,8 @@ int run_image_kernel(Device& dev, const Variant& var, ImgParams& p, const CUtens
   long long ctas = static_cast<long long>(dev.sms) * occ;
   if (work_bound < ctas) ctas = work_bound;
   if (ctas < 1) return UWB_OK;
-  cudaError_t e = launch_balanced(dev, var, p, map, static_cast<int>(ctas), smem, work_bound, st);
+  cudaError_t e =
+      launch_balanced(dev, var, p, map, static_cast<int>(ctas), occ, smem, work_bound, st);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }
@@ -976,7 +980,7 @@ int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const in
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);
   cudaError_t e =
-      launch_balanced(*dev, pl.var, p, &dummy, static_cast<int>(ctas), smem, work_bound, cs);
+      launch_balanced(*dev, pl.var, p, &dummy, static_cast<int>(ctas), occ, smem, work_bound, cs);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }

@@ -5,8 +5,8 @@ With a tile counter the persistent CTAs take chunks of tiles as they free up;
 without one (under stream capture, or with every counter busy) each CTA takes
 an equal contiguous range. Only the order in which tiles are evaluated
 differs, so images, argmaxes and localisations must be byte-identical. The
-launches here have at least 16 tiles per CTA, the point from which the kernel
-splits dynamically."""
+launches here have at least 16 tiles per CTA (the kernel splits dynamically
+from 4) and run several CTAs per SM."""
 import numpy as np
 import pytest
 import torch
