@@ -39,6 +39,8 @@ SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 # Derived shared-load peak: one 128-byte wavefront per clock per SM.
 LDS_PEAK_GWF = SMS * SM_MAX_GHZ
+# Derived FP32-pipe peak in operations (a fused multiply-add is one): 152 x 128 x 2.07 GHz.
+FP32_PIPE_PEAK_TOPS = SMS * FP32_LANES * SM_MAX_GHZ / 1e3
 
 # DRAM traffic of the final-region kernel per scan, per beamformer (0 DAS,
 # 1 identity DMAS, 2 literal DMAS), from ncu captures (dmas2d_512, 256 scans)
@@ -109,6 +111,65 @@ def flops_per_point(bf: int, M: int, W: int) -> float:
     else:
         combine = W * M * (M - 1)
     return float(per_antenna + combine + 2 * W)
+
+
+def fp32_ops_per_point(bf: int, M: int, W: int, channels: int = 0) -> float:
+    """FP32-pipe operations of one focal point of DAS (bf 0) or identity DMAS
+    (bf 1), a fused multiply-add counting once. Monostatic (channels = 0): per
+    antenna 8 for the delay (3 subtractions, 3 for the squared distance, the
+    scaled offset, the fraction). Multistatic (channels = C rows over M
+    antennas): per antenna 6 for the distance, per channel 3 (the distance
+    sum, the scaled offset, the fraction). Then per row and window sample the
+    interpolation and the sums (DAS: the weight 1 - f once, then 2
+    multiply-adds per sample; identity DMAS: the difference, the interpolating
+    multiply-add, the sum and the square sum); then per sample the window
+    energy (DAS 1; identity DMAS 4: the square, the difference with the square
+    sum, the halving, the multiply-add)."""
+    per_row = (1 + 2 * W) if bf == 0 else 4 * W
+    energy = W if bf == 0 else 4 * W
+    if channels:
+        return float(M * 6 + channels * (3 + per_row) + energy)
+    return float(M * (8 + per_row) + energy)
+
+
+def load_or_alu_roofline(n_pts: float, rows: int, W: int, ops_per_point: float,
+                         launch_ms: float, lds_meas: float, fma_meas: float) -> dict:
+    """Roofline of a DAS or identity-DMAS image pass over n_pts focal points.
+    Two resources, each with its algorithmic demand per focal point: shared
+    memory loads, rows (W + 1) conflict-free word loads per warp of 32 points
+    (rows (W + 1) / 32 wavefronts, one wavefront per clock per SM), and the FP32
+    pipe, ops_per_point operations at 128 per clock per SM. The resource with
+    the larger demand binds; the other is reported beside it."""
+    wf = n_pts * rows * (W + 1) / 32.0
+    ops = n_pts * ops_per_point
+    lds_clk = rows * (W + 1) / 32.0
+    alu_clk = ops_per_point / FP32_LANES
+    sec = launch_ms / 1e3 if launch_ms and launch_ms > 0 else None
+    gwf = wf / sec / 1e9 if sec else None
+    tops = ops / sec / 1e12 if sec else None
+    smem = {"achieved": gwf, "peak": LDS_PEAK_GWF, "unit": "G wavefronts/s",
+            "frac": gwf / LDS_PEAK_GWF if gwf else None,
+            "measured_peak": lds_meas / 1e9,
+            "frac_of_measured": gwf / (lds_meas / 1e9) if gwf else None,
+            "measured_peak_source": "uwb_measure_peaks: conflict-free 32-bit shared loads",
+            "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz",
+            "per_launch": wf, "sm_clocks_per_point_at_peak": lds_clk}
+    alu = {"achieved": tops, "peak": FP32_PIPE_PEAK_TOPS, "unit": "T FP32-pipe ops/s",
+           "frac": tops / FP32_PIPE_PEAK_TOPS if tops else None,
+           "measured_peak": fma_meas / 2,
+           "frac_of_measured": tops / (fma_meas / 2) if tops else None,
+           "measured_peak_source": "uwb_measure_peaks: independent __ffma2_rn chains "
+                                   "(TFLOP/s / 2)",
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+           "per_launch": ops, "sm_clocks_per_point_at_peak": alu_clk}
+    bind_smem = lds_clk >= alu_clk
+    bind, other = (smem, alu) if bind_smem else (alu, smem)
+    out = {k: bind[k] for k in ("achieved", "peak", "unit", "frac", "measured_peak",
+                                "frac_of_measured", "measured_peak_source", "peak_source")}
+    out.update({"bound": "smem" if bind_smem else "alu",
+                "wavefronts_per_launch": wf, "fp32_pipe_ops_per_launch": ops,
+                "other_resource": {"name": "alu" if bind_smem else "smem", **other}})
+    return out
 
 
 class ClockSampler:
@@ -601,7 +662,7 @@ def run_multistatic(args, cfg, bf, uwb, torch):
     """Multistatic imaging (Eq. 2, Eq. 4): every (transmit, receive) pair of
     the ring is a channel row. The segment search against full-resolution
     images of the same scans, both through the multistatic batch entry
-    points, with the final region's shared-load roofline."""
+    points, with the final region's roofline (shared loads or the FP32 pipe)."""
     if bf == 2:
         raise SystemExit("multistatic mode: literal-pair DMAS over channel rows is not built; "
                          "use --beamformer das or dmas")
@@ -609,7 +670,7 @@ def run_multistatic(args, cfg, bf, uwb, torch):
     ch = phantom.all_channels(cfg.n_antennas)
     batch = phantom.make_batch(cfg, B, first_scan=0, channels=ch)
     grid = cfg.grid()
-    C, N, W = len(ch), cfg.n_samples, cfg.window
+    C, N, W, M = len(ch), cfg.n_samples, cfg.window, cfg.n_antennas
     traces = torch.from_numpy(batch["traces"]).cuda()
     ants = torch.from_numpy(batch["antennas"]).cuda()
     chd = torch.from_numpy(np.ascontiguousarray(ch, dtype=np.int32)).cuda()
@@ -638,6 +699,7 @@ def run_multistatic(args, cfg, bf, uwb, torch):
     uwb.uwb_phase_timing(False)
     ms_fr = _timed(torch, stream, flush, fr, args.fullres_steps)
     clock_info = clocks.stop()
+    fma_meas, lds_meas = uwb.uwb_measure_peaks()
     res = uwb.results_from_device(out)
     pk = peak.cpu().numpy()
     gx, gy = grid["n"][0], grid["n"][1]
@@ -669,11 +731,11 @@ def run_multistatic(args, cfg, bf, uwb, torch):
             "loc_error_mm": {"framework": err(res["loc_xyz"]), "fullres": err(full_xyz)},
             "points_per_scan": {"mean": float(res["points_evaluated"].mean()), "full": P},
             "phase_ms_per_step": per,
-            "roofline": {"bound": "smem", "achieved": final_gwf, "peak": LDS_PEAK_GWF,
-                         "unit": "G wavefronts/s",
-                         "frac": final_gwf / LDS_PEAK_GWF if final_gwf else None,
-                         "kernel": "k_image multistatic final-region pass", "traffic": None,
-                         "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz"},
+            "roofline": {"kernel": "k_image multistatic final-region pass", "traffic": None,
+                         "launch_ms": per[2],
+                         **load_or_alu_roofline(float(roi_points.sum()), C, W,
+                                                fp32_ops_per_point(bf, M, W, channels=C),
+                                                per[2], lds_meas, fma_meas)},
             "status_ok": bool(np.all(res["status"] == 0)),
             "clocks": clock_info}
 
@@ -829,21 +891,14 @@ def main():
         "kernel_sha": sha,
     }
     if bf != 2:
-        # DAS and identity DMAS: bound by shared-memory loads. Algorithmic
-        # wavefronts per focal point: M (W + 1) conflict-free word loads per
-        # warp of 32 points, i.e. M (W + 1) / 32 per point.
-        wf = float(roi_points.sum()) * M * (cfg.window + 1) / 32.0
-        achieved_gwf = wf / (final_ms / 1e3) / 1e9 if final_ms > 0 else None
-        roofline.update({
-            "bound": "smem", "achieved": achieved_gwf, "peak": LDS_PEAK_GWF,
-            "unit": "G wavefronts/s",
-            "frac": achieved_gwf / LDS_PEAK_GWF if achieved_gwf else None,
-            "measured_peak": lds_meas / 1e9,
-            "frac_of_measured": achieved_gwf / (lds_meas / 1e9) if achieved_gwf else None,
-            "measured_peak_source": "uwb_measure_peaks: conflict-free 32-bit shared loads",
-            "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz",
-            "wavefronts_per_launch": wf,
-            "tflops_achieved": achieved_tflops})
+        # DAS and identity DMAS: shared loads or the FP32 pipe, whichever has the
+        # larger algorithmic demand per point (at 32 antennas and W = 20, DAS 21
+        # shared-load against 12.4 FP32-pipe SM clocks per point; identity DMAS
+        # 21 against 22.6)
+        roofline.update(load_or_alu_roofline(
+            float(roi_points.sum()), M, cfg.window, fp32_ops_per_point(bf, M, cfg.window),
+            final_ms, lds_meas, fma_meas))
+        roofline["tflops_achieved"] = achieved_tflops
 
     # ---- full-resolution GPU images of the same scans (same beamformer) ----
     P = int(np.prod(grid["n"]))
