@@ -36,3 +36,33 @@ def test_kernel_hash_follows_code_not_comments():
     assert bench.code_only(src) != bench.code_only(src.replace("a + 1", "a + 2"))
     assert '"x//y"' in bench.code_only(src)
     assert len(bench.kernel_sha()) == 16
+
+
+def test_image_roofline_takes_the_resource_with_the_larger_demand():
+    """DAS and identity-DMAS bench lines: the operation count per focal point by
+    hand, and the binding resource chosen by demand per point (shared-load
+    wavefronts M (W + 1) / 32 against FP32-pipe operations / 128)."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    # DAS, M = 32, W = 20: per antenna 3 + 3 + 1 + 1 (delay) + 1 (1 - f) + 40;
+    # per point 20 energy multiply-adds
+    assert bench.fp32_ops_per_point(0, 32, 20) == 32 * 49 + 20 == 1588
+    # identity DMAS: per antenna 8 + 4 x 20, per point 4 x 20
+    assert bench.fp32_ops_per_point(1, 32, 20) == 32 * 88 + 80 == 2896
+    # multistatic, 12 antennas and 144 channels: 6 per antenna, 3 + 80 per channel
+    assert bench.fp32_ops_per_point(1, 12, 20, channels=144) == 72 + 144 * 83 + 80
+    n_pts, ms = 1.0e6, 2.0
+    das = bench.load_or_alu_roofline(n_pts, 32, 20, 1588.0, ms, 312e9, 78.0)
+    idm = bench.load_or_alu_roofline(n_pts, 32, 20, 2896.0, ms, 312e9, 78.0)
+    assert das["bound"] == "smem" and das["other_resource"]["name"] == "alu"
+    assert idm["bound"] == "alu" and idm["other_resource"]["name"] == "smem"
+    wf = n_pts * 32 * 21 / 32
+    assert das["wavefronts_per_launch"] == idm["wavefronts_per_launch"] == wf
+    assert abs(das["achieved"] - wf / 2e-3 / 1e9) < 1e-9
+    assert abs(das["frac"] - das["achieved"] / bench.LDS_PEAK_GWF) < 1e-12
+    assert abs(idm["achieved"] - n_pts * 2896 / 2e-3 / 1e12) < 1e-12
+    assert abs(idm["frac"] - idm["achieved"] / bench.FP32_PIPE_PEAK_TOPS) < 1e-12
+    # the measured FP32 ceiling is quoted in TFLOP/s: a multiply-add is 2 FLOP, 1 operation
+    assert abs(idm["measured_peak"] - 39.0) < 1e-12
+    # both resources are reported whichever binds
+    assert abs(idm["other_resource"]["frac"] - das["frac"]) < 1e-12
