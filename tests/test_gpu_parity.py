@@ -171,6 +171,29 @@ def test_localize_512_grid_with_clutter(gpu, bf):
         assert r["points_evaluated"] < 512 * 512 / 4
 
 
+def test_benchmark_batch_sampled_scans_match_oracle(gpu):
+    """The benchmark's timed launch itself: 1024 scans of the 512 x 512
+    workload (32 antennas, 2048 samples, clutter) in one literal-DMAS batch,
+    whose final regions the tile counter splits dynamically. Every scan must
+    succeed, and sampled scans must match the oracle's decisions, region and
+    location one by one."""
+    cfg = phantom.CONFIGS["dmas2d_512"]
+    batch = phantom.make_batch(cfg, 1024, first_scan=0)
+    grid = cfg.grid()
+    g_rule, o_rule = rule_pair(gpu)
+    res = gpu_localize_batch(gpu, 2, batch["traces"], batch["antennas"], grid, cfg.v, cfg.fs,
+                             cfg.window, g_rule)
+    assert all(int(r["status"]) == 0 for r in res)
+    ties = 0
+    for s in (0, 137, 511, 700, 901, 1023):
+        tr = batch["traces"][s]
+        o = oracle.localize(tr, batch["antennas"], grid, cfg.v, cfg.fs, cfg.window, oracle.DMAS,
+                            o_rule)
+        ties += compare_localize(res[s], o, _energy_at(tr, batch["antennas"], grid, cfg.v,
+                                                        cfg.fs, cfg.window, 2))["tie"]
+    assert ties <= 1, f"{ties} near-ties in 6 sampled scans"
+
+
 def test_localize_writes_the_mixed_resolution_image(gpu):
     cfg = phantom.CONFIGS["das2d_64"]
     sc = phantom.make_scan(cfg, phantom.BASE_SEED + 2)

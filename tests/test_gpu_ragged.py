@@ -87,6 +87,34 @@ def test_ragged_localize_matches_oracle(gpu, dtype, bf):
     plan.close()
 
 
+def test_benchmark_ragged_batch_sampled_scans_match_oracle(gpu):
+    """The benchmark's ragged workload itself: 256 uneven scans (16-96
+    antennas, 1024-4096 samples, 128^2-1024^2 grids, clutter) in one plan with
+    identity DMAS, float32 traces. Every scan must succeed, and sampled scans
+    must match the oracle's decisions, region and location one by one."""
+    cfgs = phantom.ragged_configs(256, dim=2)
+    scans = [(c, phantom.make_scan(c, phantom.BASE_SEED + 200000 + k)) for k, c in enumerate(cfgs)]
+    g_rule, o_rule = rule_pair(gpu)
+    plan, host = plan_for(gpu, scans, "f32", 1, g_rule)
+    out = torch.empty(len(scans) * gpu.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    plan.localize(out)
+    torch.cuda.synchronize()
+    res = [record_to_dict(r) for r in gpu.results_from_device(out)]
+    plan.close()
+    assert all(r["status"] == 0 for r in res)
+    ties = 0
+    for k in (3, 77, 150, 255):
+        cfg, sc = scans[k]
+        o = oracle.localize(host[k], sc["antennas"], cfg.grid(), cfg.v, cfg.fs, cfg.window,
+                            oracle.DMAS, o_rule)
+
+        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
+            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, oracle.DMAS, lo=idx,
+                                      cnt=[1, 1, 1])[0, 0, 0])
+        ties += compare_localize(res[k], o, energy_at)["tie"]
+    assert ties <= 1, f"{ties} near-ties in 4 sampled scans"
+
+
 def test_ragged_plan_of_equal_scans_equals_the_uniform_batch(gpu):
     cfg = phantom.CONFIGS["dmas2d_512"]
     batch = phantom.make_batch(cfg, 3)
