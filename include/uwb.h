@@ -383,6 +383,19 @@ const char* uwb_last_error(void);
  * UWB_OK or UWB_ERR_CUDA. */
 int uwb_measure_peaks(double* fp32_tflops, double* shared_wavefronts_per_s);
 
+/* Failure-detection self-check (no counterpart in the paper): shows that a
+ * bounded device wait that runs out is reported and leaves the context usable.
+ * One warp waits on a shared-memory mbarrier that nothing ever completes,
+ * probing it with the bounded try-wait loop of the image kernels' staging wait
+ * at most `probes` times (1 .. 2^24; each probe returns within a short
+ * hardware time limit). The kernel then records UWB_ERR_TIMEOUT in the device
+ * status word, exactly as a staging wait that runs out does, and returns.
+ * Synchronous on the current device. Read the outcome with
+ * uwb_device_status(); clear it there before further work. Returns UWB_OK
+ * once the kernel has finished, UWB_ERR_ARG for probes outside 1 .. 2^24
+ * (before any launch), or UWB_ERR_CUDA. */
+int uwb_wait_selftest(int probes);
+
 /* Progressive re-evaluation: a variant of uwb_localize_batch (the paper's
  * selection loop reads only the decimated profile). Iteration 1 is the
  * paper's. Every later iteration first images again the region being split on

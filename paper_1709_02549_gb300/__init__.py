@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
             "uwb_phase_times": (i, [ctypes.POINTER(ctypes.c_double)]),
             "uwb_last_error": (ctypes.c_char_p, []),
             "uwb_measure_peaks": (i, [ctypes.POINTER(ctypes.c_double)] * 2),
+            "uwb_wait_selftest": (i, [i]),
             "uwb_cnn_selftest": (i, [ctypes.POINTER(ctypes.c_int)]),
             "uwb_cnn_pack": (i, [vp, vp, vp]),
             "uwb_cnn_forward": (i, [vp, vp, i, vp, vp]),
@@ -643,6 +644,12 @@ def uwb_localize_learned(traces, antennas, grid, v, fs, window, beamformer, rule
                                       _ptr(packed, "packed"), float(threshold), int(levels),
                                       _ptr(workspace, "workspace"), _nbytes(workspace),
                                       _ptr(out, "out"), _stream(stream)), "uwb_localize_learned")
+
+
+def uwb_wait_selftest(probes: int) -> None:
+    """Bounded-wait self-check: a wait that nothing completes runs out after
+    `probes` probes and records UWB_ERR_TIMEOUT in the device status word."""
+    _check(lib().uwb_wait_selftest(int(probes)), "uwb_wait_selftest")
 
 
 def uwb_measure_peaks():

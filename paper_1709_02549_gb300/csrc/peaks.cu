@@ -6,6 +6,7 @@
 // roofline fractions; the paper has no counterpart.
 #include <cuda_runtime.h>
 
+#include "ptx.cuh"
 #include "uwb_internal.cuh"
 
 namespace uwb {
@@ -59,6 +60,20 @@ __global__ void __launch_bounds__(256) k_peak_lds(float* out, int iters) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Failure-detection self-check: one warp waits on a shared-memory mbarrier
+// that nothing ever completes (arrival count 1, no arrival), probing it with
+// the same bounded try-wait loop as the image kernels' staging wait, at most
+// `probes` times. When the probes run out it records UWB_ERR_TIMEOUT in the
+// status word and returns, as the staging wait does.
+__global__ void __launch_bounds__(32) k_wait_selftest(int* status, long probes) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t ok = 0;
+  for (long it = 0; it < probes && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(status, UWB_ERR_TIMEOUT);
+}
+
 float time_ms(cudaEvent_t e0, cudaEvent_t e1) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -100,6 +115,13 @@ cudaError_t measure_peaks(int sms, double* tflops, double* wavefronts_per_s) {
   const double wavefronts = static_cast<double>(blocks) * (256 / 32) * lds_iters * kLdsUnroll;
   *wavefronts_per_s = wavefronts / (lds_ms * 1e-3);
   return cudaSuccess;
+}
+
+// Runs k_wait_selftest on the current device and waits for it.
+cudaError_t wait_selftest(int* status, long probes) {
+  k_wait_selftest<<<1, 32>>>(status, probes);
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : cudaDeviceSynchronize();
 }
 
 }  // namespace uwb

@@ -2348,4 +2348,14 @@ int uwb_measure_peaks(double* fp32_tflops, double* shared_wavefronts_per_s) {
   return e == cudaSuccess ? UWB_OK : cuda_fail(e, "peak microbenchmarks");
 }
 
+int uwb_wait_selftest(int probes) {
+  if (probes < 1 || probes > (1 << 24))
+    return fail(UWB_ERR_ARG, "probes must lie in 1 .. 2^24 (got %d)", probes);
+  Device* dev;
+  int st = device(&dev);
+  if (st) return st;
+  const cudaError_t e = wait_selftest(dev->status, probes);
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "bounded-wait self-check");
+}
+
 }  // extern "C"

@@ -255,6 +255,7 @@ int occupancy_image_literal(int v, bool rg, int threads, size_t smem);
 cudaError_t launch_select(const SelParams& p, cudaStream_t st);
 cudaError_t launch_prog_step(const ProgParams& p, int iteration, cudaStream_t st);
 cudaError_t measure_peaks(int sms, double* tflops, double* wavefronts_per_s);
+cudaError_t wait_selftest(int* status, long probes);
 cudaError_t launch_plan(const LatBox* boxes, int* prefix, int B, cudaStream_t st);
 cudaError_t launch_finish(const FinishParams& p, const int* status, cudaStream_t st);
 cudaError_t launch_keys_to_index(unsigned long long* keys, int B, cudaStream_t st);

@@ -144,3 +144,10 @@ def test_learned_proposal_arguments_are_rejected_on_the_host(uwb):
                              fake, None, 0, None) == uwb.UWB_ERR_ARG
     assert L.uwb_coarse_maps(4, fake, 8, 256, fake, 0, ctypes.byref(sq), 1e8, 5e10, 4, fake, 64,
                              fake, None, 0, None) == uwb.UWB_ERR_WORKSPACE
+
+
+def test_wait_selftest_rejects_probe_counts_on_the_host(uwb):
+    L = uwb.lib()
+    for probes in (0, -5, (1 << 24) + 1):
+        assert L.uwb_wait_selftest(probes) == uwb.UWB_ERR_ARG
+        assert "probes" in uwb.uwb_last_error()

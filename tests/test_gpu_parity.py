@@ -241,6 +241,18 @@ def test_localize_edge_cases(gpu):
     assert res[0]["loc_idx"] == res[3]["loc_idx"]
 
 
+def test_bounded_wait_that_runs_out_is_reported_and_the_context_stays_usable(gpu):
+    """Failure detection without a fault: a device wait that nothing completes
+    gives up after its probe limit, the kernel records UWB_ERR_TIMEOUT in the
+    status word and returns, and the same context then localises as before."""
+    assert gpu.uwb_device_status(clear=True) == 0
+    gpu.uwb_wait_selftest(4096)
+    assert gpu.uwb_device_status(clear=True) == gpu.UWB_ERR_TIMEOUT
+    assert gpu.uwb_device_status() == 0
+    _check_batch(gpu, phantom.CONFIGS["das2d_64"], 2, range(3))
+    assert gpu.uwb_device_status() == 0
+
+
 def test_localize_degenerate_grids(gpu):
     tr, ants, _, v, fs, W = random_case(4, 256, (1, 1, 1), 0.05, 6, seed=3)
     for n in [(1, 1, 1), (2, 1, 1), (5, 3, 1)]:
