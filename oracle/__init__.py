@@ -94,6 +94,33 @@ class Result(ctypes.Structure):
         }
 
 
+class Path(ctypes.Structure):
+    """orc_path: a trajectory for the selection loop to follow (test aid for
+    near-ties; see oracle.h)."""
+    _fields_ = [("n", ctypes.c_int), ("child", IT), ("cont", IT), ("error", ctypes.c_int),
+                ("own_child", IT), ("own_cont", IT), ("taken_metric", DT), ("taken_gap", DT)]
+
+
+def make_path(child, cont=None) -> Path:
+    """child[i] / cont[i] for iteration i + 1; -1 (or None for cont) leaves
+    the oracle's own outcome."""
+    child = list(child)
+    cont = [-1] * len(child) if cont is None else list(cont)
+    assert len(child) == len(cont) <= MAX_ITERS
+    p = Path()
+    p.n = len(child)
+    for i, (c, k) in enumerate(zip(child, cont)):
+        p.child[i] = int(c)
+        p.cont[i] = int(k)
+    return p
+
+
+def _path_log(p: Path, n: int) -> dict:
+    return {"error": p.error, "own_child": list(p.own_child)[:n],
+            "own_cont": list(p.own_cont)[:n], "taken_metric": list(p.taken_metric)[:n],
+            "taken_gap": list(p.taken_gap)[:n]}
+
+
 _lib = None
 
 
@@ -147,6 +174,17 @@ def lib():
         L.orc_localize_progressive.restype = ctypes.c_int
         L.orc_region_lattice.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, ip]
         L.orc_region_lattice.restype = None
+        pp = ctypes.POINTER(Path)
+        L.orc_select_path.argtypes = L.orc_select.argtypes[:4] + [pp, ctypes.POINTER(Result)]
+        L.orc_select_path.restype = ctypes.c_int
+        L.orc_localize_path.argtypes = L.orc_localize.argtypes[:-1] + [pp,
+                                                                       ctypes.POINTER(Result)]
+        L.orc_localize_path.restype = ctypes.c_int
+        L.orc_localize_progressive_path.argtypes = L.orc_localize_path.argtypes
+        L.orc_localize_progressive_path.restype = ctypes.c_int
+        L.orc_localize_multistatic_path.argtypes = \
+            L.orc_localize_multistatic.argtypes[:-1] + [pp, ctypes.POINTER(Result)]
+        L.orc_localize_multistatic_path.restype = ctypes.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -224,43 +262,63 @@ def lattice_offset(n: int, D: int) -> int:
     return lib().orc_lattice_offset(n, D)
 
 
-def select(profile_norm: np.ndarray, grid: dict, rule: Rule, D: int) -> dict:
+def select(profile_norm: np.ndarray, grid: dict, rule: Rule, D: int,
+           path: Path | None = None) -> dict:
+    """Selection loop on a normalised decimated profile. With a path, the
+    loop follows it and the result carries the path log under "path"."""
     e = np.ascontiguousarray(profile_norm, dtype=np.float64).ravel()
     g = make_grid(grid)
     res = Result()
-    st = lib().orc_select(e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(g),
-                          ctypes.byref(rule), int(D), ctypes.byref(res))
-    if st != 0:
+    st = lib().orc_select_path(e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               ctypes.byref(g), ctypes.byref(rule), int(D),
+                               None if path is None else ctypes.byref(path), ctypes.byref(res))
+    if st != 0 and (path is None or path.error == 0):
         raise ValueError(f"orc_select failed: {st}")
-    return res.to_dict()
+    out = res.to_dict()
+    if path is not None:
+        out["path"] = _path_log(path, res.n_logged)
+    return out
+
+
+def _with_path(res: Result, path: Path | None) -> dict:
+    out = res.to_dict()
+    if path is not None:
+        out["path"] = _path_log(path, res.n_logged)
+    return out
 
 
 def localize(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
-             rule: Rule | None = None) -> dict:
+             rule: Rule | None = None, path: Path | None = None) -> dict:
+    """The framework (orc_localize); with a path, along that trajectory
+    (orc_localize_path), the path log under "path"."""
     tr, trp = _f32(traces)
     an, anp = _f32(antennas)
     M, N = tr.shape
     rule = make_rule() if rule is None else rule
     g = make_grid(grid)
     res = Result()
-    lib().orc_localize(trp, M, N, anp, ctypes.byref(g), float(v), float(fs), int(window),
-                       int(beamformer), ctypes.byref(rule), ctypes.byref(res))
-    return res.to_dict()
+    lib().orc_localize_path(trp, M, N, anp, ctypes.byref(g), float(v), float(fs), int(window),
+                            int(beamformer), ctypes.byref(rule),
+                            None if path is None else ctypes.byref(path), ctypes.byref(res))
+    return _with_path(res, path)
 
 
 def localize_progressive(traces, antennas, grid: dict, v, fs, window, beamformer=DAS,
-                         rule: Rule | None = None) -> dict:
-    """The framework with progressive re-evaluation (orc_localize_progressive)."""
+                         rule: Rule | None = None, path: Path | None = None) -> dict:
+    """The framework with progressive re-evaluation (orc_localize_progressive);
+    with a path, along that trajectory."""
     tr, trp = _f32(traces)
     an, anp = _f32(antennas)
     M, N = tr.shape
     g = make_grid(grid)
     res = Result()
     rule = make_rule() if rule is None else rule
-    st = lib().orc_localize_progressive(trp, M, N, anp, ctypes.byref(g), float(v), float(fs),
-                                        int(window), int(beamformer), ctypes.byref(rule),
-                                        ctypes.byref(res))
-    out = res.to_dict()
+    st = lib().orc_localize_progressive_path(trp, M, N, anp, ctypes.byref(g), float(v),
+                                             float(fs), int(window), int(beamformer),
+                                             ctypes.byref(rule),
+                                             None if path is None else ctypes.byref(path),
+                                             ctypes.byref(res))
+    out = _with_path(res, path)
     out["status"] = st if st != 0 else out["status"]
     return out
 
@@ -291,7 +349,7 @@ def presence(traces, antennas, grid: dict, v, fs, window, beamformer=DAS, rule: 
 
 
 def localize_multistatic(traces, channels, antennas, grid: dict, v, fs, window, beamformer=DAS,
-                         rule: Rule | None = None) -> dict:
+                         rule: Rule | None = None, path: Path | None = None) -> dict:
     tr, trp = _f32(traces)
     an, anp = _f32(antennas)
     ch = np.ascontiguousarray(channels, dtype=np.int32)
@@ -299,10 +357,13 @@ def localize_multistatic(traces, channels, antennas, grid: dict, v, fs, window, 
     rule = make_rule() if rule is None else rule
     g = make_grid(grid)
     res = Result()
-    lib().orc_localize_multistatic(trp, C, N, ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), anp,
-                                   an.shape[0], ctypes.byref(g), float(v), float(fs), int(window),
-                                   int(beamformer), ctypes.byref(rule), ctypes.byref(res))
-    return res.to_dict()
+    lib().orc_localize_multistatic_path(trp, C, N,
+                                        ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), anp,
+                                        an.shape[0], ctypes.byref(g), float(v), float(fs),
+                                        int(window), int(beamformer), ctypes.byref(rule),
+                                        None if path is None else ctypes.byref(path),
+                                        ctypes.byref(res))
+    return _with_path(res, path)
 
 
 def hybrid_metric(mean_i: float, var_i: float, var_prev: float) -> float:

@@ -328,8 +328,55 @@ static double rel_gap(double hi, double lo) {
   return (hi - lo) / d;
 }
 
+/* Test aid (orc_path): clears the path's outputs. */
+static void path_reset(orc_path* p) {
+  if (!p) return;
+  p->error = 0;
+  for (int i = 0; i < ORC_MAX_ITERS; ++i) {
+    p->own_child[i] = -1;
+    p->own_cont[i] = -1;
+    p->taken_metric[i] = 0.0;
+    p->taken_gap[i] = 0.0;
+  }
+}
+
+/* Test aid (orc_path): the child iteration li + 1 takes, the path's if it
+ * names one, else the argmax `best`; -1 if the path names a non-candidate. */
+static int path_take_child(orc_path* p, int li, int nchild, int best, double best_m,
+                           const int* valid, const double* metric) {
+  int take = best;
+  if (p && li < p->n && p->child[li] >= 0) {
+    take = p->child[li];
+    if (take >= nchild || !valid[take]) {
+      p->error = li + 1;
+      return -1;
+    }
+  }
+  if (p) {
+    p->own_child[li] = best;
+    p->taken_metric[li] = metric[take];
+    p->taken_gap[li] = take == best ? 0.0 : rel_gap(best_m, metric[take]);
+  }
+  return take;
+}
+
+/* Test aid (orc_path): the continue (1) / stop (0) outcome iteration li + 1
+ * takes, the path's if it names one, else the Eq. 6-7 test's `cont`. */
+static int path_take_cont(orc_path* p, int li, int cont) {
+  if (!p) return cont;
+  p->own_cont[li] = cont;
+  if (li < p->n && p->cont[li] >= 0) return p->cont[li] ? 1 : 0;
+  return cont;
+}
+
 int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
                orc_result* res) {
+  return orc_select_path(e, g, r, D, NULL, res);
+}
+
+int orc_select_path(const double* e, const orc_grid* g, const orc_rule* r, int D,
+                    orc_path* path, orc_result* res) {
+  path_reset(path);
   lattice L;
   make_lattice(g, D, &L);
   const long total = (long)L.cnt[0] * L.cnt[1] * L.cnt[2];
@@ -359,23 +406,23 @@ int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
 
     int best = -1, nvalid = 0;
     double best_m = 0.0, second_m = 0.0;
-    int best_lo[3] = {0, 0, 0}, best_hi[3] = {0, 0, 0};
+    int clo[8][3], chi[8][3], valid[8] = {0};
+    double metric[8] = {0};
     for (int c = 0; c < nchild; ++c) {
-      int clo[3], chi[3];
       int ok = 1;
       for (int a = 0; a < 3; ++a) {
         if (a < g->dim) {
           int bit = (c >> a) & 1; /* x is bit 0, y bit 1, z bit 2 */
-          clo[a] = bit ? mid[a] : R_lo[a];
-          chi[a] = bit ? R_hi[a] : mid[a];
-          if (chi[a] - clo[a] < r->min_segment) ok = 0;
+          clo[c][a] = bit ? mid[a] : R_lo[a];
+          chi[c][a] = bit ? R_hi[a] : mid[a];
+          if (chi[c][a] - clo[c][a] < r->min_segment) ok = 0;
         } else {
-          clo[a] = R_lo[a];
-          chi[a] = R_hi[a];
+          clo[c][a] = R_lo[a];
+          chi[c][a] = R_hi[a];
         }
       }
       if (!ok) continue;
-      long nc = gather_box(e, &L, clo, chi, bufc);
+      long nc = gather_box(e, &L, clo[c], chi[c], bufc);
       if (nc == 0) continue;
       double mu = mean_of(bufc, nc), var = var_of(bufc, nc);
       double m;
@@ -387,12 +434,12 @@ int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
         m = orc_hybrid_metric_unclipped(mu, var, var_prev);
       else
         m = orc_hybrid_metric(mu, var, var_prev);
+      valid[c] = 1;
+      metric[c] = m;
       if (nvalid == 0 || m > best_m) {
         if (nvalid > 0) second_m = best_m;
         best_m = m;
         best = c;
-        memcpy(best_lo, clo, sizeof clo);
-        memcpy(best_hi, chi, sizeof chi);
       } else if (nvalid == 1 || m > second_m) {
         second_m = m;
       }
@@ -403,9 +450,16 @@ int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
       res->iters = i - 1;
       break;
     }
-    res->child[li] = best;
+    const int take = path_take_child(path, li, nchild, best, best_m, valid, metric);
+    if (take < 0) {
+      free(bufa); free(bufb); free(bufc);
+      return ORC_ERR_ARG;
+    }
+    const int* best_lo = clo[take];
+    const int* best_hi = chi[take];
+    res->child[li] = take;
     res->n_children[li] = nvalid;
-    res->metric_top[li] = best_m;
+    res->metric_top[li] = metric[take];
     res->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
 
     /* sliding framing of the chosen child */
@@ -436,7 +490,7 @@ int orc_select(const double* e, const orc_grid* g, const orc_rule* r, int D,
       double mW = rel_gap(W_prev, Wi);  /* > 0: W shrank */
       int cont = (Bi > B_prev) && (Wi < W_prev);
       res->stop_margin[li] = cont ? (mB < mW ? mB : mW) : (-mB > -mW ? -mB : -mW);
-      if (!cont) {
+      if (!path_take_cont(path, li, cont)) {
         res->stop_reason = ORC_STOP_METRIC;
         res->iters = i - 1;
         break;
@@ -489,25 +543,40 @@ static int scan_image(const scan_data* d, const orc_grid* g, const int lo[3], co
 }
 
 static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* r,
-                         orc_result* res);
+                         orc_path* path, orc_result* res);
 
 int orc_localize(const float* traces, int M, int N, const float* antennas,
                  const orc_grid* g, double v, double fs, int window, int beamformer,
                  const orc_rule* r, orc_result* res) {
+  return orc_localize_path(traces, M, N, antennas, g, v, fs, window, beamformer, r, NULL, res);
+}
+
+int orc_localize_path(const float* traces, int M, int N, const float* antennas,
+                      const orc_grid* g, double v, double fs, int window, int beamformer,
+                      const orc_rule* r, orc_path* path, orc_result* res) {
   scan_data d = {traces, M, N, NULL, antennas, M, v, fs, window, beamformer};
-  return localize_data(&d, g, r, res);
+  return localize_data(&d, g, r, path, res);
 }
 
 int orc_localize_multistatic(const float* traces, int C, int N, const int* chan,
                              const float* antennas, int M, const orc_grid* g, double v,
                              double fs, int window, int beamformer, const orc_rule* r,
                              orc_result* res) {
+  return orc_localize_multistatic_path(traces, C, N, chan, antennas, M, g, v, fs, window,
+                                       beamformer, r, NULL, res);
+}
+
+int orc_localize_multistatic_path(const float* traces, int C, int N, const int* chan,
+                                  const float* antennas, int M, const orc_grid* g, double v,
+                                  double fs, int window, int beamformer, const orc_rule* r,
+                                  orc_path* path, orc_result* res) {
   scan_data d = {traces, C, N, chan, antennas, M, v, fs, window, beamformer};
-  return localize_data(&d, g, r, res);
+  return localize_data(&d, g, r, path, res);
 }
 
 static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* r,
-                         orc_result* res) {
+                         orc_path* path, orc_result* res) {
+  path_reset(path);
   memset(res, 0, sizeof *res);
   for (int a = 0; a < 3; ++a) res->loc_idx[a] = -1;
   if (!g || !r || g->dim < 2 || g->dim > 3 || (g->dim == 2 && g->n[2] != 1) ||
@@ -552,7 +621,7 @@ static int localize_data(const scan_data* d, const orc_grid* g, const orc_rule* 
     return ORC_OK;
   }
   for (long long p = 0; p < nd; ++p) prof[p] /= mx; /* normalised energies */
-  st = orc_select(prof, g, r, D, res);
+  st = orc_select_path(prof, g, r, D, path, res);
   free(prof);
   if (st != ORC_OK) {
     res->status = st;
@@ -606,7 +675,16 @@ void orc_region_lattice(int lo, int hi, int c0, int* first, int* step, int* cnt)
 int orc_localize_progressive(const float* traces, int M, int N, const float* antennas,
                              const orc_grid* g, double v, double fs, int window,
                              int beamformer, const orc_rule* r, orc_result* res) {
+  return orc_localize_progressive_path(traces, M, N, antennas, g, v, fs, window, beamformer, r,
+                                       NULL, res);
+}
+
+int orc_localize_progressive_path(const float* traces, int M, int N, const float* antennas,
+                                  const orc_grid* g, double v, double fs, int window,
+                                  int beamformer, const orc_rule* r, orc_path* path,
+                                  orc_result* res) {
   scan_data d = {traces, M, N, NULL, antennas, M, v, fs, window, beamformer};
+  path_reset(path);
   memset(res, 0, sizeof *res);
   for (int a = 0; a < 3; ++a) res->loc_idx[a] = -1;
   if (!g || !r || g->dim < 2 || g->dim > 3 || (g->dim == 2 && g->n[2] != 1) ||
@@ -690,23 +768,23 @@ int orc_localize_progressive(const float* traces, int M, int N, const float* ant
     for (int a = 0; a < 3; ++a) mid[a] = R_lo[a] + (R_hi[a] - R_lo[a]) / 2;
     int best = -1, nvalid = 0;
     double best_m = 0.0, second_m = 0.0;
-    int best_lo[3] = {0, 0, 0}, best_hi[3] = {0, 0, 0};
+    int clo[8][3], chi[8][3], valid[8] = {0};
+    double metric[8] = {0};
     for (int c = 0; c < nchild; ++c) {
-      int clo[3], chi[3];
       int ok = 1;
       for (int a = 0; a < 3; ++a) {
         if (a < g->dim) {
           int bit = (c >> a) & 1;
-          clo[a] = bit ? mid[a] : R_lo[a];
-          chi[a] = bit ? R_hi[a] : mid[a];
-          if (chi[a] - clo[a] < r->min_segment) ok = 0;
+          clo[c][a] = bit ? mid[a] : R_lo[a];
+          chi[c][a] = bit ? R_hi[a] : mid[a];
+          if (chi[c][a] - clo[c][a] < r->min_segment) ok = 0;
         } else {
-          clo[a] = R_lo[a];
-          chi[a] = R_hi[a];
+          clo[c][a] = R_lo[a];
+          chi[c][a] = R_hi[a];
         }
       }
       if (!ok) continue;
-      long nc = gather_box(ce, &L, clo, chi, bufc);
+      long nc = gather_box(ce, &L, clo[c], chi[c], bufc);
       if (nc == 0) continue;
       double mu = mean_of(bufc, nc), var = var_of(bufc, nc);
       double m;
@@ -718,12 +796,12 @@ int orc_localize_progressive(const float* traces, int M, int N, const float* ant
         m = orc_hybrid_metric_unclipped(mu, var, var_prev);
       else
         m = orc_hybrid_metric(mu, var, var_prev);
+      valid[c] = 1;
+      metric[c] = m;
       if (nvalid == 0 || m > best_m) {
         if (nvalid > 0) second_m = best_m;
         best_m = m;
         best = c;
-        memcpy(best_lo, clo, sizeof clo);
-        memcpy(best_hi, chi, sizeof chi);
       } else if (nvalid == 1 || m > second_m) {
         second_m = m;
       }
@@ -734,9 +812,16 @@ int orc_localize_progressive(const float* traces, int M, int N, const float* ant
       res->iters = i - 1;
       break;
     }
-    res->child[li] = best;
+    const int take = path_take_child(path, li, nchild, best, best_m, valid, metric);
+    if (take < 0) {
+      st = ORC_ERR_ARG;
+      break;
+    }
+    const int* best_lo = clo[take];
+    const int* best_hi = chi[take];
+    res->child[li] = take;
     res->n_children[li] = nvalid;
-    res->metric_top[li] = best_m;
+    res->metric_top[li] = metric[take];
     res->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
     int N_lo[3], N_hi[3];
     for (int a = 0; a < 3; ++a) {
@@ -764,7 +849,7 @@ int orc_localize_progressive(const float* traces, int M, int N, const float* ant
       double mW = rel_gap(W_prev, Wi);
       int cont = (Bi > B_prev) && (Wi < W_prev);
       res->stop_margin[li] = cont ? (mB < mW ? mB : mW) : (-mB > -mW ? -mB : -mW);
-      if (!cont) {
+      if (!path_take_cont(path, li, cont)) {
         res->stop_reason = ORC_STOP_METRIC;
         res->iters = i - 1;
         break;

@@ -163,6 +163,55 @@ int orc_localize_progressive(const float* traces, int M, int N, const float* ant
  * + 1. Writes the first index, the step and the count. */
 void orc_region_lattice(int lo, int hi, int c0, int* first, int* step, int* cnt);
 
+/* Trajectory replay, a test aid with no counterpart in the paper.
+ *
+ * Where two children score within rounding of each other (Eq. 5), or B_i and
+ * W_i sit within rounding of B_{i-1} and W_{i-1} (Eq. 6-7), both outcomes are
+ * correct, and an FP32 image may take the other one. A checker then needs the
+ * oracle's answer along the path the other implementation took. An orc_path
+ * makes the selection loop (Section III, ROI Selection) follow such a path:
+ *  - iteration i (1-based, i <= n) takes child[i-1] when it is >= 0, instead
+ *    of the argmax of the metric; the child must be a candidate (it survives
+ *    the size and emptiness filters), else `error` is set to i and the call
+ *    fails with ORC_ERR_ARG;
+ *  - from the second iteration on, cont[i-1] >= 0 replaces the outcome of the
+ *    Eq. 6-7 test: 1 continues, 0 stops with ORC_STOP_METRIC.
+ * Everything else runs unchanged: every candidate's metric, the framing,
+ * both scatters, the stop margins, the final region and its argmax. For each
+ * performed iteration the loop records what it would have done itself
+ * (own_child, own_cont) and how far the child it took is from its own best
+ * (taken_gap = (best - taken) / |best|, 0 when they are the same child). The
+ * result's child, box and metric_top entries describe the child taken;
+ * metric_gap and stop_margin keep the oracle's own margins. */
+typedef struct {
+  int n;
+  int child[ORC_MAX_ITERS];
+  int cont[ORC_MAX_ITERS];
+  /* written by the loop */
+  int error;
+  int own_child[ORC_MAX_ITERS];
+  int own_cont[ORC_MAX_ITERS];        /* -1 at the first iteration (no test) */
+  double taken_metric[ORC_MAX_ITERS];
+  double taken_gap[ORC_MAX_ITERS];
+} orc_path;
+
+/* orc_select, orc_localize, orc_localize_multistatic and
+ * orc_localize_progressive along a given path (path may be NULL: the
+ * oracle's own choices, exactly as the functions without the suffix). */
+int orc_select_path(const double* e, const orc_grid* g, const orc_rule* r, int D,
+                    orc_path* path, orc_result* res);
+int orc_localize_path(const float* traces, int M, int N, const float* antennas,
+                      const orc_grid* g, double v, double fs, int window, int beamformer,
+                      const orc_rule* r, orc_path* path, orc_result* res);
+int orc_localize_multistatic_path(const float* traces, int C, int N, const int* chan,
+                                  const float* antennas, int M, const orc_grid* g, double v,
+                                  double fs, int window, int beamformer, const orc_rule* r,
+                                  orc_path* path, orc_result* res);
+int orc_localize_progressive_path(const float* traces, int M, int N, const float* antennas,
+                                  const orc_grid* g, double v, double fs, int window,
+                                  int beamformer, const orc_rule* r, orc_path* path,
+                                  orc_result* res);
+
 /* Eq. 5 hybrid metric for one candidate, weight clipped to [0, 1], and the
  * printed formula without the clip (exposed for the tests). */
 double orc_hybrid_metric(double mean_i, double var_i, double var_prev);

@@ -293,6 +293,112 @@ def test_selection_hand_worked_spike():
     assert r["between"][1] == pytest.approx(float(gold["between2"][0]), rel=1e-6)
 
 
+def _cube_spike_case():
+    gold = read_golden("select_spike_16cube.txt")
+    n = [int(x) for x in gold["grid"]]
+    at = [int(x) for x in gold["spike"]]
+    e = np.zeros((n[2], n[1], n[0]))
+    e[at[2], at[1], at[0]] = 1.0
+    grid = {"dim": 3, "n": n, "origin": [0, 0, 0], "pitch": [1e-3] * 3}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1,
+                            min_segment=int(gold["min_segment"][0]))
+    return gold, e, grid, rule
+
+
+def test_selection_hand_worked_spike_in_a_cube():
+    """Octree selection (child bit 2 = high z, framing along z, 3-D point counts
+    in Eq. 6-7) against a run worked by hand in exact fractions."""
+    gold, e, grid, rule = _cube_spike_case()
+    r = oracle.select(e, grid, rule, 1)
+    blo = [int(x) for x in gold["box_lo"]]
+    bhi = [int(x) for x in gold["box_hi"]]
+    assert r["child"] == [int(x) for x in gold["children"]]
+    assert r["box_lo"] == [blo[3 * i:3 * i + 3] for i in range(len(blo) // 3)]
+    assert r["box_hi"] == [bhi[3 * i:3 * i + 3] for i in range(len(bhi) // 3)]
+    assert r["roi_lo"] == [int(x) for x in gold["roi_lo"]]
+    assert r["roi_hi"] == [int(x) for x in gold["roi_hi"]]
+    assert r["iters"] == int(gold["iters"][0])
+    assert r["n_logged"] == int(gold["n_logged"][0])
+    assert r["stop_reason"] == int(gold["stop_reason"][0])
+    np.testing.assert_allclose(r["within"], [float(x) for x in gold["within"]], rtol=1e-13)
+    np.testing.assert_allclose(r["between"], [float(x) for x in gold["between"]], rtol=1e-12,
+                               atol=1e-18)
+
+
+def test_selection_cube_is_equivariant_under_axis_swaps():
+    """Swapping the y and z axes of the cube's energies swaps child bits 1 and 2
+    and the y and z extents of every box (the split points are the same)."""
+    gold, e, grid, rule = _cube_spike_case()
+    r = oracle.select(e, grid, rule, 1)
+    rs = oracle.select(np.ascontiguousarray(np.swapaxes(e, 0, 1)), grid, rule, 1)
+
+    def swap_bits(c):
+        return (c & 1) | ((c >> 2) & 1) << 1 | ((c >> 1) & 1) << 2
+    assert rs["child"] == [swap_bits(c) for c in r["child"]]
+    assert rs["box_lo"] == [[b[0], b[2], b[1]] for b in r["box_lo"]]
+    assert rs["box_hi"] == [[b[0], b[2], b[1]] for b in r["box_hi"]]
+    assert rs["stop_reason"] == r["stop_reason"] and rs["iters"] == r["iters"]
+
+
+# ------------------------------------------------------------- trajectory replay (test aid)
+
+def test_replay_without_forcing_is_the_oracle_itself():
+    gold, e, grid, rule = _cube_spike_case()
+    plain = oracle.select(e, grid, rule, 1)
+    free = oracle.select(e, grid, rule, 1, path=oracle.make_path([-1] * 8))
+    log = free.pop("path")
+    assert free == plain
+    assert log["error"] == 0
+    assert log["own_child"] == plain["child"] and log["taken_gap"] == [0.0] * 5
+    assert log["own_cont"] == [-1, 1, 1, 1, 0]
+    own = oracle.select(e, grid, rule, 1, path=oracle.make_path(plain["child"], log["own_cont"]))
+    own.pop("path")
+    assert own == plain
+
+
+def test_replay_follows_a_forced_child_and_logs_its_own_choice():
+    # 16 x 16 spike of the 2-D hand-worked run: force child 0 (low x, low y) at
+    # iteration 1 instead of child 1. Child 0 holds no energy: metric 0, the
+    # oracle's own best is child 1, so the gap is 1; the box is child 0's
+    # [0,8)^2 grown by 2: [0,10)^2.
+    n = [16, 16, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, min_segment=2)
+    r = oracle.select(_spike_profile(n, [11, 5]), grid, rule, 1, path=oracle.make_path([0]))
+    log = r["path"]
+    assert r["child"][0] == 0 and log["own_child"][0] == 1
+    assert log["taken_metric"][0] == 0.0 and log["taken_gap"][0] == 1.0
+    assert r["box_lo"][0][:2] == [0, 0] and r["box_hi"][0][:2] == [10, 10]
+    assert r["metric_top"][0] == 0.0
+
+
+def test_replay_forced_stop_and_forced_continue():
+    gold, e, grid, rule = _cube_spike_case()
+    # stop at iteration 2 although Eq. 6-7 says continue: the result is R1
+    stop = oracle.select(e, grid, rule, 1, path=oracle.make_path([-1, -1], [-1, 0]))
+    assert stop["stop_reason"] == oracle.STOP_METRIC and stop["iters"] == 1
+    assert stop["n_logged"] == 2 and stop["path"]["own_cont"][1] == 1
+    assert stop["roi_lo"] == [0, 6, 6] and stop["roi_hi"] == [10, 16, 16]
+    # continue at iteration 5 although B5 = 0 < B4: the loop goes on from the
+    # iteration-5 box [2,7) x [11,15) x [11,15)
+    go = oracle.select(e, grid, rule, 1, path=oracle.make_path([-1] * 5, [-1, -1, -1, -1, 1]))
+    assert go["path"]["own_cont"][4] == 0
+    assert go["n_logged"] > 5 and go["box_lo"][4] == [2, 11, 11]
+
+
+def test_replay_rejects_a_child_that_is_not_a_candidate():
+    # 7 x 8 grid, min_segment 4: the low x half [0,3) is too narrow, so
+    # children 0 and 2 are no candidates; child 5 does not exist in 2-D
+    n = [7, 8, 1]
+    grid = {"dim": 2, "n": n, "origin": [0, 0, 0], "pitch": [1e-3, 1e-3, 1.0]}
+    rule = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=1, min_segment=4)
+    for bad in (0, 2, 5):
+        r = oracle.select(_spike_profile(n, [5, 3]), grid, rule, 1, path=oracle.make_path([bad]))
+        assert r["path"]["error"] == 1
+    ok = oracle.select(_spike_profile(n, [5, 3]), grid, rule, 1, path=oracle.make_path([3]))
+    assert ok["path"]["error"] == 0 and ok["child"][0] == 3
+
+
 ALL_METRICS = [oracle.METRIC_HYBRID, oracle.METRIC_MEAN, oracle.METRIC_VARIANCE,
                oracle.METRIC_HYBRID_UNCLIPPED]
 
