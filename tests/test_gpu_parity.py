@@ -7,8 +7,8 @@ import torch
 
 import oracle
 import phantom
-from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, dev, record_to_dict,
-                    gpu_image_batch, gpu_localize_batch, rule_pair)
+from parity import (BF_ORACLE, IMG_TOL, OracleScan, assert_image_close, compare_localize,
+                    dev, record_to_dict, gpu_image_batch, gpu_localize_batch, rule_pair)
 
 pytestmark = pytest.mark.gpu
 
@@ -121,13 +121,6 @@ def test_ragged_trace_with_tma_disabled_by_alignment(gpu):
 
 # ------------------------------------------------------------------ localisation
 
-def _energy_at(tr, ants, grid, v, fs, W, bf):
-    def f(idx):
-        return float(oracle.image(tr, ants, grid, v, fs, W, BF_ORACLE[bf], lo=idx,
-                                  cnt=[1, 1, 1])[0, 0, 0])
-    return f
-
-
 def _check_batch(gpu, cfg, bf, seeds, rule_kw=None, ants=None):
     rule_kw = rule_kw or {}
     scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in seeds]
@@ -138,11 +131,8 @@ def _check_batch(gpu, cfg, bf, seeds, rule_kw=None, ants=None):
     res = gpu_localize_batch(gpu, bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, g_rule)
     ties = 0
     for s, sc in enumerate(scans):
-        o = oracle.localize(sc["traces"], ants, grid, cfg.v, cfg.fs, cfg.window, BF_ORACLE[bf],
-                            o_rule)
-        summary = compare_localize(res[s], o, _energy_at(sc["traces"], ants, grid, cfg.v, cfg.fs,
-                                                          cfg.window, bf))
-        ties += summary["tie"]
+        scan = OracleScan(sc["traces"], ants, grid, cfg.v, cfg.fs, cfg.window, bf, o_rule)
+        ties += compare_localize(res[s], scan)["tie"]
     assert ties <= max(1, len(seeds) // 4), f"{ties} near-ties in {len(seeds)} scans"
     return res
 
@@ -186,11 +176,9 @@ def test_benchmark_batch_sampled_scans_match_oracle(gpu):
     assert all(int(r["status"]) == 0 for r in res)
     ties = 0
     for s in (0, 137, 511, 700, 901, 1023):
-        tr = batch["traces"][s]
-        o = oracle.localize(tr, batch["antennas"], grid, cfg.v, cfg.fs, cfg.window, oracle.DMAS,
-                            o_rule)
-        ties += compare_localize(res[s], o, _energy_at(tr, batch["antennas"], grid, cfg.v,
-                                                        cfg.fs, cfg.window, 2))["tie"]
+        scan = OracleScan(batch["traces"][s], batch["antennas"], grid, cfg.v, cfg.fs,
+                          cfg.window, 2, o_rule)
+        ties += compare_localize(res[s], scan)["tie"]
     assert ties <= 1, f"{ties} near-ties in 6 sampled scans"
 
 
@@ -233,9 +221,8 @@ def test_localize_edge_cases(gpu):
     res = gpu_localize_batch(gpu, 0, traces, good["antennas"], grid, cfg.v, cfg.fs, cfg.window,
                              g_rule)
     for s in range(4):
-        o = oracle.localize(traces[s], good["antennas"], grid, cfg.v, cfg.fs, cfg.window,
-                            oracle.DAS, o_rule)
-        compare_localize(res[s], o)
+        compare_localize(res[s], OracleScan(traces[s], good["antennas"], grid, cfg.v, cfg.fs,
+                                            cfg.window, 0, o_rule))
     assert res[1]["stop_reason"] == oracle.STOP_NO_TARGET
     assert res[2]["status"] == -4
     assert res[0]["loc_idx"] == res[3]["loc_idx"]
@@ -260,8 +247,7 @@ def test_localize_degenerate_grids(gpu):
                 "pitch": [1e-3, 1e-3, 1.0]}
         g_rule, o_rule = rule_pair(gpu, mode=0, decimation=1, min_segment=1)
         res = gpu_localize_batch(gpu, 0, tr, ants, grid, v, fs, W, g_rule)
-        o = oracle.localize(tr, ants, grid, v, fs, W, oracle.DAS, o_rule)
-        compare_localize(res[0], o, _energy_at(tr, ants, grid, v, fs, W, 0))
+        compare_localize(res[0], OracleScan(tr, ants, grid, v, fs, W, 0, o_rule))
 
 
 # ------------------------------------------------------------------ full size
@@ -378,12 +364,19 @@ def test_presence_matches_oracle(gpu, name, bf, D2):
     r1 = [record_to_dict(r) for r in gpu.results_from_device(o1)]
     r2 = [record_to_dict(r) for r in gpu.results_from_device(o2)]
     got = present.cpu().numpy()
+    o_rule2 = oracle.make_rule(mode=oracle.DECIM_MANUAL, decimation=D2,
+                               min_tumor_diameter=o_rule.min_tumor_diameter, metric=o_rule.metric,
+                               min_segment=o_rule.min_segment, frame_num=o_rule.frame_num,
+                               frame_den=o_rule.frame_den, max_iters=o_rule.max_iters)
     for s, sc in enumerate(scans):
         want, w1, w2 = oracle.presence(sc["traces"], ants, grid, base.v, base.fs, base.window,
                                        BF_ORACLE[bf], o_rule, D2)
-        e = _energy_at(sc["traces"], ants, grid, base.v, base.fs, base.window, bf)
-        t1 = compare_localize(r1[s], w1, e)
-        t2 = compare_localize(r2[s], w2, e)
+        args = (sc["traces"], ants, grid, base.v, base.fs, base.window, bf)
+        t1 = compare_localize(r1[s], OracleScan(*args, o_rule), w1)
+        t2 = compare_localize(r2[s], OracleScan(*args, o_rule2), w2)
+        # the verdict is the agreement of the two located points
+        located = r1[s]["loc_idx"][0] >= 0 and r2[s]["loc_idx"][0] >= 0
+        assert bool(got[s]) == (located and r1[s]["loc_idx"] == r2[s]["loc_idx"]), s
         if not (t1["tie"] or t2["tie"]):
             assert bool(got[s]) == want, s
         assert r2[s]["decim"] == D2
@@ -461,13 +454,8 @@ def test_multistatic_localize_matches_oracle(gpu, bf):
     torch.cuda.synchronize()
     res = [record_to_dict(r) for r in gpu.results_from_device(out)]
     for s, sc in enumerate(scans):
-        o = oracle.localize_multistatic(sc["traces"], ch, ants, grid, cfg.v, cfg.fs, cfg.window,
-                                        BF_ORACLE[bf], o_rule)
-
-        def energy_at(idx, t=sc["traces"]):
-            return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
-                                                  BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
-        compare_localize(res[s], o, energy_at)
+        compare_localize(res[s], OracleScan(sc["traces"], ants, grid, cfg.v, cfg.fs, cfg.window,
+                                            bf, o_rule, channels=ch))
 
 
 def test_measured_peaks_are_plausible(gpu):
@@ -508,13 +496,8 @@ def test_multistatic_three_d_matches_oracle(gpu, bf):
     torch.cuda.synchronize()
     res = [record_to_dict(r) for r in gpu.results_from_device(out)]
     for s, sc in enumerate(scans):
-        o = oracle.localize_multistatic(sc["traces"], ch, ants, grid, cfg.v, cfg.fs, cfg.window,
-                                        BF_ORACLE[bf], o_rule)
-
-        def energy_at(idx, t=sc["traces"]):
-            return float(oracle.image_multistatic(t, ch, ants, grid, cfg.v, cfg.fs, cfg.window,
-                                                  BF_ORACLE[bf], lo=idx, cnt=[1, 1, 1])[0, 0, 0])
-        compare_localize(res[s], o, energy_at)
+        compare_localize(res[s], OracleScan(sc["traces"], ants, grid, cfg.v, cfg.fs, cfg.window,
+                                            bf, o_rule, channels=ch))
 
 
 @pytest.mark.parametrize("entry", ["localize_das", "localize_literal", "presence",

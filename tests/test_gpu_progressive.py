@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import phantom
-from parity import compare_localize, dev, gpu_localize_batch, record_to_dict
+from parity import OracleScan, compare_localize, dev, gpu_localize_batch, record_to_dict
 
 pytestmark = pytest.mark.gpu
 
@@ -42,16 +42,9 @@ def test_progressive_matches_oracle(gpu, name, bf, n_scans):
     ants = b["antennas"].astype(np.float32)
     res = gpu_progressive(gpu, bf, b["traces"], ants, g, cfg.v, cfg.fs, cfg.window,
                           gpu.uwb_default_rule())
-    obf = oracle.DAS if bf == 0 else oracle.DMAS
     for s in range(n_scans):
-        o = oracle.localize_progressive(b["traces"][s], ants, g, cfg.v, cfg.fs, cfg.window, obf,
-                                        oracle.make_rule())
-
-        def energy_at(idx, s=s):
-            return float(oracle.image(b["traces"][s], ants, g, cfg.v, cfg.fs, cfg.window, obf,
-                                      lo=idx, step=[1, 1, 1], cnt=[1, 1, 1])[0, 0, 0])
-
-        compare_localize(res[s], o, energy_at)
+        compare_localize(res[s], OracleScan(b["traces"][s], ants, g, cfg.v, cfg.fs, cfg.window,
+                                            bf, oracle.make_rule(), progressive=True))
 
 
 def test_progressive_on_a_full_resolution_lattice_is_the_framework(gpu):

@@ -7,8 +7,8 @@ import torch
 
 import oracle
 import phantom
-from parity import (BF_ORACLE, IMG_TOL, assert_image_close, compare_localize, record_to_dict,
-                    rule_pair)
+from parity import (BF_ORACLE, IMG_TOL, OracleScan, assert_image_close, compare_localize,
+                    record_to_dict, rule_pair)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,14 +76,8 @@ def test_ragged_localize_matches_oracle(gpu, dtype, bf):
     torch.cuda.synchronize()
     res = [record_to_dict(r) for r in gpu.results_from_device(out)]
     for k, (cfg, sc) in enumerate(scans):
-        g = cfg.grid()
-        o = oracle.localize(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, BF_ORACLE[bf],
-                            o_rule)
-
-        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
-            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, BF_ORACLE[bf], lo=idx,
-                                      cnt=[1, 1, 1])[0, 0, 0])
-        compare_localize(res[k], o, energy_at)
+        compare_localize(res[k], OracleScan(host[k], sc["antennas"], cfg.grid(), cfg.v, cfg.fs,
+                                            cfg.window, bf, o_rule))
     plan.close()
 
 
@@ -105,13 +99,8 @@ def test_benchmark_ragged_batch_sampled_scans_match_oracle(gpu):
     ties = 0
     for k in (3, 77, 150, 255):
         cfg, sc = scans[k]
-        o = oracle.localize(host[k], sc["antennas"], cfg.grid(), cfg.v, cfg.fs, cfg.window,
-                            oracle.DMAS, o_rule)
-
-        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
-            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, oracle.DMAS, lo=idx,
-                                      cnt=[1, 1, 1])[0, 0, 0])
-        ties += compare_localize(res[k], o, energy_at)["tie"]
+        ties += compare_localize(res[k], OracleScan(host[k], sc["antennas"], cfg.grid(), cfg.v,
+                                                    cfg.fs, cfg.window, 1, o_rule))["tie"]
     assert ties <= 1, f"{ties} near-ties in 4 sampled scans"
 
 
@@ -241,13 +230,8 @@ def test_ragged_literal_blocks_per_scan_match_oracle(gpu, dtype):
         ref = oracle.image(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DMAS)
         got = imgs[plan.image_offset(k):plan.image_offset(k + 1)].reshape(ref.shape)
         assert_image_close(got, ref, what=f"scan {k} ({cfg.n_antennas} antennas)")
-        o = oracle.localize(host[k], sc["antennas"], g, cfg.v, cfg.fs, cfg.window, oracle.DMAS,
-                            o_rule)
-
-        def energy_at(idx, t=host[k], a=sc["antennas"], c=cfg):
-            return float(oracle.image(t, a, c.grid(), c.v, c.fs, c.window, oracle.DMAS, lo=idx,
-                                      step=[1, 1, 1], cnt=[1, 1, 1])[0, 0, 0])
-        compare_localize(res[k], o, energy_at)
+        compare_localize(res[k], OracleScan(host[k], sc["antennas"], g, cfg.v, cfg.fs,
+                                            cfg.window, 2, o_rule))
     plan.close()
 
 
