@@ -34,13 +34,51 @@ METRIC = "localised scans/s (DAS/DMAS, 1 GB300) vs full-res GPU image at same lo
 UNIT = "scans/s"
 BEAMFORMERS = {"das": 0, "dmas": 1, "literal": 2}
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
-# Derived FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.07 GHz max SM clock.
-SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
-# Derived shared-load peak: one 128-byte wavefront per clock per SM.
-LDS_PEAK_GWF = SMS * SM_MAX_GHZ
-# Derived FP32-pipe peak in operations (a fused multiply-add is one): 152 x 128 x 2.07 GHz.
-FP32_PIPE_PEAK_TOPS = SMS * FP32_LANES * SM_MAX_GHZ / 1e3
+# The CPU baseline and the reference arm localise the same declared pool of
+# scans: the first CPU_POOL_SCANS scans of the GPU arm's batch (rank 0).
+CPU_POOL_SCANS = 128
+# Derived peaks, set from the device by configure_peaks() (these defaults are
+# a GB300's: 152 SMs at a 2.07 GHz maximum SM clock).
+FP32_LANES = 128
+SMS, SM_MAX_GHZ = 152, 2.07
+
+
+def configure_peaks(sms: int, ghz: float) -> None:
+    """Derived peaks for `sms` SMs at `ghz` GHz: FP32 FLOP/s (128 lanes x 2 FLOP
+    of a multiply-add), FP32-pipe operations/s (128 lanes, a multiply-add is one)
+    and shared-load wavefronts/s (one 128-byte wavefront per clock per SM)."""
+    global SMS, SM_MAX_GHZ, FP32_PEAK_TFLOPS, LDS_PEAK_GWF, FP32_PIPE_PEAK_TOPS
+    SMS, SM_MAX_GHZ = int(sms), float(ghz)
+    FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+    LDS_PEAK_GWF = SMS * SM_MAX_GHZ
+    FP32_PIPE_PEAK_TOPS = SMS * FP32_LANES * SM_MAX_GHZ / 1e3
+
+
+configure_peaks(SMS, SM_MAX_GHZ)
+
+
+def device_peaks(torch, device: int) -> None:
+    """SM count from the device, maximum SM clock from nvidia-smi (else the
+    measured-peaks file MEASURED_PEAKS.json, else 2.07 GHz)."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = None
+    try:
+        q = subprocess.run(["nvidia-smi", "-i", str(device), "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                           timeout=20)
+        mhz = float(q.stdout.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        try:
+            mhz = float(json.load(open(ROOT / "MEASURED_PEAKS.json"))["sm_max_mhz"])
+        except (OSError, ValueError, KeyError):
+            mhz = 2070.0
+    configure_peaks(sms, mhz / 1e3)
+
+
+def peak_source(kind: str) -> str:
+    per = {"flops": "128 FP32 lanes x 2 FLOP", "ops": "128 FP32 lanes",
+           "wavefronts": "1 wavefront per clock"}[kind]
+    return f"derived: {SMS} SMs x {per} x {SM_MAX_GHZ:.3g} GHz (device SM count, max SM clock)"
 
 # DRAM traffic of the final-region kernel per scan, per beamformer (0 DAS,
 # 1 identity DMAS, 2 literal DMAS), from ncu captures (dmas2d_512, 256 scans)
@@ -98,19 +136,20 @@ def kernel_sha() -> str:
 
 
 def flops_per_point(bf: int, M: int, W: int) -> float:
-    """Algorithmic FLOPs of one focal point (see the kernel roofline notes):
-    per antenna 10 for the delay (3 sub, 3 mul-add, sqrt, scale) and 3 per
-    window sample for the interpolation; then the combine: DAS W*M adds,
-    identity-DMAS W*(3M + 3), literal DMAS W*M(M-1) (M(M-1)/2 multiply-adds per
-    sample); then 2W to square and sum over the window."""
-    per_antenna = M * (10 + 3 * W)
+    """Algorithmic FLOPs of one focal point: per antenna 10 for the delay (3
+    subtractions, 3 for the squared distance, the square root, the scaled
+    offset, the fraction) and 2 per window sample for the interpolated sample
+    and its sum; then the combine: none more for DAS, W (2M + 3) for the
+    identity form of DMAS, W M(M - 1) for literal DMAS (M(M - 1)/2 multiply-adds
+    per sample). At M = 32, W = 20 literal DMAS is 21 440 FLOP per point."""
+    per_antenna = M * (10 + 2 * W)
     if bf == 0:
-        combine = W * M
+        combine = 0
     elif bf == 1:
-        combine = W * (3 * M + 3)
+        combine = W * (2 * M + 3)
     else:
         combine = W * M * (M - 1)
-    return float(per_antenna + combine + 2 * W)
+    return float(per_antenna + combine)
 
 
 def fp32_ops_per_point(bf: int, M: int, W: int, channels: int = 0) -> float:
@@ -152,7 +191,7 @@ def load_or_alu_roofline(n_pts: float, rows: int, W: int, ops_per_point: float,
             "measured_peak": lds_meas / 1e9,
             "frac_of_measured": gwf / (lds_meas / 1e9) if gwf else None,
             "measured_peak_source": "uwb_measure_peaks: conflict-free 32-bit shared loads",
-            "peak_source": "derived: 152 SMs x 1 wavefront per clock x 2.07 GHz",
+            "peak_source": peak_source("wavefronts"),
             "per_launch": wf, "sm_clocks_per_point_at_peak": lds_clk}
     alu = {"achieved": tops, "peak": FP32_PIPE_PEAK_TOPS, "unit": "T FP32-pipe ops/s",
            "frac": tops / FP32_PIPE_PEAK_TOPS if tops else None,
@@ -160,7 +199,7 @@ def load_or_alu_roofline(n_pts: float, rows: int, W: int, ops_per_point: float,
            "frac_of_measured": tops / (fma_meas / 2) if tops else None,
            "measured_peak_source": "uwb_measure_peaks: independent __ffma2_rn chains "
                                    "(TFLOP/s / 2)",
-           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+           "peak_source": peak_source("ops"),
            "per_launch": ops, "sm_clocks_per_point_at_peak": alu_clk}
     bind_smem = lds_clk >= alu_clk
     bind, other = (smem, alu) if bind_smem else (alu, smem)
@@ -261,64 +300,75 @@ def nearest_error_mm(xyz, tumors):
     return float(np.min(np.linalg.norm(np.asarray(tumors) - np.asarray(xyz), axis=1)) * 1e3)
 
 
-def run_reference(args, cfg, bf):
-    """FP64 C oracle on the host cores, each step a bounded sample of scans:
-    step k localises the next scans of the GPU arm's own batch (seeds
-    BASE_SEED + k * per_step ...), synthesised before the timed region, so the
-    sample follows the workload's spread of final-region sizes."""
-    import oracle
-    oracle.build()
+def cpu_pool(cfg, n=CPU_POOL_SCANS):
+    """The declared scan pool of the CPU legs: scans 0 .. n-1 of the GPU arm's
+    batch (rank 0), synthesised before any timing."""
+    return [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in range(n)]
+
+
+def oracle_localize_scans(oracle, cfg, bf, scans):
     grid = cfg.grid()
     obf = oracle.DAS if bf == 0 else oracle.DMAS
     rule = oracle.make_rule()
-    per_step = args.ref_scans_per_step
-    n = args.steps * per_step
-    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + s) for s in range(n)]
-    for _ in range(args.warmup):
-        for sc in scans[:per_step]:
-            oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf,
-                            rule)
-    t0 = time.perf_counter()
     for sc in scans:
         oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf, rule)
+
+
+def run_reference(args, cfg, bf):
+    """FP64 C oracle on the host cores. Every step localises the whole declared
+    pool (the first CPU_POOL_SCANS scans of the GPU arm's batch), the same
+    scans the GPU arm's cpu_baseline leg times, so the two legs measure one
+    rate."""
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # torch.distributed.run sets one OpenMP thread per rank; rank 0 alone
+        # runs the oracle here, on every core it may use
+        os.environ["OMP_NUM_THREADS"] = str(len(os.sched_getaffinity(0)))
+    import oracle
+    oracle.build()
+    pool = cpu_pool(cfg, args.cpu_pool)
+    for _ in range(args.warmup):
+        oracle_localize_scans(oracle, cfg, bf, pool)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_localize_scans(oracle, cfg, bf, pool)
     dt = time.perf_counter() - t0
+    n = args.steps * len(pool)
     value = n / dt
     cores = oracle.num_threads()
-    sample = (f"{per_step} scans per step, scans 0 .. {n - 1} of the GPU arm's batch of the same "
-              f"workload, oracle localisation (FP64)")
+    sample = (f"every step localises the pool of scans 0 .. {len(pool) - 1} of the GPU arm's "
+              f"batch of the same workload (oracle localisation, FP64)")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(cfg, args.beamformer, per_step),
-                   "batch_per_step": per_step},
+        "config": {"workload": workload_name(cfg, args.beamformer, len(pool)),
+                   "batch_per_step": len(pool)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def cpu_baseline(cfg, bf, seconds, pool=32):
-    """The oracle as it stands, on the host cores: a pool of scans is synthesised
-    first (not timed), then localised in turn until about `seconds` of oracle
-    time."""
+def cpu_baseline(cfg, bf, seconds, pool_size=CPU_POOL_SCANS):
+    """The oracle as it stands, on the host cores: whole passes over the
+    declared pool (synthesised first, not timed) until about `seconds` of
+    oracle time, at least one pass."""
     import oracle
     oracle.build()
-    grid = cfg.grid()
-    obf = oracle.DAS if bf == 0 else oracle.DMAS
-    rule = oracle.make_rule()
-    scans = [phantom.make_scan(cfg, phantom.BASE_SEED + 100000 + k) for k in range(pool)]
-    n, busy = 0, 0.0
-    while busy < seconds:
-        sc = scans[n % pool]
+    pool = cpu_pool(cfg, pool_size)
+    passes, busy = 0, 0.0
+    while passes == 0 or busy < seconds:
         t1 = time.perf_counter()
-        oracle.localize(sc["traces"], sc["antennas"], grid, cfg.v, cfg.fs, cfg.window, obf, rule)
+        oracle_localize_scans(oracle, cfg, bf, pool)
         busy += time.perf_counter() - t1
-        n += 1
+        passes += 1
+    n = passes * len(pool)
     return {"value": n / busy, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} localisations of {pool} scans of the same workload by the FP64 "
-                      f"oracle ({busy:.1f} s of oracle time)"}
+            "sample": f"{passes} pass(es) over the pool of scans 0 .. {len(pool) - 1} of the "
+                      f"GPU arm's batch of the same workload by the FP64 oracle ({n} "
+                      f"localisations, {busy:.1f} s of oracle time)"}
 
 
 def run_presence(args, cfg, bf, uwb, torch):
@@ -373,11 +423,14 @@ def run_presence(args, cfg, bf, uwb, torch):
             "confirmed_rate": rates, "gpu_launches": 11 * args.steps}
 
 
-def run_ragged(args, uwb, torch):
+def run_ragged(args, uwb, torch, graph_replay=False):
     """Uneven scans (16-96 antennas, 1024-4096 samples, 128^2-1024^2 grids) in one
     plan per element type: localised scans/s after tile autotuning, full-resolution
     images of the same scans, and each image's error against the FP64 oracle at
-    sampled focal points (traces stored in float32, float16, bfloat16)."""
+    sampled focal points (traces stored in float32, float16, bfloat16). With
+    graph_replay, the float32 plan's localisation is also captured in a CUDA
+    graph and its replays timed (and their records compared with the direct
+    launches')."""
     import oracle
     oracle.build()
     B = args.batch
@@ -433,6 +486,17 @@ def run_ragged(args, uwb, torch):
             return tot / args.steps
 
         loc_ms = timed(lambda: plan.localize(res))
+        graph_info = None
+        if graph_replay and name == "f32":
+            gres = torch.zeros_like(res)
+            side = torch.cuda.Stream()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=side):
+                plan.localize(gres, side)
+            graph_ms = timed(graph.replay)
+            graph_info = {"value": B / (graph_ms / 1e3), "ms_per_step": graph_ms,
+                          "records_equal_direct_launch": bool(torch.equal(gres, res))}
+            del graph
         imgs = torch.empty(plan.image_offset(B), device="cuda")
         peak = torch.empty(B, dtype=torch.int64, device="cuda")
         img_ms = timed(lambda: plan.images(imgs, peak))
@@ -466,6 +530,8 @@ def run_ragged(args, uwb, torch):
             "max_image_error_vs_fp64_oracle": errs,
             "status_ok": bool((recs["status"] == 0).all()),
         }
+        if graph_info is not None:
+            out["by_dtype"][name]["graph_replay"] = graph_info
         plan.close()
     out["value"] = out["by_dtype"]["f32"]["value"]
     uwb.uwb_set_tile_shape(bf, dim, None)
@@ -487,19 +553,25 @@ def _timed(torch, stream, flush, fn, steps):
     return tot / steps
 
 
-def run_learned(args, cfg, bf, uwb, torch):
+def run_learned(args, cfg, bf, uwb, torch, batch=None, traces=None):
     """Localisation with the learned segment proposal (trained weights shipped
     with the package) on held-out scans, against the plain framework and the
-    full-resolution image with the same beamformer on the same scans."""
+    full-resolution image with the same beamformer on the same scans. batch /
+    traces: scans already synthesised and resident (default: args.batch scans
+    from the evaluation seeds, which training never saw)."""
     from paper_1709_02549_gb300 import proposal
-    B = args.batch
     theta, record = proposal.load()
     threshold = record["threshold"]
     wl = proposal.Workload(cfg.name)
     packed = torch.zeros(uwb.CNN_PACKED_BYTES, dtype=torch.uint8, device="cuda")
     uwb.uwb_cnn_pack(torch.from_numpy(theta).cuda(), packed)
-    batch = phantom.make_batch(cfg, B, first_scan=proposal.EVAL_FIRST_SCAN)
-    traces = torch.from_numpy(batch["traces"]).cuda()
+    first_scan = proposal.EVAL_FIRST_SCAN
+    if batch is None:
+        batch = phantom.make_batch(cfg, args.batch, first_scan=first_scan)
+        traces = torch.from_numpy(batch["traces"]).cuda()
+    else:
+        first_scan = int(batch.get("first_scan", 0))
+    B = int(traces.shape[0])
     ants = wl.ants
     grid, rule = wl.grid, wl.rule
     stream = torch.cuda.current_stream()
@@ -578,7 +650,7 @@ def run_learned(args, cfg, bf, uwb, torch):
         "warmup": args.warmup, "ms_per_step": ms_l, "higher_is_better": True,
         "dtype": "f32 image, bf16 network", "data": "synthetic (held-out seeds)",
         "config": {"workload": workload_name(cfg, args.beamformer, B),
-                   "scans_first_seed_offset": proposal.EVAL_FIRST_SCAN,
+                   "scans_first_seed_offset": first_scan,
                    "threshold": threshold, "levels": 2,
                    "trained_on": f"{record['train_scans']} scans, seeds from offset "
                                  f"{record['train_first_scan']}",
@@ -600,6 +672,7 @@ def run_learned(args, cfg, bf, uwb, torch):
         "roofline": {"bound": "alu", "achieved": final_tflops, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s",
                      "frac": final_tflops / FP32_PEAK_TFLOPS if final_tflops else None,
+                     "peak_source": peak_source("flops"),
                      "kernel": "k_image final-region pass", "traffic": None},
         "cnn_roofline": {"bound": "tensor", "achieved": cnn_tflops, "peak": bf16_peak,
                          "unit": "TFLOP/s", "frac": cnn_tflops / bf16_peak,
@@ -743,6 +816,164 @@ def run_multistatic(args, cfg, bf, uwb, torch):
             "clocks": clock_info}
 
 
+def launch_replicas(n: int) -> int:
+    """Runs this command as n ranks of torch.distributed.run on this node (one
+    process per GPU, rendezvous on 127.0.0.1) and returns its exit code."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+           str(pathlib.Path(__file__).resolve())] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def final_roofline(bf: int, M: int, W: int, res, phase_ms_per_step, fma_meas: float,
+                   lds_meas: float) -> dict:
+    """Roofline of the final-region pass of one localisation step: literal DMAS
+    in FLOP/s against the FP32 peak; DAS and identity DMAS against shared loads
+    or the FP32 pipe, whichever has the larger algorithmic demand per point."""
+    roi_points = float(np.prod(res["roi_hi"] - res["roi_lo"], axis=1).astype(np.float64).sum())
+    final_ms = phase_ms_per_step[2]
+    final_flops = roi_points * flops_per_point(bf, M, W)
+    tflops = final_flops / (final_ms / 1e3) / 1e12 if final_ms > 0 else None
+    roof = {
+        "bound": "alu",
+        "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (tflops / FP32_PEAK_TFLOPS) if tflops else None,
+        "measured_peak": fma_meas,
+        "frac_of_measured": (tflops / fma_meas) if tflops else None,
+        "measured_peak_source": "uwb_measure_peaks: independent __ffma2_rn chains, "
+                                "8 CTAs x 256 threads per SM",
+        "traffic": None,
+        "kernel": f"k_image<{['DAS', 'DMAS', 'DMAS_LITERAL'][bf]}> final-region pass",
+        "peak_source": peak_source("flops"),
+        "launch_ms": final_ms,
+        "flops_per_launch": final_flops,
+        "flops_per_point": flops_per_point(bf, M, W),
+        "points_per_launch": roi_points,
+        "phase_ms_per_step": list(phase_ms_per_step),
+    }
+    if bf != 2:
+        roof.update(load_or_alu_roofline(roi_points, M, W, fp32_ops_per_point(bf, M, W),
+                                         final_ms, lds_meas, fma_meas))
+        roof["tflops_achieved"] = tflops
+    return roof
+
+
+def fullres_compare(uwb, torch, cfg, bf, traces, ants, batch, res, steps, flush, stream):
+    """Full-resolution images of the same scans with the same beamformer: their
+    rate, the agreement of the framework's locations with the full-resolution
+    argmax, and the distance of both to the nearest true tumour."""
+    grid = cfg.grid()
+    B = int(traces.shape[0])
+    P = int(np.prod(grid["n"]))
+    img = torch.empty(B, P, device="cuda")
+    peak = torch.empty(B, dtype=torch.int64, device="cuda")
+    fr = lambda: uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img,
+                                     peak, stream)
+    fr()
+    torch.cuda.synchronize()
+    ms = _timed(torch, stream, flush, fr, steps)
+    pk = peak.cpu().numpy()
+    del img
+    gx, gy = grid["n"][0], grid["n"][1]
+    full_idx = np.stack([pk % gx, (pk // gx) % gy, pk // (gx * gy)], 1)
+    agree = float(np.mean(np.all(full_idx == res["loc_idx"], axis=1)))
+    err_fw, err_fr = [], []
+    for s in range(B):
+        xyz_fr = [grid["origin"][a] + full_idx[s, a] * grid["pitch"][a] for a in range(3)]
+        err_fw.append(nearest_error_mm(res["loc_xyz"][s], batch["tumors"][s]))
+        err_fr.append(nearest_error_mm(xyz_fr, batch["tumors"][s]))
+    return ({"value": B / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "loc_agreement": agree},
+            err_fw, err_fr)
+
+
+def measure_workload(uwb, torch, cfg, bf, B, steps, warmup, fullres_steps, flush, stream,
+                     fma_meas, lds_meas) -> dict:
+    """One workload, framework against full resolution with the same
+    beamformer on the same B scans (device-resident, L2 flushed before every
+    step): scans/s of each, their ratio, location agreement, mean errors, and
+    the final-region pass's roofline, with the clocks seen meanwhile."""
+    batch = phantom.make_batch(cfg, B, first_scan=0)
+    grid = cfg.grid()
+    M, N = cfg.n_antennas, cfg.n_samples
+    traces = torch.from_numpy(batch["traces"]).cuda()
+    ants = torch.from_numpy(batch["antennas"]).cuda()
+    rule = uwb.uwb_default_rule()
+    ws = torch.empty(uwb.uwb_localize_workspace(B, M, N, grid, bf, rule), dtype=torch.uint8,
+                     device="cuda")
+    out = torch.empty(B * uwb.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    step = lambda: uwb.uwb_localize_batch(traces, ants, grid, cfg.v, cfg.fs, cfg.window, bf,
+                                          rule, ws, out, None, stream)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    uwb.uwb_phase_timing(True)
+    ms = _timed(torch, stream, flush, step, steps)
+    calls, phase_ms = uwb.uwb_phase_times()
+    uwb.uwb_phase_timing(False)
+    res = uwb.results_from_device(out)
+    fullres, err_fw, err_fr = fullres_compare(uwb, torch, cfg, bf, traces, ants, batch, res,
+                                              fullres_steps, flush, stream)
+    clock_info = clocks.stop()
+    value = B / (ms / 1e3)
+    return {"workload": workload_name(cfg, ["das", "dmas", "literal"][bf], B),
+            "beamformer": ["das", "dmas (identity)", "dmas (literal pairs)"][bf],
+            "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "fullres": fullres, "speedup_vs_fullres": value / fullres["value"],
+            "loc_error_mm": {"framework_mean": float(np.nanmean(err_fw)),
+                             "fullres_mean": float(np.nanmean(err_fr))},
+            "points_per_scan": {"mean": float(res["points_evaluated"].mean()),
+                                "full": int(np.prod(grid["n"]))},
+            "roofline": final_roofline(bf, M, cfg.window, res,
+                                       [p / max(calls, 1) for p in phase_ms], fma_meas,
+                                       lds_meas),
+            "status_ok": bool(np.all(res["status"] == 0)),
+            "clocks": clock_info}
+
+
+def measure_extras(args, cfg, bf, uwb, torch, batch, traces, flush, stream, fma_meas,
+                   lds_meas) -> dict:
+    """The paths and workloads besides the headline, each timed on its own after
+    the headline's timed region: the learned segment proposal on the headline's
+    own scans; the 256^3 hemispherical workload (literal and identity DMAS);
+    the 64^2 DAS workload; the uneven batch through the plan API (FP32, FP16,
+    BF16 traces) with a CUDA-graph replay."""
+    import copy
+    extra = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.fullres_steps = args.extra_steps, 3, 2
+    learned = run_learned(a, cfg, bf, uwb, torch, batch=batch, traces=traces)
+    extra["learned"] = {k: learned[k] for k in (
+        "value", "unit", "ms_per_step", "framework", "fullres", "speedup_vs_framework",
+        "speedup_vs_fullres", "agreement_with_framework", "agreement_with_fullres",
+        "fallback_rate", "loc_error_mm", "points_per_scan", "phase_ms_per_step", "roofline",
+        "cnn_roofline", "clocks")}
+    extra["learned"]["config"] = {k: learned["config"][k] for k in
+                                  ("threshold", "levels", "trained_on",
+                                   "scans_first_seed_offset")}
+    hemi = phantom.CONFIGS["hemi3d_256"]
+    extra["hemi3d_256"] = {
+        name: measure_workload(uwb, torch, hemi, b, 4, args.extra_steps, 2, 2, flush, stream,
+                               fma_meas, lds_meas)
+        for name, b in (("literal", 2), ("identity", 1))}
+    extra["das2d_64"] = measure_workload(uwb, torch, phantom.CONFIGS["das2d_64"], 0, 4096,
+                                         args.extra_steps, 3, 2, flush, stream, fma_meas,
+                                         lds_meas)
+    r = copy.copy(args)
+    r.batch, r.steps, r.warmup, r.beamformer = 256, args.extra_steps, 3, "dmas"
+    r.ragged_dim, r.ragged_literal = 2, False
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    extra["ragged"] = run_ragged(r, uwb, torch, graph_replay=True)
+    extra["ragged"]["clocks"] = clocks.stop()
+    return extra
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -757,8 +988,15 @@ def main():
                     help="scans per step (default 1024; 256 in multistatic mode)")
     ap.add_argument("--fullres-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--ref-scans-per-step", type=int, default=2)
+    ap.add_argument("--cpu-pool", type=int, default=CPU_POOL_SCANS,
+                    help="scans in the CPU legs' declared pool (reference arm: one pass per "
+                         "step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="localize mode: skip the other workloads measured after the "
+                         "headline (learned proposal, hemi3d_256, das2d_64, ragged batch)")
+    ap.add_argument("--extra-steps", type=int, default=5,
+                    help="timed steps of each extra workload")
     ap.add_argument("--mode", default="localize",
                     choices=["localize", "presence", "ragged", "learned", "progressive",
                              "multistatic"],
@@ -783,6 +1021,9 @@ def main():
         args.beamformer = "dmas" if ms_mode else "literal"
     cfg = phantom.CONFIGS[args.config]
     bf = BEAMFORMERS[args.beamformer]
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: relaunch under torch.distributed.run
+        sys.exit(launch_replicas(args.gpus))
     world, rank, local = dist_setup()
 
     if args.impl == "reference":
@@ -793,7 +1034,11 @@ def main():
     import torch
     import paper_1709_02549_gb300 as uwb
 
+    if local >= torch.cuda.device_count():
+        raise SystemExit(f"rank {rank}: local rank {local} but only "
+                         f"{torch.cuda.device_count()} visible GPU(s)")
     torch.cuda.set_device(local)
+    device_peaks(torch, local)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -815,7 +1060,9 @@ def main():
     if args.mode == "multistatic":
         print(json.dumps(run_multistatic(args, cfg, bf, uwb, torch)), flush=True)
         return
-    batch = phantom.make_batch(cfg, B, first_scan=shard_first_scan(rank, B))
+    first = shard_first_scan(rank, B)
+    batch = phantom.make_batch(cfg, B, first_scan=first)
+    batch["first_scan"] = first
     grid = cfg.grid()
     M, N = cfg.n_antennas, cfg.n_samples
     traces_host = torch.from_numpy(batch["traces"]).pin_memory()
@@ -864,12 +1111,7 @@ def main():
 
     res = uwb.results_from_device(out)
     status_ok = bool(np.all(res["status"] == 0))
-    roi_points = np.prod(res["roi_hi"] - res["roi_lo"], axis=1).astype(np.float64)
     pts_eval = res["points_evaluated"].astype(np.float64)
-    fpp = flops_per_point(bf, M, cfg.window)
-    final_ms = phase_ms[2] / max(calls, 1)
-    final_flops = float(roi_points.sum()) * fpp
-    achieved_tflops = final_flops / (final_ms / 1e3) / 1e12 if final_ms > 0 else None
     sha = kernel_sha()
     traffic = None
     if NCU_TRAFFIC[bf]["sha"] == sha:
@@ -877,59 +1119,13 @@ def main():
         traffic = NCU_TRAFFIC[bf]["bytes_per_scan"] * B
     # the same GPU's measured ceilings (paired-FMA chains; conflict-free shared loads)
     fma_meas, lds_meas = uwb.uwb_measure_peaks()
-    roofline = {
-        "bound": "alu",
-        "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": (achieved_tflops / FP32_PEAK_TFLOPS) if achieved_tflops else None,
-        "measured_peak": fma_meas,
-        "frac_of_measured": (achieved_tflops / fma_meas) if achieved_tflops else None,
-        "measured_peak_source": "uwb_measure_peaks: independent __ffma2_rn chains, "
-                                "8 CTAs x 256 threads per SM",
-        "traffic": traffic,
-        "kernel": f"k_image<{['DAS', 'DMAS', 'DMAS_LITERAL'][bf]}> final-region pass",
-        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.07 GHz",
-        "launch_ms": final_ms,
-        "flops_per_launch": final_flops,
-        "phase_ms_per_step": [p / max(calls, 1) for p in phase_ms],
-        "kernel_sha": sha,
-    }
-    if bf != 2:
-        # DAS and identity DMAS: shared loads or the FP32 pipe, whichever has the
-        # larger algorithmic demand per point (at 32 antennas and W = 20, DAS 21
-        # shared-load against 12.4 FP32-pipe SM clocks per point; identity DMAS
-        # 21 against 22.6)
-        roofline.update(load_or_alu_roofline(
-            float(roi_points.sum()), M, cfg.window, fp32_ops_per_point(bf, M, cfg.window),
-            final_ms, lds_meas, fma_meas))
-        roofline["tflops_achieved"] = achieved_tflops
+    roofline = final_roofline(bf, M, cfg.window, res, [p / max(calls, 1) for p in phase_ms],
+                              fma_meas, lds_meas)
+    roofline.update({"traffic": traffic, "kernel_sha": sha})
 
     # ---- full-resolution GPU images of the same scans (same beamformer) ----
-    P = int(np.prod(grid["n"]))
-    img = torch.empty(B, P, device="cuda")
-    peak = torch.empty(B, dtype=torch.int64, device="cuda")
-    uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img, peak)
-    torch.cuda.synchronize()
-    fr_ms = 0.0
-    for _ in range(args.fullres_steps):
-        flush.zero_()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        uwb.uwb_image_batch(bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, img, peak)
-        s1.record(stream)
-        torch.cuda.synchronize()
-        fr_ms += s0.elapsed_time(s1)
-    fr_value = B * args.fullres_steps / (fr_ms / 1e3)
-    pk = peak.cpu().numpy()
-    del img
-    gx, gy = grid["n"][0], grid["n"][1]
-    full_idx = np.stack([pk % gx, (pk // gx) % gy, pk // (gx * gy)], 1)
-    agree = float(np.mean(np.all(full_idx == res["loc_idx"], axis=1)))
-    err_fw, err_fr = [], []
-    for s in range(B):
-        xyz_fr = [grid["origin"][a] + full_idx[s, a] * grid["pitch"][a] for a in range(3)]
-        err_fw.append(nearest_error_mm(res["loc_xyz"][s], batch["tumors"][s]))
-        err_fr.append(nearest_error_mm(xyz_fr, batch["tumors"][s]))
+    fullres, err_fw, err_fr = fullres_compare(uwb, torch, cfg, bf, traces, ants, batch, res,
+                                              args.fullres_steps, flush, stream)
 
     # ---- end to end through the public API with host buffers: the reachable
     # window of every trace goes H2D, the search runs, the results come back ----
@@ -961,10 +1157,17 @@ def main():
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(B * uwb.RESULT_BYTES),
            "api": "uwb_localize_host (pinned host traces; only the reachable sample window "
                   "is copied)", "same_locations_as_device_path": e2e_same}
+    del ws_h, out_host
+
+    # ---- the other workloads and paths, measured after the timed headline ----
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = measure_extras(args, cfg, bf, uwb, torch, batch, traces, flush, stream,
+                                fma_meas, lds_meas)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cfg, bf, args.cpu_seconds)
+        cpu = cpu_baseline(cfg, bf, args.cpu_seconds, args.cpu_pool)
 
     if rank == 0:
         line = {
@@ -982,13 +1185,14 @@ def main():
             "e2e": e2e,
             "clocks": clock_info,
             "gpu_launches": 5 * args.steps,
-            "fullres": {"value": fr_value, "unit": UNIT, "ms_per_step": fr_ms / args.fullres_steps,
-                        "loc_agreement": agree},
-            "speedup_vs_fullres": value / fr_value,
+            "fullres": fullres,
+            "speedup_vs_fullres": value / (world * fullres["value"]),
             "loc_error_mm": {"framework_mean": float(np.nanmean(err_fw)),
                              "fullres_mean": float(np.nanmean(err_fr))},
-            "points_per_scan": {"mean": float(pts_eval.mean()), "full": P},
+            "points_per_scan": {"mean": float(pts_eval.mean()),
+                                "full": int(np.prod(grid["n"]))},
             "status_ok": status_ok,
+            **extras,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

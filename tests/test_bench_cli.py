@@ -10,7 +10,7 @@ from conftest import ROOT
 def test_reference_arm_prints_one_json_line():
     r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference",
                         "--config", "das2d_64", "--steps", "2", "--warmup", "3",
-                        "--ref-scans-per-step", "1"], capture_output=True, text=True,
+                        "--cpu-pool", "2"], capture_output=True, text=True,
                        timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     lines = [l for l in r.stdout.splitlines() if l.strip()]
@@ -66,3 +66,31 @@ def test_image_roofline_takes_the_resource_with_the_larger_demand():
     assert abs(idm["measured_peak"] - 39.0) < 1e-12
     # both resources are reported whichever binds
     assert abs(idm["other_resource"]["frac"] - das["frac"]) < 1e-12
+
+
+def test_flop_count_per_point():
+    """Algorithmic FLOP per focal point: 10 + 2W per antenna, plus W M(M - 1)
+    for literal DMAS pairs or W (2M + 3) for the identity form. At 32 antennas
+    and W = 20 the literal count is 21 440; a full 512^2 literal image is then
+    5.6e9 FLOP and a 256^3 one with 64 antennas 1.4e12."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert bench.flops_per_point(2, 32, 20) == 32 * 50 + 20 * 32 * 31 == 21440
+    assert bench.flops_per_point(1, 32, 20) == 32 * 50 + 20 * 67
+    assert bench.flops_per_point(0, 32, 20) == 32 * 50
+    assert round(512 ** 2 * bench.flops_per_point(2, 32, 20) / 1e9, 1) == 5.6
+    assert round(256 ** 3 * bench.flops_per_point(2, 64, 20) / 1e12, 1) == 1.4
+
+
+def test_derived_peaks_follow_the_device():
+    sys.path.insert(0, str(ROOT))
+    import bench
+    old = (bench.SMS, bench.SM_MAX_GHZ)
+    try:
+        bench.configure_peaks(148, 1.98)
+        assert abs(bench.FP32_PEAK_TFLOPS - 148 * 128 * 2 * 1.98 / 1e3) < 1e-9
+        assert abs(bench.LDS_PEAK_GWF - 148 * 1.98) < 1e-9
+        assert abs(bench.FP32_PIPE_PEAK_TOPS - 148 * 128 * 1.98 / 1e3) < 1e-9
+        assert "148 SMs" in bench.peak_source("flops")
+    finally:
+        bench.configure_peaks(*old)

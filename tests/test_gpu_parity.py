@@ -563,3 +563,25 @@ def test_device_entry_points_replay_in_a_cuda_graph(gpu, entry):
         torch.cuda.synchronize()
         for g, o in zip(graphed, outs):
             assert torch.equal(g, o)
+
+
+@pytest.mark.parametrize("bf", BFS)
+def test_exact_tie_scenes_follow_the_gpu_path(gpu, bf):
+    """Mirror-symmetric scenes (two equal noiseless scatterers at (+-x, y), the
+    symmetric 16-antenna ring, decimation 3 on the 64 x 64 grid, a lattice
+    symmetric under x -> 63 - x): the first split's low-x and high-x children
+    tie up to rounding, so the GPU may take either. Whichever it takes, the
+    oracle replayed along its path must agree on every later step."""
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], snr_db=None)
+    ants = phantom.antenna_positions(cfg).astype(np.float32)
+    grid = cfg.grid()
+    g_rule, o_rule = rule_pair(gpu, mode=0, decimation=3)
+    traces = np.stack([phantom.point_scatterer_traces(cfg, [[-x, y, 0], [x, y, 0]], [1, 1])
+                       for x, y in ((0.021, 0.013), (0.017, -0.02), (0.03, 0.004),
+                                    (0.012, 0.025))])
+    res = gpu_localize_batch(gpu, bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, g_rule)
+    for s in range(len(traces)):
+        scan = OracleScan(traces[s], ants, grid, cfg.v, cfg.fs, cfg.window, bf, o_rule)
+        o = scan.localize()
+        assert o["metric_gap"][0] < 1e-9          # the mirror children tie
+        compare_localize(res[s], scan, o)

@@ -45,3 +45,25 @@ def test_two_ranks_shard_scans_and_take_the_slowest_time():
 
 def test_single_process_timing_is_unchanged():
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+
+
+def test_gpus_flag_launches_one_rank_per_gpu_and_rank_zero_prints():
+    """`bench.py --gpus 2` without a launcher relaunches itself as two ranks of
+    torch.distributed.run; the reference arm runs on rank 0 only, which prints
+    the one JSON line with the world size as n_gpus."""
+    import json
+    import subprocess
+    import sys
+
+    from conftest import ROOT
+    r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--config", "das2d_64", "--steps", "1", "--warmup", "3",
+                        "--cpu-pool", "1"], capture_output=True, text=True, timeout=600,
+                       cwd=ROOT, env={k: v for k, v in os.environ.items()
+                                      if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")})
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
+    assert d["cpu_baseline"]["cores"] >= 1
