@@ -462,6 +462,31 @@ int uwb_cnn_pack(const float* theta, void* packed, void* stream);
 int uwb_cnn_forward(const void* packed, const float* maps, int batch, float* scores,
                     void* stream);
 
+/* The per-map record of the forward pass, UWB_CNN_RECORD_BYTES per map (map b
+ * at byte b * UWB_CNN_RECORD_BYTES). Map position (y, x) is buffer position
+ * u = 34 + 33 y + x. Byte offsets within one map's record:
+ *   0       X0 = E / max E, float, at 4 u
+ *   5120    A1, BF16: channel c of position u at 5120 + (c / 8) * 19616 +
+ *           16 u + 2 (c % 8)
+ *   83584   A2, same layout (after uwb_cnn_gradients: G1, the BF16 gradient
+ *           at layer 1's pre-activation)
+ *   162048  A3, same layout (after uwb_cnn_gradients: G2, layer 2's)
+ *   240512  segment means F[16][32], float
+ *   242560  dz[16] = (softmax(z) - onehot(label)) / batch, float (written
+ *           only when labels are given)
+ * The same record is the first batch * UWB_CNN_RECORD_BYTES bytes of the
+ * workspace of uwb_cnn_gradients. */
+#define UWB_CNN_RECORD_BYTES 242688
+
+/* uwb_cnn_forward that also writes the record above (record: 256-byte aligned
+ * device memory of at least batch * UWB_CNN_RECORD_BYTES bytes), for checking
+ * the network layer by layer. With labels (device int[batch] in [0, 16)) it
+ * also writes dz and the mean cross-entropy into *loss (one device float,
+ * zeroed first); labels may be NULL, and then loss is not used. */
+int uwb_cnn_forward_record(const void* packed, const float* maps, const int* labels, int batch,
+                           float* scores, float* loss, void* record, size_t record_bytes,
+                           void* stream);
+
 /* Workspace of uwb_cnn_train_step (a per-map record of the forward pass plus
  * one gradient vector); uwb_cnn_gradients needs batch * 242688 bytes. 0 for a
  * batch outside [1, 2^20]. */

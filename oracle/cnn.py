@@ -182,9 +182,38 @@ def proposal(z: np.ndarray, p: np.ndarray, threshold: float):
     return seg, conf >= threshold
 
 
+def head_grad(dz: np.ndarray, F: np.ndarray):
+    """Gradients of the head z[s] = bh + sum_c wh[c] F[s, c] for score
+    gradients dz [B, 16] and segment means F [B, 16, 32]: (dwh [32], dbh [1])."""
+    return np.einsum("bs,bsc->c", dz, F), np.array([dz.sum()])
+
+
+def g3_from_dz(dz: np.ndarray, A3: np.ndarray, wh: np.ndarray, quantise: bool = True):
+    """G3 = q(dA3 * [A3 > 0]): the gradient at layer 3's pre-activation, where
+    dA3[c, y, x] = dz[segment of (y, x)] wh[c] / 64 (the segment mean's share)."""
+    q = bf16 if quantise else _ident
+    B = dz.shape[0]
+    dF = dz[:, :, None] * wh[None, None, :]                 # [B, 16, 32]
+    dA3 = np.repeat(np.repeat(
+        dF.reshape(B, SEG, SEG, CH).transpose(0, 3, 1, 2), SEG_SIDE, axis=2),
+        SEG_SIDE, axis=3) / (SEG_SIDE * SEG_SIDE)
+    return q(dA3 * (A3 > 0))
+
+
+def layer_grad(G: np.ndarray, A_in: np.ndarray):
+    """Weight and bias gradients of conv(A_in; W) + b for its pre-activation
+    gradient G: (dW [Cout, 9, Cin], db [Cout]), summed over the batch."""
+    return conv_weight_grad(G, A_in), G.sum(axis=(0, 2, 3))
+
+
+def input_grad(G: np.ndarray, W: np.ndarray, A_in: np.ndarray, quantise: bool = True):
+    """The previous layer's pre-activation gradient q(conv^T(G; W) * [A_in > 0])."""
+    q = bf16 if quantise else _ident
+    return q(conv_input_grad(G, W) * (A_in > 0))
+
+
 def loss_and_grad(theta, maps, labels, quantise: bool = True):
     """Mean cross-entropy and its gradient with respect to theta (flat)."""
-    q = bf16 if quantise else _ident
     f = forward(theta, maps, quantise)
     B = maps.shape[0]
     labels = np.asarray(labels, dtype=np.int64)
@@ -195,21 +224,14 @@ def loss_and_grad(theta, maps, labels, quantise: bool = True):
     dz /= B
     P = f["P"]
     g = {}
-    g["wh"] = np.einsum("bs,bsc->c", dz, f["F"])
-    g["bh"] = np.array([dz.sum()])
-    dF = dz[:, :, None] * P["wh"][None, None, :]            # [B, 16, 32]
-    dA3 = np.repeat(np.repeat(
-        dF.reshape(B, SEG, SEG, CH).transpose(0, 3, 1, 2), SEG_SIDE, axis=2),
-        SEG_SIDE, axis=3) / (SEG_SIDE * SEG_SIDE)
-    G3 = q(dA3 * (f["A3"] > 0))
-    g["W3"] = conv_weight_grad(G3, f["A2"])
-    g["b3"] = G3.sum(axis=(0, 2, 3))
-    G2 = q(conv_input_grad(G3, f["W3"]) * (f["A2"] > 0))
-    g["W2"] = conv_weight_grad(G2, f["A1"])
-    g["b2"] = G2.sum(axis=(0, 2, 3))
-    G1 = q(conv_input_grad(G2, f["W2"]) * (f["A1"] > 0))
-    g["W1"] = conv_weight_grad(G1, f["X0"])[:, :, 0]
-    g["b1"] = G1.sum(axis=(0, 2, 3))
+    g["wh"], g["bh"] = head_grad(dz, f["F"])
+    G3 = g3_from_dz(dz, f["A3"], P["wh"], quantise)
+    g["W3"], g["b3"] = layer_grad(G3, f["A2"])
+    G2 = input_grad(G3, f["W3"], f["A2"], quantise)
+    g["W2"], g["b2"] = layer_grad(G2, f["A1"])
+    G1 = input_grad(G2, f["W2"], f["A1"], quantise)
+    dW1, g["b1"] = layer_grad(G1, f["X0"])
+    g["W1"] = dW1[:, :, 0]
     return loss, pack(g)
 
 

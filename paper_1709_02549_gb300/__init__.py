@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
             "uwb_cnn_pack": (i, [vp, vp, vp]),
             "uwb_cnn_forward": (i, [vp, vp, i, vp, vp]),
             "uwb_cnn_train_workspace": (sz, [i]),
+            "uwb_cnn_forward_record": (i, [vp, vp, vp, i, vp, vp, vp, sz, vp]),
             "uwb_cnn_gradients": (i, [vp, vp, vp, i, vp, vp, vp, sz, vp]),
             "uwb_cnn_adam": (i, [vp, vp, vp, vp, vp, i, ctypes.c_float, vp]),
             "uwb_cnn_train_step": (i, [vp, vp, vp, vp, vp, vp, i, i, ctypes.c_float, vp, vp, sz,
@@ -575,6 +576,42 @@ def uwb_cnn_forward(packed, maps, scores, stream=None):
     """maps: CUDA float32 [B, 32, 32]; scores: CUDA float32 [B, 16]."""
     _check(lib().uwb_cnn_forward(_ptr(packed, "packed"), _f32(maps, "maps"), maps.shape[0],
                                  _f32(scores, "scores"), _stream(stream)), "uwb_cnn_forward")
+
+
+CNN_RECORD_BYTES = 242688
+
+
+def uwb_cnn_forward_record(packed, maps, scores, record, labels=None, loss=None, stream=None):
+    """uwb_cnn_forward that also fills `record` (CUDA uint8 [B * CNN_RECORD_BYTES]);
+    with labels (CUDA int32 [B]) also dz and the loss (CUDA float32 [1])."""
+    _check(lib().uwb_cnn_forward_record(_ptr(packed, "packed"), _f32(maps, "maps"),
+                                        _ptr(labels, "labels", True), maps.shape[0],
+                                        _f32(scores, "scores"), _ptr(loss, "loss", True),
+                                        _ptr(record, "record"),
+                                        record.numel() * record.element_size(),
+                                        _stream(stream)), "uwb_cnn_forward_record")
+
+
+def cnn_record_arrays(record, B: int) -> dict:
+    """Decodes B maps' forward records (host bytes, the layout of
+    UWB_CNN_RECORD_BYTES in uwb.h) into float64 arrays: X0 [B, 32, 32], A1, A2,
+    A3 [B, 32, 32, 32] (channel first), F [B, 16, 32], dz [B, 16]."""
+    raw = np.asarray(record, dtype=np.uint8)[:B * CNN_RECORD_BYTES].reshape(B, CNN_RECORD_BYTES)
+    y, x = np.mgrid[0:32, 0:32]
+    u = 34 + 33 * y + x                                         # [32, 32]
+    x0 = raw[:, :5120].copy().view(np.float32)                  # [B, 1280]
+    out = {"X0": x0[:, u].astype(np.float64)}
+    c = np.arange(32)[:, None, None]
+    off = (c // 8) * 19616 + 16 * u[None] + 2 * (c % 8)         # [32, 32, 32]
+    for name, base in (("A1", 5120), ("A2", 83584), ("A3", 162048)):
+        lo = raw[:, base + off].astype(np.uint32)
+        hi = raw[:, base + off + 1].astype(np.uint32)
+        bits = ((hi << 8) | lo) << 16
+        out[name] = bits.view(np.float32).astype(np.float64)
+    out["F"] = raw[:, 240512:240512 + 2048].copy().view(np.float32).reshape(B, 16, 32) \
+        .astype(np.float64)
+    out["dz"] = raw[:, 242560:242560 + 64].copy().view(np.float32).astype(np.float64)
+    return out
 
 
 def uwb_cnn_train_workspace(batch) -> int:

@@ -1784,6 +1784,36 @@ int uwb_cnn_forward(const void* packed, const float* maps, int batch, float* sco
   return e == cudaSuccess ? UWB_OK : cuda_fail(e, "network forward launch");
 }
 
+static_assert(cnn::SAVE_BYTES == UWB_CNN_RECORD_BYTES && cnn::SAVE_A1 == 5120 &&
+                  cnn::SAVE_A2 == 83584 && cnn::SAVE_A3 == 162048 && cnn::SAVE_F == 240512 &&
+                  cnn::SAVE_DZ == 242560 && cnn::LBO_ACT == 19616 && cnn::PAD0 == 34 &&
+                  cnn::Q == 33,
+              "the record layout documented in uwb.h");
+
+int uwb_cnn_forward_record(const void* packed, const float* maps, const int* labels, int batch,
+                           float* scores, float* loss, void* record, size_t record_bytes,
+                           void* stream) {
+  int st;
+  if ((st = check_cnn_batch(batch))) return st;
+  if (!packed || !maps || !scores) return fail(UWB_ERR_ARG, "null argument");
+  if (labels && !loss) return fail(UWB_ERR_ARG, "labels need a loss");
+  if (!record || (reinterpret_cast<uintptr_t>(record) & 255))
+    return fail(UWB_ERR_WORKSPACE, "record must be non-null and 256-byte aligned");
+  if (record_bytes < static_cast<size_t>(batch) * cnn::SAVE_BYTES)
+    return fail(UWB_ERR_WORKSPACE, "record of %zu bytes < %zu needed", record_bytes,
+                static_cast<size_t>(batch) * cnn::SAVE_BYTES);
+  if ((st = umma_ready())) return st;
+  Device* dev;
+  if ((st = device(&dev))) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (labels && (e = cudaMemsetAsync(loss, 0, 4, cs)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync");
+  e = cnn::launch_forward(packed, maps, batch, scores, labels, record, labels ? loss : nullptr,
+                          dev->status, cnn_ctas(*dev, batch), cs);
+  return e == cudaSuccess ? UWB_OK : cuda_fail(e, "network forward launch");
+}
+
 size_t uwb_cnn_train_workspace(int batch) {
   if (batch < 1 || batch > (1 << 20)) return 0;
   return train_layout_grad(batch) + align256(cnn::N_PARAMS * 4);
