@@ -151,3 +151,17 @@ def test_wait_selftest_rejects_probe_counts_on_the_host(uwb):
     for probes in (0, -5, (1 << 24) + 1):
         assert L.uwb_wait_selftest(probes) == uwb.UWB_ERR_ARG
         assert "probes" in uwb.uwb_last_error()
+
+
+def _header_define(name):
+    text = (ROOT / "include" / "uwb.h").read_text()
+    m = re.search(r"#define\s+" + name + r"\s+(.+)", text)
+    assert m, name
+    return eval(re.sub(r"(\d+)u\b", r"\1", m.group(1)))
+
+
+def test_binding_constants_equal_the_header(uwb):
+    assert uwb.NOALLOC_SCRATCH_BYTES == _header_define("UWB_NOALLOC_SCRATCH_BYTES")
+    assert uwb.CNN_RECORD_BYTES == _header_define("UWB_CNN_RECORD_BYTES")
+    assert uwb.CNN_PARAMS == _header_define("UWB_CNN_PARAMS")
+    assert uwb.CNN_PACKED_BYTES == _header_define("UWB_CNN_PACKED_BYTES")
