@@ -37,7 +37,12 @@
  *    Errors found on the device (a bounded wait that ran out, non-finite
  *    energies) are reported in uwb_result.status or by uwb_device_status().
  *  - Staging waits inside kernels are bounded; a kernel that gives up records
- *    UWB_ERR_TIMEOUT instead of hanging.
+ *    UWB_ERR_TIMEOUT instead of hanging. A CTA that gives up leaves after one
+ *    more bounded wait even if its copy is still in flight, and that copy may
+ *    still land in shared memory another CTA of the same launch then uses:
+ *    once UWB_ERR_TIMEOUT is reported, treat every output of that call as
+ *    invalid, not only the scans it names. Launches that hand out tiles
+ *    through a counter stop handing them out after such a timeout.
  *  - Image launches with at least 4 tiles per CTA and several CTAs per SM
  *    hand tiles out through a counter taken from a per-device pool of 64 (a
  *    counter is reused only after the launch that used it has completed).

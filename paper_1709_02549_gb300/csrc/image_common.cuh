@@ -826,8 +826,13 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
           if (__syncthreads_or(!ok)) {
             // the copy did not land in time: record it, give the copy a last
             // bounded chance to finish (it writes this CTA's shared memory),
-            // then leave without touching the outputs.
-            if (tid == 0) atomicExch(P.status, UWB_ERR_TIMEOUT);
+            // then leave without touching the outputs. The launch's results
+            // are invalid from here on, so a counter-driven launch hands out
+            // no more tiles (every later grab lands beyond the last tile).
+            if (tid == 0) {
+              atomicExch(P.status, UWB_ERR_TIMEOUT);
+              if (dyn) atomicExch(P.work, INT_MAX / 2);
+            }
             for (long it = 0; it < kWaitProbes && !ok; ++it) ok = mbar_try_wait(bar, phase);
             __syncthreads();
             return;
