@@ -434,10 +434,9 @@ def run_ragged(args, uwb, torch, graph_replay=False):
     import oracle
     oracle.build()
     B = args.batch
-    # literal-pair DMAS is built for up to 64 antennas: --ragged-literal draws
-    # 16-64 antennas per scan; otherwise a DMAS request runs the identity form
-    # on the 16-96 antenna batches
-    max_m = 64 if args.ragged_literal else 96
+    # --ragged-literal: literal-pair DMAS on the 16-96 antenna batch; otherwise a
+    # DMAS request runs the identity form
+    max_m = 96
     bf = 2 if args.ragged_literal else (BEAMFORMERS[args.beamformer]
                                         if args.beamformer != "literal" else 1)
     dim = args.ragged_dim
@@ -1007,7 +1006,7 @@ def main():
     ap.add_argument("--ragged-dim", type=int, default=2, choices=[2, 3],
                     help="ragged mode: 2-D grids (128^2-1024^2) or 128^3 cubes")
     ap.add_argument("--ragged-literal", action="store_true",
-                    help="ragged mode: literal-pair DMAS on scans of 16-64 antennas")
+                    help="ragged mode: literal-pair DMAS on the scans of 16-96 antennas")
     ap.add_argument("--decimation2", type=int, default=0,
                     help="second decimation factor of the presence test (0 = 2/3 of the first)")
     args = ap.parse_args()

@@ -67,13 +67,14 @@ struct KernelShape {
   static constexpr bool pair = !lit && !RG;
   static constexpr int pp = pair ? 2 : 1;
   static constexpr int threads = (lit || (pair && !MS)) ? 128 : 256;
-  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas.
+  // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas, 2
+  // for the 64-antenna block, 3 for the 96-antenna block form (no delay table).
   // Monostatic point pairs: DAS 4 and identity DMAS 3, where the paired
   // window accumulators fit registers; ragged (one point per thread): DAS 3,
   // identity DMAS 2. Multistatic: one CTA per SM (its channel window takes
   // most of the shared memory), 256 threads of two points.
   static constexpr int min_blocks =
-      lit ? (V <= 32 ? 4 : 2)
+      lit ? (V <= 32 ? 4 : (V <= 64 ? 2 : 3))
           : (MS ? 1 : (pair ? (BF == BF_DAS ? 4 : 3) : (BF == BF_DAS ? 3 : 2)));
 };
 
@@ -552,6 +553,160 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
   return energy;
 }
 
+// ------------------------------------------------------- literal DMAS, blocks of 32
+// Register blocks beyond 64 antennas (MMAX = 32 NB): for one window pair (k,
+// k+1) the M(M-1)/2 products are formed block pair by block pair, every one
+// explicitly. Block a's 32 interpolated sample pairs are held in registers
+// while its own pairs are formed (a streamed triangle, as in energy_literal);
+// then every antenna of each later block is interpolated and multiplied with
+// the 32 held ones. A scan forms pairs only among its own M antennas. Each
+// antenna's delay is recomputed at each visit: a per-thread (offset,
+// fraction) table of 96 antennas would take 96 KB of shared memory per CTA
+// beside the staged window, leaving one CTA per SM.
+
+// Shared-window byte address (staged) or absolute sample index (global path)
+// of sample 0 of antenna i's window for this focal point, and its fraction:
+// the same arithmetic as energy_literal's table.
+template <bool STAGED>
+__device__ __forceinline__ int lit_delay(const ImgParams& P, const float4* __restrict__ sAnt,
+                                         int i, float px, float py, float pz, float kscale,
+                                         float hf, uint32_t base, int nlo, int cl_lo, int cl_hi,
+                                         float& f) {
+  const float4 a = sAnt[i];
+  const float dx = px - a.x;
+  const float dy = py - a.y;
+  const float dz = pz - a.z;
+  const float d = dist3(dx, dy, dz);
+  const float t = fmaf(d, kscale, -hf);
+  const float fl = floorf(t);
+  f = t - fl;
+  const int n0 = static_cast<int>(fl);
+  if (STAGED) return static_cast<int>(base) + 4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
+  return n0;
+}
+
+// The interpolated sample pair (k0, k0 + 1) of antenna i from its delay.
+template <bool STAGED>
+__device__ __forceinline__ float2 lit_pair(const ImgParams& P, const ScanDesc* __restrict__ sS,
+                                           int i, int at, float f, int k0) {
+  LitRaw r;
+  r.f = f;
+  if (STAGED) {
+    const uint32_t a = static_cast<uint32_t>(at) + 4u * static_cast<uint32_t>(k0);
+    asm volatile(
+        "ld.shared.f32 %0, [%3];\n\t"
+        "ld.shared.f32 %1, [%3+4];\n\t"
+        "ld.shared.f32 %2, [%3+8];"
+        : "=f"(r.y0), "=f"(r.y1), "=f"(r.y2)
+        : "r"(a));
+  } else {
+    const ScanDesc S = *sS;
+    r.y0 = sample_at(S, P.dtype, i, at + k0);
+    r.y1 = sample_at(S, P.dtype, i, at + k0 + 1);
+    r.y2 = sample_at(S, P.dtype, i, at + k0 + 2);
+  }
+  return lit_interp(r);
+}
+
+template <int NB, bool STAGED, bool RG>
+__device__ __forceinline__ float energy_literal_blocks(const ImgParams& P,
+                                                       const ScanDesc* __restrict__ sS,
+                                                       const float* __restrict__ sTr,
+                                                       const float4* __restrict__ sAnt, int nlo,
+                                                       int cl_lo, int cl_hi, float px, float py,
+                                                       float pz) {
+  const int M = min(scan_M<RG>(P, sS), 32 * NB);
+  const float kscale = scan_kscale<RG>(P, sS);
+  const float hf = static_cast<float>(P.h);
+  const uint32_t base = STAGED ? smem_u32(sTr) : 0u;
+  const int nb = (M + 31) >> 5;
+  float energy = 0.f;
+  for (int k0 = 0; k0 < P.W; k0 += 2) {
+    float2 acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int blk = 0; blk < nb; ++blk) {
+      const int ia = 32 * blk;
+      const int na = min(32, M - ia);
+      // the held block: its own pairs, streamed one antenna ahead
+      float2 xa[32];
+      float fn;
+      int an = lit_delay<STAGED>(P, sAnt, ia, px, py, pz, kscale, hf, base, nlo, cl_lo, cl_hi,
+                                 fn);
+      float2 xn = lit_pair<STAGED>(P, sS, ia, an, fn, k0);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < na) {
+          const float2 x = xn;
+          if (j + 1 < na) {
+            an = lit_delay<STAGED>(P, sAnt, ia + j + 1, px, py, pz, kscale, hf, base, nlo, cl_lo,
+                                   cl_hi, fn);
+            xn = lit_pair<STAGED>(P, sS, ia + j + 1, an, fn, k0);
+          }
+#pragma unroll
+          for (int i = 0; i < j; ++i) acc[(i + j) & 7] = __ffma2_rn(xa[i], x, acc[(i + j) & 7]);
+          xa[j] = x;
+        } else {
+          xa[j] = make_float2(0.f, 0.f);
+        }
+        asm volatile("" ::: "memory");
+      }
+      // every antenna of the later blocks against the held block, four at a
+      // time: the next four are interpolated (independent delay chains) while
+      // the current four's 128 products run
+      int jb = ia + 32;
+      float2 xq[4];
+      auto load4 = [&](int j0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float fq;
+          const int aq = lit_delay<STAGED>(P, sAnt, j0 + q, px, py, pz, kscale, hf, base, nlo,
+                                           cl_lo, cl_hi, fq);
+          xq[q] = lit_pair<STAGED>(P, sS, j0 + q, aq, fq, k0);
+        }
+      };
+      if (jb + 4 <= M) load4(jb);
+#pragma unroll 1
+      for (; jb + 4 <= M; jb += 4) {
+        const float2 x0 = xq[0], x1 = xq[1], x2 = xq[2], x3 = xq[3];
+        if (jb + 8 <= M) load4(jb + 4);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i & 7] = __ffma2_rn(xa[i], x0, acc[i & 7]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i & 7] = __ffma2_rn(xa[i], x1, acc[i & 7]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i & 7] = __ffma2_rn(xa[i], x2, acc[i & 7]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i & 7] = __ffma2_rn(xa[i], x3, acc[i & 7]);
+        asm volatile("" ::: "memory");
+      }
+#pragma unroll 1
+      for (; jb < M; ++jb) {
+        float fr;
+        const int ar = lit_delay<STAGED>(P, sAnt, jb, px, py, pz, kscale, hf, base, nlo, cl_lo,
+                                         cl_hi, fr);
+        const float2 x = lit_pair<STAGED>(P, sS, jb, ar, fr, k0);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i & 7] = __ffma2_rn(xa[i], x, acc[i & 7]);
+      }
+    }
+    const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
+    const float2 s45 = __fadd2_rn(acc[4], acc[5]), s67 = __fadd2_rn(acc[6], acc[7]);
+    const float2 p = __fadd2_rn(__fadd2_rn(s01, s23), __fadd2_rn(s45, s67));
+    energy = fmaf(p.x, p.x, energy);
+    if (k0 + 1 < P.W) energy = fmaf(p.y, p.y, energy);
+  }
+  return energy;
+}
+
+template <int NB, bool RG>
+__device__ __noinline__ float energy_literal_blocks_global(const ImgParams& P, const ScanDesc* sS,
+                                                           const float4* sAnt, float px, float py,
+                                                           float pz) {
+  return energy_literal_blocks<NB, false, RG>(P, sS, nullptr, sAnt, 0, 0, 0, px, py, pz);
+}
+
 // The global-load fallback (a window wider than the staged span) runs as a
 // real call, so its bounds checks and type conversions do not add to the
 // register allocation of the staged hot path.
@@ -846,7 +1001,7 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
               return f16 ? __half2float(__ushort_as_half(b))
                          : __bfloat162float(__ushort_as_bfloat16(b));
             };
-            if (BF == BF_DMAS_LIT) {  // the raw window sits in a separate area
+            if (BF == BF_DMAS_LIT && V <= 64) {  // the raw window sits in the delay table
               for (int j = tid; j < total_s; j += T) sTr[j] = widen(j);
             } else {
               // in place: the raw window starts at byte >= 2 * total_s of the
@@ -940,7 +1095,12 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
       }
     } else if (valid[0]) {
       if constexpr (BF == BF_DMAS_LIT) {
-        if constexpr (V <= 16) {
+        if constexpr (V > 64) {
+          energy[0] = fits ? energy_literal_blocks<V / 32, true, RG>(P, sS, sTr, sAnt, nlo, cl_lo,
+                                                                     cl_hi, px[0], py[0], pz[0])
+                           : energy_literal_blocks_global<V / 32, RG>(P, sS, sAnt, px[0], py[0],
+                                                                      pz[0]);
+        } else if constexpr (V <= 16) {
           energy[0] = fits ? energy_literal4<V, true, RG>(P, sS, sTr, sAnt, sNF, nlo, cl_lo, cl_hi,
                                                           px[0], py[0], pz[0])
                            : energy_literal_global<V>(P, sS, sAnt, sNF, px[0], py[0], pz[0]);

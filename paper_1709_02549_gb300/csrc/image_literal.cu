@@ -14,6 +14,8 @@ cudaError_t launch_image_literal(int v, const ImgParams& p, const CUtensorMap* t
       return launch_variant<BF_DMAS_LIT, 32, false>(p, tmap, ctas, threads, smem, st);
     case 64:
       return launch_variant<BF_DMAS_LIT, 64, false>(p, tmap, ctas, threads, smem, st);
+    case 96:
+      return launch_variant<BF_DMAS_LIT, 96, false>(p, tmap, ctas, threads, smem, st);
     default:
       return cudaErrorInvalidValue;
   }
@@ -27,6 +29,8 @@ int occupancy_image_literal(int v, bool rg, int threads, size_t smem) {
       return occupancy_variant<BF_DMAS_LIT, 32, false>(rg, threads, smem);
     case 64:
       return occupancy_variant<BF_DMAS_LIT, 64, false>(rg, threads, smem);
+    case 96:
+      return occupancy_variant<BF_DMAS_LIT, 96, false>(rg, threads, smem);
     default:
       return 0;
   }

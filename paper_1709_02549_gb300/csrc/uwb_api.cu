@@ -235,15 +235,16 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   if (var.ms && bf == BF_DMAS_LIT)
     return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS is built for monostatic data only");
   if (bf == BF_DMAS_LIT) {
-    if (M > 64) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 64 (M=%d)", M);
-    var.v = M <= 16 ? 16 : (M <= 32 ? 32 : 64);
+    if (M > 96) return fail(UWB_ERR_UNSUPPORTED, "literal-pair DMAS supports M <= 96 (M=%d)", M);
+    var.v = M <= 16 ? 16 : (M <= 32 ? 32 : (M <= 64 ? 64 : 96));
     // window samples go in fours (16-antenna block) or pairs
     var.wpad = var.v <= 16 ? (W + 3) / 4 * 4 : (W + 1) / 2 * 2;
     var.threads = 128;
     var.rows = var.v;
-    // 4 CTAs (2 for the 64-antenna block) per SM, each with the 1 KB the
-    // runtime reserves per CTA, fill the SM's 228 KB
-    var.smem_budget = var.v <= 32 ? 56 * 1024 : 112 * 1024;
+    // 4 CTAs (2 for the 64-antenna block, 3 for the 96-antenna block form)
+    // per SM, each with the 1 KB the runtime reserves per CTA, fill the SM's
+    // 228 KB
+    var.smem_budget = var.v <= 32 ? 56 * 1024 : (var.v <= 64 ? 112 : 74) * 1024;
     var.tdim[0] = 128; var.tdim[1] = 0; var.tdim[2] = 0;  // linear tiles
   } else {
     // window chunk: the whole window up to 20 samples; longer windows go in

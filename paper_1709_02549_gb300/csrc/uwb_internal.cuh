@@ -121,7 +121,10 @@ inline __host__ __device__ SmemLayout image_smem_layout(int bf, int Mcap, int Rc
   const size_t window = static_cast<size_t>(rows) * span * 4;
   size_t off = align_up(window, 128);
   L.raw = off;
-  if (dtype != DT_F32 && bf != BF_DMAS_LIT) {
+  // literal DMAS up to 64 antennas keeps a per-thread (offset, fraction)
+  // table; the 32-antenna block form beyond recomputes delays instead
+  const bool lit_table = bf == BF_DMAS_LIT && rows <= 64;
+  if (dtype != DT_F32 && !lit_table) {
     // a 16-bit window lands in the upper half of the float window's area
     // (128-byte aligned for the copy) and is widened in place, front to back
     L.raw = align_up(static_cast<size_t>(rows) * span * 2, 128);
@@ -132,16 +135,15 @@ inline __host__ __device__ SmemLayout image_smem_layout(int bf, int Mcap, int Rc
   off += static_cast<size_t>(Mcap) * 16;
   L.ch = off;
   if (ms) off += static_cast<size_t>(Rcap) * 8;
-  if (bf == BF_DMAS_LIT && dtype != DT_F32) {
-    // literal DMAS writes its per-thread (offset, fraction) table only after a
-    // staged window has been widened, so a 16-bit window lands in the table
-    // (rows * span * 2 <= rows * threads * 8 bytes: span <= 256 <= 4 * threads;
-    // 128-byte aligned for the copy)
+  if (lit_table && dtype != DT_F32) {
+    // the table is written only after a staged window has been widened, so a
+    // 16-bit window lands in the table (rows * span * 2 <= rows * threads * 8
+    // bytes: span <= 256 <= 4 * threads; 128-byte aligned for the copy)
     off = align_up(off, 128);
     L.raw = off;
   }
   L.nf = off;
-  if (bf == BF_DMAS_LIT) off += static_cast<size_t>(rows) * threads * 8;
+  if (lit_table) off += static_cast<size_t>(rows) * threads * 8;
   L.d = off;
   if (ms) off += static_cast<size_t>(Mcap) * threads * 4;
   off = align_up(off, 16);

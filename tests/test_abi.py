@@ -87,8 +87,8 @@ def test_bad_rule_and_workspace_are_rejected(uwb):
                           None) == -6
     assert L.uwb_localize(fake, 4, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 7,
                           ctypes.byref(ok), fake, 1 << 20, fake, None, None) == -1
-    # literal pairs are built for up to 64 antennas
-    assert L.uwb_dmas_image(fake, 65, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 1, fake, None,
+    # literal pairs are built for up to 96 antennas
+    assert L.uwb_dmas_image(fake, 97, 64, fake, ctypes.byref(g), 1e8, 5e10, 4, 1, fake, None,
                             None) == -5
 
 

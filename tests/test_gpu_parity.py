@@ -58,6 +58,9 @@ CASES = {
     "literal_register_block_64": (33, 640, (19, 21, 1), 0.08, 5, 2),
     "three_d": (12, 1024, (20, 18, 14), 0.08, 20, 3),
     "window_beyond_shared_memory": (8, 4096, (16, 12, 1), 0.60, 20, 2),  # global-load path
+    "literal_block_96": (96, 1024, (23, 19, 1), 0.08, 20, 2),       # three 32-antenna blocks
+    "literal_block_70": (70, 1024, (17, 21, 1), 0.08, 9, 2),        # a partial last block
+    "block_96_beyond_shared_memory": (80, 4096, (11, 9, 1), 0.60, 20, 2),
 }
 
 
@@ -145,6 +148,14 @@ def test_localize_small_scans(gpu, bf):
 @pytest.mark.parametrize("metric", [1, 2, 3])
 def test_localize_other_metrics(gpu, metric):
     _check_batch(gpu, phantom.CONFIGS["das2d_64"], 0, range(6), {"metric": metric})
+
+
+@pytest.mark.parametrize("bf", [1, 2])
+def test_localize_96_antennas(gpu, bf):
+    """Localisation with a 96-antenna ring (literal pairs through the
+    32-antenna block form; identity DMAS beside it)."""
+    cfg = phantom.with_changes(phantom.CONFIGS["das2d_64"], n_antennas=96, radius=0.06)
+    _check_batch(gpu, cfg, bf, range(4))
 
 
 def test_localize_manual_decimation_and_framing(gpu):

@@ -204,15 +204,18 @@ def test_linear_and_shaped_tiles_give_identical_results(gpu, bf, grid_n):
     assert bool((img0 >= 0).all())
 
 
+@pytest.mark.parametrize("antennas", [(8, 20, 40, 60), (8, 33, 70, 96)])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_ragged_literal_blocks_per_scan_match_oracle(gpu, dtype):
+def test_ragged_literal_blocks_per_scan_match_oracle(gpu, dtype, antennas):
     """A literal-DMAS plan holds scans of 8 to 60 antennas (the 64-antenna
-    register block); each scan runs the smallest block that holds it (16, 32
-    or 64 antennas), and images and localisations match the oracle. 16-bit
-    windows land in the per-thread delay table before they are widened."""
+    register block: each scan runs the smallest block that holds it, 16, 32 or
+    64 antennas, and 16-bit windows land in the per-thread delay table before
+    they are widened) or of 8 to 96 (the 96-antenna block form: pairs formed
+    block pair by block pair up to each scan's own antenna count, 16-bit
+    windows in their own area); images and localisations match the oracle."""
     base = phantom.CONFIGS["das2d_64"]
     scans = []
-    for k, m in enumerate((8, 20, 40, 60)):
+    for k, m in enumerate(antennas):
         cfg = phantom.with_changes(base, n_antennas=m, grid_n=(40 + 3 * k, 36, 1),
                                    n_samples=1024, n_clutter=5)
         scans.append((cfg, phantom.make_scan(cfg, phantom.BASE_SEED + 950 + k)))
