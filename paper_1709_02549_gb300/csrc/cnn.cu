@@ -84,13 +84,17 @@ __device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t phase, int* sta
 // each MMA adds its operand's byte offset / 16 to the 14-bit address field,
 // which stays inside [0, 2^14) for every operand of the layer (shared-memory
 // addresses are below 256 KB and all offsets land inside the buffers), so
-// nothing carries into the stride fields.
-__device__ __forceinline__ void issue_conv(uint32_t in_base, uint32_t w_base, uint32_t tmem) {
+// nothing carries into the stride fields. This thread issues tiles first,
+// first + stride, ...: each tile's 18 MMAs, then an arrive on bars[i] once
+// they (and every earlier MMA of this thread) have completed, so that tile
+// i's epilogue can run while the tensor cores compute later tiles.
+__device__ __forceinline__ void issue_conv_tiles(uint32_t in_base, uint32_t w_base, uint32_t tmem,
+                                                 uint64_t* bars, int first, int stride) {
   const uint64_t a0 = umma_desc(in_base + PAD0 * 16, LBO_ACT, 128);
   const uint64_t b0 = umma_desc(w_base, 512, 128);
 #pragma unroll 1
-  for (int i = 0; i < TILES; ++i) {
-    const uint64_t ai = a0 + static_cast<uint64_t>(i * 128);  // 128 rows of 16 bytes
+  for (int i = first; i < TILES; i += stride) {
+    const uint64_t ai = a0 + static_cast<uint64_t>(i * 128);
     const uint32_t d = tmem + i * CH;
 #pragma unroll
     for (int t = 0; t < TAPS; ++t)
@@ -100,7 +104,17 @@ __device__ __forceinline__ void issue_conv(uint32_t in_base, uint32_t w_base, ui
         const uint64_t b = b0 + static_cast<uint64_t>((t * WTAP + ks * 2 * 512) / 16);
         umma_bf16(d, ai + static_cast<uint64_t>(da), b, kIdesc, (t | ks) != 0);
       }
+    umma_commit(bars + i);
   }
+}
+
+// One warp's bounded wait for a phase of `bar`: lane 0 polls, the warp learns
+// whether it came.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t phase, int lane) {
+  uint32_t ok = 0;
+  if (lane == 0)
+    for (long it = 0; it < kProbes && !ok; ++it) ok = mbar_try_wait(bar, phase);
+  return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
 // ---------------------------------------------------------------- self-check
@@ -167,19 +181,37 @@ constexpr int W1_ROW = 12;                     // W1 rows padded to 3 float4
 constexpr int F_W1 = F_X + U * 4;              // W1 as float [32][12]
 constexpr int F_BIAS = F_W1 + CH * W1_ROW * 4; // b1, b2, b3, wh [32] each, bh
 constexpr int F_F = F_BIAS + 144 * 4;          // segment means, [32 channels][16 segments]
-constexpr int F_RED = F_F + SEGS * CH * 4;     // reduction scratch [8]
-constexpr int F_BAR = F_RED + 64;
-constexpr int F_SLOT = F_BAR + 8;
+constexpr int F_RED = F_F + SEGS * CH * 4;     // reduction scratch [16]
+constexpr int F_BAR = F_RED + 64;              // one mbarrier per tile
+constexpr int F_SLOT = F_BAR + 8 * 16;
 constexpr int F_SMEM = F_SLOT + 8;
 static_assert(F_W2 % 16 == 0 && F_W3 % 16 == 0 && F_X % 16 == 0 && F_BAR % 8 == 0, "alignment");
 
-// Epilogue of a forward layer: TMEM tile rows + bias, ReLU, BF16 -> `out`.
-// Warps 0-3 take the even tiles, warps 4-7 the odd ones; a warp reads the
-// TMEM lane quarter (warp % 4), i.e. tile rows 32 (warp % 4) + lane.
-__device__ __forceinline__ void epilogue_relu(unsigned char* out, const float* bias,
-                                              uint32_t tmem, int warp, int lane) {
+// The forward kernel runs 16 warps. One lane of each of warps 0-3 (one warp
+// per scheduler) issues the MMAs of tiles w, w + 4, ...: with N = 32 output
+// channels each MMA is short, and one issuing thread left the tensor pipe
+// idle between them (162 MMAs per layer took 4.0 us from one thread, 5.9 us
+// beside polling epilogue warps, 4.0 us from four threads while the
+// epilogues of finished tiles run). Warps 4-15 are three epilogue groups of
+// four, group g taking tiles g, g + 3, g + 6 of a layer, each as soon as its
+// own commit has arrived; every warp takes part in the CUDA-core work
+// (normalisation, layer 1, segment means).
+constexpr int F_THREADS = 512;
+constexpr int F_WARPS = F_THREADS / 32;
+static_assert(F_WARPS * 2 <= 64 && TILES == 9, "reduction scratch and epilogue groups");
+
+// Epilogue of a forward layer for this warp's tiles: TMEM tile rows + bias,
+// ReLU, BF16 -> `out`. A warp reads the TMEM lane quarter (warp % 4), i.e.
+// tile rows 32 (warp % 4) + lane. Returns false if a tile's commit did not
+// arrive within the bounded wait.
+__device__ __forceinline__ bool epilogue_relu(unsigned char* out, const float* bias,
+                                              uint32_t tmem, uint64_t* bars, uint32_t phase,
+                                              int warp, int lane) {
+  if (warp < 4) return true;
   const int q = warp & 3;
-  for (int i = warp >> 2; i < TILES; i += 2) {
+  for (int i = (warp >> 2) - 1; i < TILES; i += 3) {
+    if (!warp_wait(bars + i, phase, lane)) return false;
+    tc_fence_after();
     float v[32];
     tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + i * CH, v);
     const int p = i * 128 + q * 32 + lane;
@@ -194,9 +226,10 @@ __device__ __forceinline__ void epilogue_relu(unsigned char* out, const float* b
             make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
     }
   }
+  return true;
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(F_THREADS, 1)
     k_cnn_forward(const unsigned char* __restrict__ packed, const float* __restrict__ maps,
                   int B, float* __restrict__ scores, const int* __restrict__ labels,
                   unsigned char* __restrict__ save, float* __restrict__ loss, int* status) {
@@ -213,24 +246,24 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // the padding of both maps and of X0 stays zero for the whole kernel
-  for (int i = tid; i < 2 * ACT_BYTES / 16; i += THREADS)
+  for (int i = tid; i < 2 * ACT_BYTES / 16; i += F_THREADS)
     reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = tid; i < U; i += THREADS) sX[i] = 0.f;
+  for (int i = tid; i < U; i += F_THREADS) sX[i] = 0.f;
   const uint16_t* pw1 = reinterpret_cast<const uint16_t*>(packed + PK_W1);
   const uint16_t* pw2 = reinterpret_cast<const uint16_t*>(packed + PK_W2);
   const uint16_t* pw3 = reinterpret_cast<const uint16_t*>(packed + PK_W3);
   const float* pf = reinterpret_cast<const float*>(packed + PK_F32);
-  for (int i = tid; i < CH * W1_ROW; i += THREADS) {
+  for (int i = tid; i < CH * W1_ROW; i += F_THREADS) {
     const int c = i / W1_ROW, t = i % W1_ROW;
     sW1[i] = t < TAPS ? bf2f(pw1[c * TAPS + t]) : 0.f;
   }
-  for (int i = tid; i < 4 * CH + 1; i += THREADS) sBias[i] = pf[i];
-  for (int i = tid; i < CH * TAPS * CH; i += THREADS) {
+  for (int i = tid; i < 4 * CH + 1; i += F_THREADS) sBias[i] = pf[i];
+  for (int i = tid; i < CH * TAPS * CH; i += F_THREADS) {
     const int o = i / (TAPS * CH), t = (i / CH) % TAPS, c = i % CH;  // W[o][t][c]
     *reinterpret_cast<uint16_t*>(sm + F_W2 + wop_off(t, o, c)) = pw2[i];
     *reinterpret_cast<uint16_t*>(sm + F_W3 + wop_off(t, o, c)) = pw3[i];
   }
-  if (tid == 0) mbar_init(bar, 1);
+  if (tid < TILES) mbar_init(bar + tid, 1);
   if (warp == 0) tmem_alloc(slot, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
@@ -239,25 +272,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t phase = 0;
 
   // each map's energies are loaded one map ahead
-  float e_next[4] = {0.f, 0.f, 0.f, 0.f};
+  constexpr int PER = MAP * MAP / F_THREADS;  // map points per thread
+  float e_next[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) e_next[j] = 0.f;
   if (blockIdx.x < B)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      e_next[j] = maps[static_cast<size_t>(blockIdx.x) * (MAP * MAP) + tid + THREADS * j];
+    for (int j = 0; j < PER; ++j)
+      e_next[j] = maps[static_cast<size_t>(blockIdx.x) * (MAP * MAP) + tid + F_THREADS * j];
 
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     unsigned char* sv = save ? save + static_cast<size_t>(b) * SAVE_BYTES : nullptr;
     // ---- X0 = E / max E (all-zero maps stay zero; non-finite values are
     // recorded and read as zero)
-    float e[4], mx = 0.f;
+    float e[PER], mx = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) e[j] = e_next[j];
+    for (int j = 0; j < PER; ++j) e[j] = e_next[j];
     if (b + static_cast<int>(gridDim.x) < B)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        e_next[j] = maps[static_cast<size_t>(b + gridDim.x) * (MAP * MAP) + tid + THREADS * j];
+      for (int j = 0; j < PER; ++j)
+        e_next[j] = maps[static_cast<size_t>(b + gridDim.x) * (MAP * MAP) + tid + F_THREADS * j];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < PER; ++j) {
       if (!isfinite(e[j])) {
         if (status) atomicExch(status, UWB_ERR_NONFINITE);
         e[j] = 0.f;
@@ -269,54 +305,54 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) sRed[warp] = mx;
     __syncthreads();
     mx = sRed[0];
-    for (int w = 1; w < THREADS / 32; ++w) mx = fmaxf(mx, sRed[w]);
+    for (int w = 1; w < F_WARPS; ++w) mx = fmaxf(mx, sRed[w]);
     const float scale = mx > 0.f ? 1.0f / mx : 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int p = tid + THREADS * j;
+    for (int j = 0; j < PER; ++j) {
+      const int p = tid + F_THREADS * j;
       sX[pos_u(p >> 5, p & 31)] = e[j] * scale;
     }
     __syncthreads();
     if (sv) copy16(sv + SAVE_X0, sX, U * 4);
 
-    // ---- layer 1 (1 -> 32 channels) on the CUDA cores: this thread's 4
-    // positions at once, so that every weight is read once per 4 positions
+    // ---- layer 1 (1 -> 32 channels) on the CUDA cores: this thread's two
+    // positions as the lanes of paired multiply-adds (each lane the same
+    // fused multiply-adds in the same order as one position alone), so that
+    // every weight is read once per two positions
+    static_assert(PER == 2, "layer 1 pairs the thread's two positions");
     {
-      float xv[4][TAPS];
-      int uu[4];
+      float2 xv[TAPS];
+      int uu[PER];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int p = tid + THREADS * j;
+      for (int j = 0; j < PER; ++j) {
+        const int p = tid + F_THREADS * j;
         uu[j] = pos_u(p >> 5, p & 31);
-#pragma unroll
-        for (int t = 0; t < TAPS; ++t) xv[j][t] = sX[uu[j] + tap_shift(t)];
       }
+#pragma unroll
+      for (int t = 0; t < TAPS; ++t)
+        xv[t] = make_float2(sX[uu[0] + tap_shift(t)], sX[uu[1] + tap_shift(t)]);
 #pragma unroll 1
       for (int g = 0; g < 4; ++g) {
-        uint32_t w[4][4];
+        uint32_t w[PER][4];
 #pragma unroll
         for (int c2 = 0; c2 < 4; ++c2) {
-          float z[2][4];
+          float2 z[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int c = 8 * g + 2 * c2 + h;
             const float4* wr = reinterpret_cast<const float4*>(sW1 + c * W1_ROW);
             const float4 q0 = wr[0], q1 = wr[1], q2 = wr[2];
             const float wt[TAPS] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x};
-            const float bc = sBias[c];
+            float2 acc = make_float2(sBias[c], sBias[c]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              float acc = bc;
-#pragma unroll
-              for (int t = 0; t < TAPS; ++t) acc = fmaf(wt[t], xv[j][t], acc);
-              z[h][j] = fmaxf(acc, 0.f);
-            }
+            for (int t = 0; t < TAPS; ++t) acc = __ffma2_rn(make_float2(wt[t], wt[t]), xv[t], acc);
+            z[h] = make_float2(fmaxf(acc.x, 0.f), fmaxf(acc.y, 0.f));
           }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) w[j][c2] = pack2(z[0][j], z[1][j]);
+          w[0][c2] = pack2(z[0].x, z[1].x);
+          w[1][c2] = pack2(z[0].y, z[1].y);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < PER; ++j)
           *reinterpret_cast<uint4*>(act0 + act_off(uu[j], 8 * g)) =
               make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
       }
@@ -330,31 +366,40 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int l = 0; l < 2 && alive; ++l) {
       unsigned char* in = l == 0 ? act0 : act1;
       unsigned char* out = l == 0 ? act1 : act0;
-      if (tid == 0) {
+      if (warp < 4 && lane == 0) {
         tc_fence_after();
-        issue_conv(smem_u32(in), smem_u32(sm + (l == 0 ? F_W2 : F_W3)), tmem);
-        umma_commit(bar);
+        issue_conv_tiles(smem_u32(in), smem_u32(sm + (l == 0 ? F_W2 : F_W3)), tmem, bar, warp, 4);
       }
-      alive = wait_mma(bar, phase, status);
-      phase ^= 1u;
-      if (!alive) break;
-      tc_fence_after();
-      epilogue_relu(out, sBias + CH * (l + 1), tmem, warp, lane);
+      const bool ok = epilogue_relu(out, sBias + CH * (l + 1), tmem, bar, phase, warp, lane);
       tc_fence_before();
       fence_proxy_async_smem();
-      __syncthreads();
+      alive = !__syncthreads_or(!ok);
+      if (!alive) {
+        // a commit did not arrive in time: record it, give the MMAs a last
+        // bounded chance to complete (they write the TMEM freed below), stop
+        if (tid == 0) {
+          if (status) atomicExch(status, UWB_ERR_TIMEOUT);
+          for (int i = 0; i < TILES; ++i) {  // every issuing thread's last commit among them
+            uint32_t done = 0;
+            for (long it = 0; it < kProbes && !done; ++it) done = mbar_try_wait(bar + i, phase);
+          }
+        }
+        __syncthreads();
+        break;
+      }
+      phase ^= 1u;
       if (sv) copy16(sv + (l == 0 ? SAVE_A2 : SAVE_A3), out, ACT_BYTES);
     }
     if (!alive) break;
 
     // ---- segment means F[s][c] of A3 (in act0): thread = (segment s,
-    // 8-channel group g, pair of segment rows r); the 4 row pairs of a
-    // (s, g) are neighbouring lanes and are summed with shuffles
+    // 8-channel group g, segment row r); the 8 rows of a (s, g) are
+    // neighbouring lanes and are summed with shuffles
     {
-      const int r = tid & 3, g = (tid >> 2) & 3, s = tid >> 4, sy = s >> 2, sx = s & 3;
+      const int r = tid & 7, g = (tid >> 3) & 3, s = tid >> 5, sy = s >> 2, sx = s & 3;
       float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-      for (int iy = 2 * r; iy < 2 * r + 2; ++iy)
+      {
+        const int iy = r;
 #pragma unroll
         for (int ix = 0; ix < 8; ++ix) {
           const uint4 v = *reinterpret_cast<const uint4*>(
@@ -366,10 +411,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             acc[2 * k + 1] += bf2f(wv[k] >> 16);
           }
         }
+      }
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], 1);
         acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], 2);
+        acc[k] += __shfl_xor_sync(0xFFFFFFFFu, acc[k], 4);
       }
       if (r == 0)
 #pragma unroll
@@ -403,7 +450,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
     if (sv)
-      for (int i = tid; i < SEGS * CH; i += THREADS)
+      for (int i = tid; i < SEGS * CH; i += F_THREADS)
         reinterpret_cast<float*>(sv + SAVE_F)[i] = sF[(i % CH) * SEGS + i / CH];  // F[s][c]
     __syncthreads();
   }
@@ -830,7 +877,7 @@ cudaError_t launch_forward(const void* packed, const float* maps, int B, float* 
                            cudaStream_t st) {
   if (!smem_ready(reinterpret_cast<const void*>(k_cnn_forward), F_SMEM, g_fwd_attr))
     return cudaErrorInvalidValue;
-  k_cnn_forward<<<ctas, THREADS, F_SMEM, st>>>(static_cast<const unsigned char*>(packed), maps, B,
+  k_cnn_forward<<<ctas, F_THREADS, F_SMEM, st>>>(static_cast<const unsigned char*>(packed), maps, B,
                                                scores, labels, static_cast<unsigned char*>(save),
                                                loss, status);
   return cudaGetLastError();
