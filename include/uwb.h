@@ -44,11 +44,15 @@
  *    invalid, not only the scans it names. Launches that hand out tiles
  *    through a counter stop handing them out after such a timeout.
  *  - Image launches with at least 4 tiles per CTA and several CTAs per SM
- *    hand tiles out through a counter taken from a per-device pool of 64 (a
- *    counter is reused only after the launch that used it has completed).
- *    Launches captured into a CUDA graph, or made while every counter is
- *    busy, split tiles into equal contiguous ranges instead. Results do not
- *    depend on the split.
+ *    hand tiles out through a counter. uwb_localize, uwb_localize_batch,
+ *    uwb_localize_batch_noalloc, uwb_localize_host,
+ *    uwb_localize_multistatic_batch and the plan calls own their counters in
+ *    their workspace and zero them themselves, so their launches split
+ *    dynamically in a CUDA graph too. The other entry points take a counter
+ *    from a per-device pool of 64 (reused only after the launch that used it
+ *    has completed); launched under stream capture, or while every counter
+ *    is busy, they split tiles into equal contiguous ranges instead. Results
+ *    do not depend on the split.
  */
 #ifndef UWB_H
 #define UWB_H

@@ -483,11 +483,20 @@ int take_counter(Device& dev, cudaStream_t st) {
 // else with the static split. The counter evens out CTAs that share an SM;
 // with one CTA per SM (per_sm == 1, the multistatic instances) the static
 // split measured 2-4 % faster. Tile counts near 2^31 keep the static split.
+// A call that owns a counter in its workspace (own_ctr, zeroed on the
+// launch's stream before the launch) uses it instead of the pool: then a
+// launch captured into a CUDA graph keeps the dynamic split, since every
+// replay zeroes the counter again.
 cudaError_t launch_balanced(Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
                             int ctas, int per_sm, size_t smem, long long work_bound,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* own_ctr = nullptr) {
+  const bool balance = per_sm >= 2 && work_bound < (1LL << 30);
+  if (own_ctr) {
+    p.work = balance ? own_ctr : nullptr;
+    return launch(var, p, map, ctas, smem, st);
+  }
   std::lock_guard<std::mutex> lk(dev.counter_mu);
-  const int slot = (per_sm >= 2 && work_bound < (1LL << 30)) ? take_counter(dev, st) : -1;
+  const int slot = balance ? take_counter(dev, st) : -1;
   p.work = nullptr;
   if (slot >= 0) {
     const cudaError_t e = cudaMemsetAsync(dev.counters + slot, 0, sizeof(int), st);
@@ -501,7 +510,8 @@ cudaError_t launch_balanced(Device& dev, const Variant& var, ImgParams& p, const
 }
 
 int run_image_kernel(Device& dev, const Variant& var, ImgParams& p, const CUtensorMap* map,
-                     long long work_bound, const double step[3], cudaStream_t st) {
+                     long long work_bound, const double step[3], cudaStream_t st,
+                     int* own_ctr = nullptr) {
   double delta[3];
   for (int a = 0; a < 3; ++a) delta[a] = step[a] * p.pit[a] * p.kscale;
   if (p.gn[2] == 1) delta[2] = 1e9;  // keep warps flat in 2-D
@@ -513,8 +523,8 @@ int run_image_kernel(Device& dev, const Variant& var, ImgParams& p, const CUtens
   long long ctas = static_cast<long long>(dev.sms) * occ;
   if (work_bound < ctas) ctas = work_bound;
   if (ctas < 1) return UWB_OK;
-  cudaError_t e =
-      launch_balanced(dev, var, p, map, static_cast<int>(ctas), occ, smem, work_bound, st);
+  cudaError_t e = launch_balanced(dev, var, p, map, static_cast<int>(ctas), occ, smem,
+                                  work_bound, st, own_ctr);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }
@@ -641,8 +651,11 @@ Decim decimate(const uwb_grid& g, const uwb_rule& r) {
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct WsLayout {
-  size_t keys, status, profile, boxes, prefix, total;
+  size_t keys, status, counters, profile, boxes, prefix, total;
 };
+
+// Tile counters a localisation owns in its workspace: one per image pass.
+constexpr int kWsCounters = 2;
 
 WsLayout ws_layout(int B, long long Pd) {
   WsLayout w;
@@ -650,7 +663,8 @@ WsLayout ws_layout(int B, long long Pd) {
   w.keys = off;
   off += static_cast<size_t>(B) * 8;       // argmax keys ...
   w.status = off;                           // ... followed by the status word
-  off = align256(off + 4);
+  w.counters = off + 4;                     // and the passes' tile counters
+  off = align256(off + 4 + 4 * kWsCounters);
   w.profile = off;
   off += align256(static_cast<size_t>(B) * static_cast<size_t>(Pd) * 4);
   w.boxes = off;
@@ -712,8 +726,10 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
   auto* profile = reinterpret_cast<float*>(ws + wl.profile);
   auto* boxes = reinterpret_cast<LatBox*>(ws + wl.boxes);
   auto* prefix = reinterpret_cast<int*>(ws + wl.prefix);
+  auto* counters = reinterpret_cast<int*>(ws + wl.counters);
 
-  cudaError_t e = cudaMemsetAsync(ws + wl.keys, 0, wl.status + 4 - wl.keys, cs);
+  // keys, status word and tile counters start at zero
+  cudaError_t e = cudaMemsetAsync(ws + wl.keys, 0, wl.counters + 4 * kWsCounters - wl.keys, cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
 
   const int span = pick_span(var, M);
@@ -736,7 +752,8 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
   const double dstep[3] = {static_cast<double>(dc.step[0]), static_cast<double>(dc.step[1]),
                            static_cast<double>(dc.step[2])};
   if ((st = run_image_kernel(*dev, var, p1, &map,
-                             static_cast<long long>(batch) * p1.uni.tiles, dstep, cs)))
+                             static_cast<long long>(batch) * p1.uni.tiles, dstep, cs,
+                             counters)))
     return st;
 
   timer.mark();
@@ -776,7 +793,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
   const double step1[3] = {1, 1, 1};
   if ((st = run_image_kernel(*dev, var, p2, &map,
                              static_cast<long long>(batch) * lattice_tiles(full_cnt, var.tdim), step1,
-                             cs)))
+                             cs, counters + 1)))
     return st;
 
   timer.mark();
@@ -885,7 +902,7 @@ int host_checks(int batch, const float* traces, int M, int N, const float* ant,
 
 struct PlanLayout {
   size_t descs, maps, pboxes, pprefix, fboxes, fprefix, sel, fin;  // written at upload
-  size_t keys, status, profiles, rboxes, rprefix;                   // scratch of a run
+  size_t keys, status, counters, profiles, rboxes, rprefix;         // scratch of a run
   size_t total;
 };
 
@@ -934,8 +951,9 @@ PlanLayout plan_layout(const uwb_plan& pl) {
   L.fprefix = take((B + 1) * 4, 256);
   L.sel = take(B * sizeof(SelScan), 256);
   L.fin = take(B * sizeof(FinScan), 256);
-  L.keys = take(B * 8 + 4, 256);  // keys, then the status word
+  L.keys = take(B * 8 + 4 + 4 * kWsCounters, 256);  // keys, the status word, tile counters
   L.status = L.keys + B * 8;
+  L.counters = L.status + 4;
   L.profiles = take(static_cast<size_t>(pl.prof_total) * 4, 256);
   L.rboxes = take(B * sizeof(LatBox), 256);
   L.rprefix = take((B + 1) * 4, 256);
@@ -963,7 +981,7 @@ ImgParams plan_params(const uwb_plan& pl, int* status) {
 }
 
 int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const int wdim[3],
-                cudaStream_t cs) {
+                cudaStream_t cs, int* own_ctr) {
   Device* dev;
   int st = device(&dev);
   if (st) return st;
@@ -980,8 +998,8 @@ int plan_launch(const uwb_plan& pl, ImgParams& p, long long work_bound, const in
   if (ctas < 1) return UWB_OK;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);
-  cudaError_t e =
-      launch_balanced(*dev, pl.var, p, &dummy, static_cast<int>(ctas), occ, smem, work_bound, cs);
+  cudaError_t e = launch_balanced(*dev, pl.var, p, &dummy, static_cast<int>(ctas), occ, smem,
+                                  work_bound, cs, own_ctr);
   if (e != cudaSuccess) return cuda_fail(e, "image kernel launch");
   return UWB_OK;
 }
@@ -1411,7 +1429,9 @@ int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* 
   if (!images) return fail(UWB_ERR_ARG, "null images");
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   int* status = reinterpret_cast<int*>(plan->ws + plan->lay.status);
-  cudaError_t e = cudaMemsetAsync(status, 0, 4, cs);
+  int* counters = reinterpret_cast<int*>(plan->ws + plan->lay.counters);
+  // the status word and the tile counters start at zero
+  cudaError_t e = cudaMemsetAsync(status, 0, 4 + 4 * kWsCounters, cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   if (peak_index) {
     e = cudaMemsetAsync(peak_index, 0, sizeof(long long) * plan->B, cs);
@@ -1422,7 +1442,7 @@ int uwb_plan_images(uwb_plan* plan, float* images, long long* peak_index, void* 
   p.prefix = reinterpret_cast<const int*>(plan->ws + plan->lay.fprefix);
   p.image = images;
   p.keys = reinterpret_cast<unsigned long long*>(peak_index);
-  int st = plan_launch(*plan, p, plan->fprefix[plan->B], plan->wdim_full, cs);
+  int st = plan_launch(*plan, p, plan->fprefix[plan->B], plan->wdim_full, cs, counters);
   if (st) return st;
   if (peak_index) {
     e = launch_keys_to_index(p.keys, plan->B, cs);
@@ -1442,7 +1462,10 @@ int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream) {
   auto* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);
   auto* rboxes = reinterpret_cast<LatBox*>(ws + L.rboxes);
   auto* rprefix = reinterpret_cast<int*>(ws + L.rprefix);
-  cudaError_t e = cudaMemsetAsync(ws + L.keys, 0, static_cast<size_t>(B) * 8 + 4, cs);
+  int* counters = reinterpret_cast<int*>(ws + L.counters);
+  // keys, status word and tile counters start at zero
+  cudaError_t e =
+      cudaMemsetAsync(ws + L.keys, 0, static_cast<size_t>(B) * 8 + 4 + 4 * kWsCounters, cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   PhaseTimer timer(cs);
   timer.mark();
@@ -1451,7 +1474,7 @@ int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream) {
   p1.boxes = reinterpret_cast<const LatBox*>(ws + L.pboxes);
   p1.prefix = reinterpret_cast<const int*>(ws + L.pprefix);
   p1.compact = reinterpret_cast<float*>(ws + L.profiles);
-  int st = plan_launch(*plan, p1, plan->pprefix[B], plan->wdim_dec, cs);
+  int st = plan_launch(*plan, p1, plan->pprefix[B], plan->wdim_dec, cs, counters);
   if (st) return st;
   timer.mark();
   // 2. selection (per-scan lattices) and work planning
@@ -1473,7 +1496,8 @@ int uwb_plan_localize(uwb_plan* plan, uwb_result* out, void* stream) {
   p2.boxes = rboxes;
   p2.prefix = rprefix;
   p2.keys = keys;
-  if ((st = plan_launch(*plan, p2, plan->fprefix[B], plan->wdim_full, cs))) return st;
+  if ((st = plan_launch(*plan, p2, plan->fprefix[B], plan->wdim_full, cs, counters + 1)))
+    return st;
   timer.mark();
   FinishParams fp;
   memset(&fp, 0, sizeof fp);

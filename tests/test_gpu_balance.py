@@ -2,11 +2,14 @@
 oracle (needs a GB300).
 
 With a tile counter the persistent CTAs take chunks of tiles as they free up;
-without one (under stream capture, or with every counter busy) each CTA takes
-an equal contiguous range. Only the order in which tiles are evaluated
-differs, so images, argmaxes and localisations must be byte-identical. The
-launches here have at least 16 tiles per CTA (the kernel splits dynamically
-from 4) and run several CTAs per SM."""
+without one each CTA takes an equal contiguous range. The image entry points
+take their counter from a per-device pool, so under stream capture (or with
+every counter busy) they split statically; the localisation entry points own
+their counters in the workspace, zeroed by the call itself, so a graph replay
+splits dynamically too. Only the order in which tiles are evaluated differs,
+so images, argmaxes and localisations must be byte-identical. The launches
+here have at least 16 tiles per CTA (the kernel splits dynamically from 4)
+and run several CTAs per SM."""
 import numpy as np
 import pytest
 import torch
@@ -18,15 +21,16 @@ from parity import BF_ORACLE, IMG_TOL, dev, rule_pair
 pytestmark = pytest.mark.gpu
 
 
-def _captured(fn):
-    """fn(stream) captured into a CUDA graph and replayed once: while a stream
-    is captured the library takes no tile counter, so every image launch in
-    fn splits its tiles statically."""
+def _captured(fn, replays=1):
+    """fn(stream) captured into a CUDA graph and replayed: while a stream is
+    captured the library takes no counter from its pool, so the image entry
+    points split their tiles statically there."""
     s = torch.cuda.Stream()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=s):
         fn(s)
-    graph.replay()
+    for _ in range(replays):
+        graph.replay()
     torch.cuda.synchronize()
 
 
@@ -60,9 +64,10 @@ def test_dynamic_split_images_equal_the_static_split(gpu, bf):
     assert np.max(np.abs(got - ref)) <= IMG_TOL * float(last.max())
 
 
-def test_dynamic_split_localisation_equals_the_static_split(gpu):
+def test_graph_replayed_localisation_keeps_the_dynamic_split(gpu):
     # 64 scans: the final regions hold about 13k tiles of 128 points, split
-    # dynamically over 608 CTAs when run eagerly
+    # dynamically over 608 CTAs through the workspace's counters, eagerly and
+    # in each of three replays of a captured graph (each replay zeroes them)
     cfg = phantom.CONFIGS["dmas2d_512"]
     batch = phantom.make_batch(cfg, 64, first_scan=80)
     grid = cfg.grid()
@@ -80,7 +85,7 @@ def test_dynamic_split_localisation_equals_the_static_split(gpu):
     assert tiles >= 16 * 608
     out_s = torch.zeros_like(out_d)
     _captured(lambda s: gpu.uwb_localize_batch(tr, ants, grid, cfg.v, cfg.fs, cfg.window, 2,
-                                               g_rule, ws, out_s, stream=s))
+                                               g_rule, ws, out_s, stream=s), replays=3)
     assert torch.equal(out_d, out_s)
 
 
