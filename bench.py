@@ -85,9 +85,9 @@ def peak_source(kind: str) -> str:
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "e5861a37dd6ad9cb", "bytes_per_scan": 9012736 / 256},
-    1: {"sha": "e5861a37dd6ad9cb", "bytes_per_scan": 9406464 / 256},
-    2: {"sha": "e5861a37dd6ad9cb", "bytes_per_scan": 6732288 / 256},
+    0: {"sha": "18b3a638c44cd4cb", "bytes_per_scan": 9011712 / 256},
+    1: {"sha": "18b3a638c44cd4cb", "bytes_per_scan": 9327360 / 256},
+    2: {"sha": "18b3a638c44cd4cb", "bytes_per_scan": 6724608 / 256},
 }
 
 
