@@ -1,9 +1,10 @@
 // Device-resident segment search (Section III, "ROI Selection"): one warp per
 // scan runs the whole coarse-to-fine loop on the decimated energy profile --
-// quadrant/octant split, per-child mean and variance in float64, the Eq. 5
-// decision metric, sliding framing of the chosen child, and the Eq. 6-7
-// stopping rule -- then writes the final region as a lattice box for the
-// full-resolution pass. No host round trip between steps.
+// quadrant/octant split, per-child mean and variance (compensated float32
+// sums finished in float64), the Eq. 5 decision metric, sliding framing of
+// the chosen child, and the Eq. 6-7 stopping rule -- then writes the final
+// region as a lattice box for the full-resolution pass. No host round trip
+// between steps.
 //
 // Readings where the paper is silent or inconsistent (the same ones the
 // float64 reference implementation takes):
@@ -75,6 +76,68 @@ __device__ __forceinline__ void for_box_points(const KBox& b, int start, int str
   }
 }
 
+// Normalisation by 1 / m (m = the profile maximum) in two parts, so that the
+// work per lattice point stays in float32 (float64 is this GPU's slow path,
+// about two lanes per clock per SM): e = I * 2^k exactly (m 2^k in [0.5, 1),
+// applied as two float32 power-of-two factors), sums of e and e^2 carried as
+// compensated float32 pairs, and the finished sums scaled by r = 2^-k / m in
+// float64. Energies below 2^-126 of the maximum underflow in e^2; they add
+// less than 1e-37 of the sums.
+struct Norm {
+  float sa, sb;
+  double r;
+};
+
+__device__ __forceinline__ Norm make_norm(float m) {
+  int ex;
+  frexpf(m, &ex);  // m = f 2^ex, f in [0.5, 1); ex in [-148, 128]
+  const int k = -ex, k1 = k / 2, k2 = k - k1;
+  Norm n;
+  n.sa = __int_as_float((k1 + 127) << 23);
+  n.sb = __int_as_float((k2 + 127) << 23);
+  n.r = ldexp(1.0 / static_cast<double>(m), -k);
+  return n;
+}
+
+// A float32 sum carried with its rounding error (hi + lo; Knuth's two-sum
+// recovers each addition's error exactly): about 48 significant bits.
+struct Acc2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bv = s - a;
+  return (a - (s - bv)) + (b - bv);
+}
+
+__device__ __forceinline__ void acc_add(Acc2& a, float b) {
+  const float s = a.hi + b;
+  a.lo += two_sum_err(a.hi, b, s);
+  a.hi = s;
+}
+
+// e^2 as the product and its exact error (a fused multiply-add)
+__device__ __forceinline__ void acc_sq(Acc2& a, float e) {
+  const float p = e * e;
+  acc_add(a, p);
+  a.lo += fmaf(e, e, -p);
+}
+
+// Symmetric in its operands (the two-sum error is exact either way), so the
+// lanes of a butterfly reduction end with the same value.
+__device__ __forceinline__ Acc2 acc_merge(const Acc2& a, const Acc2& b) {
+  const float s = a.hi + b.hi;
+  return Acc2{s, (a.lo + b.lo) + two_sum_err(a.hi, b.hi, s)};
+}
+
+__device__ __forceinline__ Acc2 acc_shfl_xor(const Acc2& a, int o) {
+  return Acc2{__shfl_xor_sync(0xFFFFFFFFu, a.hi, o), __shfl_xor_sync(0xFFFFFFFFu, a.lo, o)};
+}
+
+__device__ __forceinline__ double acc_value(const Acc2& a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+
 struct Stats {
   long long n;
   // of the normalised energies; scatter = sum of squared deviations,
@@ -82,43 +145,42 @@ struct Stats {
   double sum, mean, scatter, var;
 };
 
-// Lane-partial sum and sum of squares of the raw energies of the decimated
-// points inside a box (one pass, float64).
+// Lane-partial sums of e and e^2 (e = I 2^k, see Norm) over the decimated
+// points j = start, start + stride, ... of a box (one pass).
 __device__ __forceinline__ void lane_sums(const SelScan& P, const float* prof, const KBox& b,
-                                          double& s1, double& s2) {
-  const int lane = threadIdx.x & 31;
-  double a1 = 0.0, a2 = 0.0;
-  for_box_points(b, lane, 32, [&](int kx, int ky, int kz) {
-    const double v = static_cast<double>(prof[kx + P.cnt[0] * (ky + P.cnt[1] * kz)]);
-    a1 += v;
-    a2 = fma(v, v, a2);
+                                          const Norm& nm, int start, int stride, Acc2& a1,
+                                          Acc2& a2) {
+  a1 = Acc2{0.f, 0.f};
+  a2 = Acc2{0.f, 0.f};
+  for_box_points(b, start, stride, [&](int kx, int ky, int kz) {
+    const float e = (prof[kx + P.cnt[0] * (ky + P.cnt[1] * kz)] * nm.sa) * nm.sb;
+    acc_add(a1, e);
+    acc_sq(a2, e);
   });
-  s1 = a1;
-  s2 = a2;
 }
 
-// Statistics of the normalised energies e = I * inv (inv = 1 / the profile
-// maximum) inside a box: count, sum, mean, scatter (sum of squared
-// deviations, as sum e^2 - (sum e) mean; the energies are non-negative and
-// bounded, so float64 keeps ~14 digits even for nearly flat segments) and
-// variance. float64 is this GPU's slow path (about two lanes per clock per
-// SM): one pass, and one division (1 / n) per box.
-__device__ Stats box_stats(const SelScan& P, const float* prof, double inv, const KBox& b) {
+// Statistics of the normalised energies I / m (m = the profile maximum)
+// inside a box: count, sum, mean, scatter (sum of squared deviations, as
+// sum e^2 - (sum e) mean; the energies are non-negative and bounded, and the
+// sums carry about 48 significant bits, so even nearly flat segments keep
+// ~14 digits) and variance, finished in float64: one pass, and one division
+// (1 / n) per box.
+__device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, const KBox& b) {
   Stats st;
   st.n = b.n;
   st.sum = st.mean = st.scatter = st.var = 0.0;
   if (b.n == 0) return st;
-  double s1, s2;
-  lane_sums(P, prof, b, s1, s2);
+  Acc2 a1, a2;
+  lane_sums(P, prof, b, nm, threadIdx.x & 31, 32, a1, a2);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+    a1 = acc_merge(a1, acc_shfl_xor(a1, o));
+    a2 = acc_merge(a2, acc_shfl_xor(a2, o));
   }
   const double rn = 1.0 / static_cast<double>(b.n);
-  st.sum = s1 * inv;
+  st.sum = acc_value(a1) * nm.r;
   st.mean = st.sum * rn;
-  st.scatter = fmax(s2 * inv * inv - st.sum * st.mean, 0.0);
+  st.scatter = fmax(acc_value(a2) * nm.r * nm.r - st.sum * st.mean, 0.0);
   st.var = st.scatter * rn;
   return st;
 }
@@ -148,7 +210,8 @@ struct Choice {
   int blo[3], bhi[3];
 };
 
-__device__ Choice choose_child(const SelScan& Q, const float* vals, double inv, const int Rlo[3],
+__device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& nm,
+                               const int Rlo[3],
                                const int Rhi[3], int dim, const uwb_rule& rule,
                                double var_prev) {
   const int lane = threadIdx.x & 31;
@@ -172,25 +235,19 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, double inv, 
   }
   const KBox kb = lattice_in_box(Q, clo, chi);
   // this group's partial sums over child c
-  double s1 = 0.0, s2 = 0.0;
-  if (ok) {
-    for_box_points(kb, r, G, [&](int kx, int ky, int kz) {
-      const double v = static_cast<double>(vals[kx + Q.cnt[0] * (ky + Q.cnt[1] * kz)]);
-      s1 += v;
-      s2 = fma(v, v, s2);
-    });
-  }
+  Acc2 a1{0.f, 0.f}, a2{0.f, 0.f};
+  if (ok) lane_sums(Q, vals, kb, nm, r, G, a1, a2);
   for (int o = G >> 1; o > 0; o >>= 1) {
-    s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-    s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+    a1 = acc_merge(a1, acc_shfl_xor(a1, o));
+    a2 = acc_merge(a2, acc_shfl_xor(a2, o));
   }
   double m = 0.0;
   const bool valid = ok && kb.n > 0;
   if (valid) {
     const double rn = 1.0 / static_cast<double>(kb.n);
-    const double sum = s1 * inv;
+    const double sum = acc_value(a1) * nm.r;
     const double mean = sum * rn;
-    const double scatter = fmax(s2 * inv * inv - sum * mean, 0.0);
+    const double scatter = fmax(acc_value(a2) * nm.r * nm.r - sum * mean, 0.0);
     m = decision_metric(rule.metric, mean, scatter * rn, var_prev);
   }
   Choice ch;
@@ -291,19 +348,19 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     }
     return;
   }
-  const double inv = 1.0 / static_cast<double>(fmx);
+  const Norm nm = make_norm(fmx);
   const int dim = P.dim;
   const uwb_rule& rule = P.rule;
 
   int Rlo[3] = {0, 0, 0}, Rhi[3] = {Q.gn[0], Q.gn[1], Q.gn[2]};
-  Stats sa = box_stats(Q, prof, inv, lattice_in_box(Q, Rlo, Rhi));
+  Stats sa = box_stats(Q, prof, nm, lattice_in_box(Q, Rlo, Rhi));
   double var_prev = sa.var;
   double B_prev = 0.0, W_prev = 0.0;
   int iters = 0, n_logged = 0, stop = UWB_STOP_NONE;
 
   for (int i = 1; i <= Q.max_iters; ++i) {
     const int li = i - 1;
-    const Choice ch = choose_child(Q, prof, inv, Rlo, Rhi, dim, rule, var_prev);
+    const Choice ch = choose_child(Q, prof, nm, Rlo, Rhi, dim, rule, var_prev);
     const int best = ch.best, nvalid = ch.nvalid;
     const double best_m = ch.best_m, second_m = ch.second_m;
     int blo[3], bhi[3];
@@ -332,7 +389,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       }
     }
     // Eq. 6-7 between the regions of consecutive iterations
-    const Stats sb = box_stats(Q, prof, inv, lattice_in_box(Q, Nlo, Nhi));
+    const Stats sb = box_stats(Q, prof, nm, lattice_in_box(Q, Nlo, Nhi));
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
@@ -500,7 +557,7 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
     return;
   }
   const uwb_rule& rule = P.rule;
-  const double inv = 1.0 / static_cast<double>(S->pmax);
+  const Norm nm = make_norm(S->pmax);
   int Rlo[3], Rhi[3];
   for (int a = 0; a < 3; ++a) {
     Rlo[a] = S->Rlo[a];
@@ -528,9 +585,9 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       return;
     }
   }
-  const Stats sr = box_stats(Qc, cv, inv, lattice_in_box(Qc, Rlo, Rhi));
+  const Stats sr = box_stats(Qc, cv, nm, lattice_in_box(Qc, Rlo, Rhi));
   const double var_prev = sr.var;
-  const Choice ch = choose_child(Qc, cv, inv, Rlo, Rhi, dim, rule, var_prev);
+  const Choice ch = choose_child(Qc, cv, nm, Rlo, Rhi, dim, rule, var_prev);
   const int best = ch.best, nvalid = ch.nvalid;
   const double best_m = ch.best_m, second_m = ch.second_m;
   int blo[3], bhi[3];
@@ -561,8 +618,8 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       }
     }
     // Eq. 6-7 on the decimated profile between the region and the framed child
-    const Stats sa = box_stats(Q0, prof, inv, lattice_in_box(Q0, Rlo, Rhi));
-    const Stats sb = box_stats(Q0, prof, inv, lattice_in_box(Q0, Nlo, Nhi));
+    const Stats sa = box_stats(Q0, prof, nm, lattice_in_box(Q0, Rlo, Rhi));
+    const Stats sb = box_stats(Q0, prof, nm, lattice_in_box(Q0, Nlo, Nhi));
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
