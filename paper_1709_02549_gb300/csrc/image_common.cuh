@@ -1053,13 +1053,34 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
 #pragma unroll
     for (int q = 0; q < PP; ++q) {
       if (linear) {
-        // point t * (T * PP) + tid + q * T of the box, x fastest
+        // point t * (T * PP) + tid + q * T of the box
         const int idx = static_cast<int>(t) * (T * PP) + tid + q * T;
-        kz[q] = idx / cxy;
-        const int r = idx - kz[q] * cxy;
-        ky[q] = r / L.cnt[0];
-        kx[q] = r - ky[q] * L.cnt[0];
-        valid[q] = kz[q] < L.cnt[2];
+        if (P.strip > 1 && L.cnt[2] == 1) {
+          // 2-D boxes with steep delays: strips of S rows numbered column by
+          // column, so that a warp's 32 points form a block of 32 / S columns
+          // by S rows whose delays span fewer than 32 samples (no two lanes
+          // read words 32 apart: no shared-memory bank conflicts)
+          const int S = P.strip;
+          kz[q] = 0;
+          valid[q] = idx < cxy;
+          if (valid[q]) {
+            const int sc = S * L.cnt[0];
+            const int j = idx / sc;
+            const int r = idx - j * sc;
+            const int h = min(S, L.cnt[1] - S * j);
+            kx[q] = r / h;
+            ky[q] = S * j + (r - kx[q] * h);
+          } else {
+            kx[q] = ky[q] = 0;
+          }
+        } else {
+          // x fastest
+          kz[q] = idx / cxy;
+          const int r = idx - kz[q] * cxy;
+          ky[q] = r / L.cnt[0];
+          kx[q] = r - ky[q] * L.cnt[0];
+          valid[q] = kz[q] < L.cnt[2];
+        }
       } else {
         kx[q] = tix * P.tdim[0] + lx[q];
         ky[q] = tiy * P.tdim[1] + ly[q];

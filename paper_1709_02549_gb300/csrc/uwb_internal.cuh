@@ -86,6 +86,9 @@ struct ImgParams {
   const LatBox* boxes;       // per-scan lattices (device) or nullptr
   const int* prefix;         // [B+1] exclusive tile prefix when boxes != nullptr
   int tdim[3];               // tile shape, or {P, 0, 0} for linear tiles (tile_linear)
+  int strip;                 // linear tiles of a 2-D box: > 1 = points numbered in strips
+                             // of `strip` rows (column by column inside a strip), else
+                             // row by row
   int wdim[3];               // warp sub-block extent of shaped tiles (product 32)
   int span;                  // samples staged per antenna (multiple of 4)
   int wpad;                  // window samples a thread may read (>= W, chunk multiple)
