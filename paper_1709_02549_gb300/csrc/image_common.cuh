@@ -70,7 +70,8 @@ struct KernelShape {
   // literal DMAS: 4 resident CTAs (<= 128 registers) up to 32 antennas, 2
   // for the 64-antenna block, 3 for the 96-antenna block form (no delay table).
   // Monostatic point pairs: DAS 4 and identity DMAS 3, where the paired
-  // window accumulators fit registers; ragged (one point per thread): DAS 3,
+  // window accumulators fit registers (twice as many when the host launches
+  // them with 64 threads, for few trace rows); ragged (one point per thread): DAS 3,
   // identity DMAS 2. Multistatic: one CTA per SM (its channel window takes
   // most of the shared memory), 256 threads of two points.
   static constexpr int min_blocks =

@@ -225,6 +225,9 @@ bool tile_ok(int bf, const int t[3]) {
   return t[0] * t[1] * t[2] == points;
 }
 
+int var_points(const Variant& v);
+int pick_span(const Variant& var, int M, int dtype = DT_F32);
+
 int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
   Variant var;
   var.bf = bf;
@@ -251,8 +254,9 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     // chunks of 16 (two focal points per thread) or 32 (multistatic)
     var.v = W <= 4 ? 4 : W <= 8 ? 8 : W <= 16 ? 16 : W <= 20 ? 20 : (var.ms ? 32 : 16);
     var.wpad = (W + var.v - 1) / var.v * var.v;
-    // uniform monostatic: 128 threads of two focal points each; multistatic
-    // (and ragged plans, see use_ragged_shape): 256 threads of one
+    // uniform monostatic: 128 threads of two focal points each (64 for few
+    // trace rows, below); multistatic: 256 threads of two; ragged plans (see
+    // use_ragged_shape): 256 threads of one
     var.threads = var.ms ? 256 : 128;
     var.rows = var.R;
     // window budget per CTA: the CTAs per SM of the launch shape share the
@@ -268,18 +272,32 @@ int pick_variant(int bf, int M, int W, int dim, Variant* out, int R = -1) {
     if (t[0] && (dim == 3 || t[2] == 1))
       for (int a = 0; a < 3; ++a) var.tdim[a] = t[a];
   }
+  if (!var.ms && bf != BF_DMAS_LIT && tile_linear(var.tdim)) {
+    // Few trace rows: CTAs of 64 threads (128-point tiles), twice as many per
+    // SM, wherever half the shared-memory budget stages the same span. On
+    // small final regions (a few hundred points per scan) each CTA spends a
+    // good part of its time waiting on its own staging, tile grabs and
+    // per-scan reductions; with more, smaller CTAs per SM those waits overlap
+    // the other CTAs' tiles. The kernel takes its CTA size from the launch.
+    Variant half = var;
+    half.threads = 64;
+    half.tdim[0] = 128;
+    half.smem_budget = (bf == BF_DAS ? 27 : 37) * 1024;
+    if (pick_span(half, M) == pick_span(var, M)) var = half;
+  }
   *out = var;
   return UWB_OK;
 }
 
 // The coarse DAS maps of the learned proposal: 32 x 32 lattices with steps of
-// 4 to 16 grid points. Shaped 32 x 8 tiles divide them exactly and keep each
-// warp's delay samples compact (fewer shared-memory bank conflicts than rows
-// of 32 points), so they are used unless a shape was set for 2-D DAS.
+// 4 to 16 grid points. Shaped tiles 32 wide (8 rows, or 4 for CTAs of 64
+// threads) divide them exactly and keep each warp's delay samples compact
+// (fewer shared-memory bank conflicts than rows of 32 points), so they are
+// used unless a shape was set for 2-D DAS.
 int pick_map_variant(int M, int window, Variant* vm) {
   const int st = pick_variant(BF_DAS, M, window, 2, vm);
   if (st == UWB_OK && tile_linear(vm->tdim)) {
-    vm->tdim[0] = 32; vm->tdim[1] = 8; vm->tdim[2] = 1;
+    vm->tdim[0] = 32; vm->tdim[1] = var_points(*vm) / 32; vm->tdim[2] = 1;
   }
   return st;
 }
@@ -296,6 +314,7 @@ void use_ragged_shape(Variant* var) {
   var->rg = true;
   if (var->bf != BF_DMAS_LIT) {
     var->threads = 256;
+    if (tile_linear(var->tdim)) var->tdim[0] = 256;  // one point per thread
     // those run 3 (DAS) or 2 (identity DMAS) CTAs per SM, each with the 1 KB
     // the runtime reserves: the rest of the SM's 228 KB sizes the staged span
     // of their (up to 96-row) windows
@@ -326,7 +345,7 @@ void pick_warp(const int tdim[3], const double delta[3], int wdim[3]) {
 
 // Samples staged per antenna: what the variant's shared-memory budget allows,
 // at most one TMA box width (256), at least the window plus a margin.
-int pick_span(const Variant& var, int M, int dtype = DT_F32) {
+int pick_span(const Variant& var, int M, int dtype) {
   // the largest span (a multiple of 8: 16-byte TMA rows for 16-bit traces too)
   // whose whole layout fits the budget
   int span = 256;
