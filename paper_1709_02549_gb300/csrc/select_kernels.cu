@@ -1,5 +1,6 @@
-// Device-resident segment search (Section III, "ROI Selection"): one warp per
-// scan runs the whole coarse-to-fine loop on the decimated energy profile --
+// Device-resident segment search (Section III, "ROI Selection"): one warp (or,
+// for large batches of small profiles, a quarter warp) per scan runs the
+// whole coarse-to-fine loop on the decimated energy profile --
 // quadrant/octant split, per-child mean and variance (compensated float32
 // sums finished in float64), the Eq. 5 decision metric, sliding framing of
 // the chosen child, and the Eq. 6-7 stopping rule -- then writes the final
@@ -164,19 +165,22 @@ __device__ __forceinline__ void lane_sums(const SelScan& P, const float* prof, c
 // sum e^2 - (sum e) mean; the energies are non-negative and bounded, and the
 // sums carry about 48 significant bits, so even nearly flat segments keep
 // ~14 digits) and variance, finished in float64: one pass, and one division
-// (1 / n) per box.
-__device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, const KBox& b) {
+// (1 / n) per box. The SW lanes of the scan's sub-warp (sl = lane in it)
+// share the points; every lane of the warp takes part in the shuffles.
+template <int SW>
+__device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, const KBox& b,
+                           int sl) {
   Stats st;
   st.n = b.n;
   st.sum = st.mean = st.scatter = st.var = 0.0;
-  if (b.n == 0) return st;
   Acc2 a1, a2;
-  lane_sums(P, prof, b, nm, threadIdx.x & 31, 32, a1, a2);
+  lane_sums(P, prof, b, nm, sl, SW, a1, a2);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = SW / 2; o > 0; o >>= 1) {
     a1 = acc_merge(a1, acc_shfl_xor(a1, o));
     a2 = acc_merge(a2, acc_shfl_xor(a2, o));
   }
+  if (b.n == 0) return st;
   const double rn = 1.0 / static_cast<double>(b.n);
   st.sum = acc_value(a1) * nm.r;
   st.mean = st.sum * rn;
@@ -184,6 +188,11 @@ __device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, 
   st.var = st.scatter * rn;
   return st;
 }
+
+// Batches of at least this many scans, with at most this many decimated
+// points per scan, select with four scans per warp.
+constexpr int kSelectPackedMinScans = 2048;
+constexpr long long kSelectPackedMaxPoints = 4096;
 
 __device__ __forceinline__ double rel_gap(double hi, double lo) {
   const double d = fmax(fabs(hi), fabs(lo));
@@ -200,8 +209,9 @@ __device__ double decision_metric(int metric, double mu, double var, double var_
 }
 
 // Child choice of one iteration (Eq. 5 over the 2^dim children of the region
-// [Rlo, Rhi)), all children at once: lane group c = lane / G (G = 32 / 2^dim
-// lanes) sums child c's lattice points, the group's sums are reduced within
+// [Rlo, Rhi)), all children at once: lane group c = sl / G of the scan's
+// sub-warp (G = SW / 2^dim lanes, sl = lane in the sub-warp, base = its first
+// lane) sums child c's lattice points, the group's sums are reduced within
 // the group, and every lane then runs the choice over the children in index
 // order (first maximum wins; the runner-up is kept for the margin).
 struct Choice {
@@ -210,14 +220,13 @@ struct Choice {
   int blo[3], bhi[3];
 };
 
+template <int SW>
 __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& nm,
-                               const int Rlo[3],
-                               const int Rhi[3], int dim, const uwb_rule& rule,
-                               double var_prev) {
-  const int lane = threadIdx.x & 31;
+                               const int Rlo[3], const int Rhi[3], int dim,
+                               const uwb_rule& rule, double var_prev, int sl, int base) {
   const int nchild = 1 << dim;
-  const int G = 32 / nchild;
-  const int c = lane / G, r = lane % G;
+  const int G = SW / nchild;
+  const int c = sl / G, r = sl % G;
   int mid[3], clo[3], chi[3];
   bool ok = true;
 #pragma unroll
@@ -256,8 +265,8 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& 
   ch.best_m = ch.second_m = 0.0;
   for (int a = 0; a < 3; ++a) ch.blo[a] = ch.bhi[a] = 0;
   for (int cc = 0; cc < nchild; ++cc) {
-    const double mc = __shfl_sync(0xFFFFFFFFu, m, cc * G);
-    const int vc = __shfl_sync(0xFFFFFFFFu, valid ? 1 : 0, cc * G);
+    const double mc = __shfl_sync(0xFFFFFFFFu, m, base + cc * G);
+    const int vc = __shfl_sync(0xFFFFFFFFu, valid ? 1 : 0, base + cc * G);
     if (!vc) continue;
     if (ch.nvalid == 0 || mc > ch.best_m) {
       if (ch.nvalid > 0) ch.second_m = ch.best_m;
@@ -284,14 +293,32 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& 
   return ch;
 }
 
+// One scan per sub-warp of SW lanes: SW = 32, a warp per scan; SW = 8, four
+// scans per warp. A scan's float32 point sums spread over its sub-warp's
+// lanes, while the float64 finishing (one division per box, Eq. 5, Eq. 6-7)
+// of all of a warp's scans runs as one instruction stream: float64 is this
+// GPU's slow pipe, and with one scan per warp every lane repeats its scan's
+// scalar finishing. A sub-warp without a scan to run (past the batch,
+// skipped, no target, or stopped earlier than the others) keeps taking part
+// in the shuffles on empty boxes, with its results and stores switched off.
+template <int SW>
 __global__ void __launch_bounds__(256) k_select(const SelParams P) {
-  const int lane = threadIdx.x & 31;
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (s >= P.B) return;
-  if (P.skip && P.skip[s]) return;
-  // this scan's lattice and grid
+  const int lane = threadIdx.x & 31, sl = lane & (SW - 1), base = lane - sl;
+  const int s = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) / SW);
+  const bool in = s < P.B && !(P.skip && P.skip[s]);
+  // this scan's lattice and grid (an empty lattice for a sub-warp without one)
   SelScan Q;
-  if (P.scans) {
+  if (!in) {
+    Q.prof_off = 0;
+    for (int a = 0; a < 3; ++a) {
+      Q.gn[a] = 1;
+      Q.off[a] = 0;
+      Q.step[a] = 1;
+      Q.cnt[a] = 0;
+    }
+    Q.D = 1;
+    Q.max_iters = 0;
+  } else if (P.scans) {
     Q = P.scans[s];
   } else {
     Q.prof_off = static_cast<long long>(s) * P.prof_stride;
@@ -305,28 +332,30 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     Q.max_iters = P.max_iters;
   }
   const float* prof = P.profile + Q.prof_off;
-  uwb_result* R = P.out + s;
-  LatBox* box = P.boxes + s;
+  uwb_result* R = P.out + (in ? s : 0);
+  LatBox* box = P.boxes + (in ? s : 0);
 
   // clear the result record
-  {
+  if (in) {
     int* w = reinterpret_cast<int*>(R);
-    for (int j = lane; j < static_cast<int>(sizeof(uwb_result) / 4); j += 32) w[j] = 0;
-    __syncwarp();
+    for (int j = sl; j < static_cast<int>(sizeof(uwb_result) / 4); j += SW) w[j] = 0;
   }
+  __syncwarp();
   const long long Pd = static_cast<long long>(Q.cnt[0]) * Q.cnt[1] * Q.cnt[2];
   float fmx = 0.f;
-  bool bad = false;
-  for (long long j = lane; j < Pd; j += 32) {
+  int bad = 0;
+  for (long long j = sl; j < Pd; j += SW) {
     const float v = prof[j];
     bad |= !isfinite(v);
     fmx = fmaxf(fmx, v);
   }
-  bad = __any_sync(0xFFFFFFFFu, bad);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) fmx = fmaxf(fmx, __shfl_xor_sync(0xFFFFFFFFu, fmx, o));
+  for (int o = SW / 2; o > 0; o >>= 1) {
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, o);
+    fmx = fmaxf(fmx, __shfl_xor_sync(0xFFFFFFFFu, fmx, o));
+  }
 
-  if (lane == 0) {
+  if (in && sl == 0) {
     R->decim = Q.D;
     for (int a = 0; a < 3; ++a) {
       R->offset[a] = Q.off[a];
@@ -334,9 +363,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       R->loc_idx[a] = -1;
     }
     R->profile_max = fmx;
-  }
-  if (bad || fmx == 0.f) {
-    if (lane == 0) {
+    if (bad || fmx == 0.f) {
       R->status = bad ? UWB_ERR_NONFINITE : UWB_OK;
       R->stop_reason = bad ? UWB_STOP_NONE : UWB_STOP_NO_TARGET;
       for (int a = 0; a < 3; ++a) {
@@ -346,50 +373,47 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       }
       box->tiles = 0;
     }
-    return;
   }
-  const Norm nm = make_norm(fmx);
+  const bool live = in && !bad && fmx != 0.f;
+  if (!__any_sync(0xFFFFFFFFu, live)) return;
+  const Norm nm = make_norm(live ? fmx : 1.f);
   const int dim = P.dim;
   const uwb_rule& rule = P.rule;
 
   int Rlo[3] = {0, 0, 0}, Rhi[3] = {Q.gn[0], Q.gn[1], Q.gn[2]};
-  Stats sa = box_stats(Q, prof, nm, lattice_in_box(Q, Rlo, Rhi));
+  Stats sa = box_stats<SW>(Q, prof, nm, lattice_in_box(Q, Rlo, Rhi), sl);
   double var_prev = sa.var;
   double B_prev = 0.0, W_prev = 0.0;
   int iters = 0, n_logged = 0, stop = UWB_STOP_NONE;
+  bool run = live && Q.max_iters >= 1;
 
-  for (int i = 1; i <= Q.max_iters; ++i) {
+  for (int i = 1; __any_sync(0xFFFFFFFFu, run); ++i) {
     const int li = i - 1;
-    const Choice ch = choose_child(Q, prof, nm, Rlo, Rhi, dim, rule, var_prev);
+    const Choice ch = choose_child<SW>(Q, prof, nm, Rlo, Rhi, dim, rule, var_prev, sl, base);
     const int best = ch.best, nvalid = ch.nvalid;
     const double best_m = ch.best_m, second_m = ch.second_m;
-    int blo[3], bhi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      blo[a] = ch.blo[a];
-      bhi[a] = ch.bhi[a];
-    }
-    if (nvalid == 0) {
+    if (run && nvalid == 0) {
       stop = UWB_STOP_MINSIZE;
       iters = i - 1;
-      break;
+      run = false;
     }
     // sliding framing of the chosen child
     int Nlo[3], Nhi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a < dim) {
-        const int side = bhi[a] - blo[a];
+        const int side = ch.bhi[a] - ch.blo[a];
         const int grow = (side * rule.frame_num + rule.frame_den - 1) / rule.frame_den;
-        Nlo[a] = max(blo[a] - grow, 0);
-        Nhi[a] = min(bhi[a] + grow, Q.gn[a]);
+        Nlo[a] = max(ch.blo[a] - grow, 0);
+        Nhi[a] = min(ch.bhi[a] + grow, Q.gn[a]);
       } else {
-        Nlo[a] = blo[a];
-        Nhi[a] = bhi[a];
+        Nlo[a] = ch.blo[a];
+        Nhi[a] = ch.bhi[a];
       }
     }
     // Eq. 6-7 between the regions of consecutive iterations
-    const Stats sb = box_stats(Q, prof, nm, lattice_in_box(Q, Nlo, Nhi));
+    const Stats sb = box_stats<SW>(Q, prof, nm, lattice_in_box(Q, Nlo, Nhi), sl);
+    if (!run) continue;
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
@@ -401,7 +425,7 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
       cont = (Bi > B_prev) && (Wi < W_prev);
       margin = cont ? fmin(mB, mW) : fmax(-mB, -mW);
     }
-    if (lane == 0) {
+    if (sl == 0) {
       R->child[li] = best;
       R->n_children[li] = nvalid;
       R->metric_top[li] = best_m;
@@ -418,7 +442,8 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     if (!cont) {
       stop = UWB_STOP_METRIC;
       iters = i - 1;
-      break;
+      run = false;
+      continue;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -432,10 +457,10 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     iters = i;
     if (i == Q.max_iters) {
       stop = UWB_STOP_CAP;
-      break;
+      run = false;
     }
   }
-  if (lane == 0) {
+  if (live && sl == 0) {
     R->status = UWB_OK;
     R->iters = iters;
     R->n_logged = n_logged;
@@ -585,9 +610,9 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       return;
     }
   }
-  const Stats sr = box_stats(Qc, cv, nm, lattice_in_box(Qc, Rlo, Rhi));
+  const Stats sr = box_stats<32>(Qc, cv, nm, lattice_in_box(Qc, Rlo, Rhi), lane);
   const double var_prev = sr.var;
-  const Choice ch = choose_child(Qc, cv, nm, Rlo, Rhi, dim, rule, var_prev);
+  const Choice ch = choose_child<32>(Qc, cv, nm, Rlo, Rhi, dim, rule, var_prev, lane, 0);
   const int best = ch.best, nvalid = ch.nvalid;
   const double best_m = ch.best_m, second_m = ch.second_m;
   int blo[3], bhi[3];
@@ -618,8 +643,8 @@ __global__ void __launch_bounds__(256) k_prog_step(const ProgParams P, int it) {
       }
     }
     // Eq. 6-7 on the decimated profile between the region and the framed child
-    const Stats sa = box_stats(Q0, prof, nm, lattice_in_box(Q0, Rlo, Rhi));
-    const Stats sb = box_stats(Q0, prof, nm, lattice_in_box(Q0, Nlo, Nhi));
+    const Stats sa = box_stats<32>(Q0, prof, nm, lattice_in_box(Q0, Rlo, Rhi), lane);
+    const Stats sb = box_stats<32>(Q0, prof, nm, lattice_in_box(Q0, Nlo, Nhi), lane);
     const double Wi = sa.scatter + sb.scatter;
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
@@ -815,9 +840,18 @@ __global__ void k_keys_to_index(unsigned long long* keys, int B) {
 
 }  // namespace
 
+// Four scans per warp for large uniform batches of small profiles (a lane's
+// share of a scan's points stays short); otherwise a warp per scan. Packed
+// warps run as CTAs of one warp, so that the few warps of a batch spread
+// evenly over the SMs.
 cudaError_t launch_select(const SelParams& p, cudaStream_t st) {
-  const int warps = 8;
-  k_select<<<(p.B + warps - 1) / warps, warps * 32, 0, st>>>(p);
+  const long long Pd = static_cast<long long>(p.cnt[0]) * p.cnt[1] * p.cnt[2];
+  if (!p.scans && p.B >= kSelectPackedMinScans && Pd <= kSelectPackedMaxPoints) {
+    k_select<8><<<(p.B + 3) / 4, 32, 0, st>>>(p);
+  } else {
+    const int warps = 8;
+    k_select<32><<<(p.B + warps - 1) / warps, warps * 32, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 

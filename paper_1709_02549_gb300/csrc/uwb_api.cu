@@ -785,7 +785,7 @@ int localize_core(const Geo& geo, const float* traces, const float* ant, long lo
 
   timer.mark();
 
-  // 2. ROI selection loop (Section III, "ROI Selection"), one warp per scan
+  // 2. ROI selection loop (Section III, "ROI Selection"), a warp or a quarter warp per scan
   SelParams sp;
   memset(&sp, 0, sizeof sp);
   sp.profile = profile;

@@ -177,7 +177,7 @@ struct FinScan {
   long long Pd;              // decimated points
 };
 
-// Segment-selection inputs (one warp per scan).
+// Segment-selection inputs (one warp, or a quarter warp, per scan).
 struct SelParams {
   const SelScan* scans;      // ragged: [B] (device), else nullptr
   const float* profile;      // [B][Pd] decimated energies, lattice order (x fastest)

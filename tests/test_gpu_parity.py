@@ -193,6 +193,54 @@ def test_benchmark_batch_sampled_scans_match_oracle(gpu):
     assert ties <= 1, f"{ties} near-ties in 6 sampled scans"
 
 
+@pytest.mark.parametrize("bf", [0, 1])
+def test_packed_selection_batch_matches_oracle(gpu, bf):
+    """A batch large enough for the selection kernel's packed form (four scans
+    per warp in 8-lane sub-warps, batches of at least 2048 scans of at most
+    4096 decimated points): 2050 scans of the 64 x 64 workload, so that the
+    last warp holds two scans and two idle sub-warps. A zero scan and a scan
+    with a non-finite sample sit in packed warps beside scans that run.
+    Sampled scans at every sub-warp position must match the oracle one by
+    one; and on every scan the packed form must take the decisions of the
+    one-warp-per-scan form (the same batch minus its last three scans)."""
+    cfg = phantom.CONFIGS["das2d_64"]
+    B = 2050
+    batch = phantom.make_batch(cfg, B, first_scan=0)
+    traces = batch["traces"].copy()
+    traces[1] = 0.0
+    traces[6, 3, 100] = np.nan
+    ants, grid = batch["antennas"], cfg.grid()
+    g_rule, o_rule = rule_pair(gpu)
+    packed = gpu_localize_batch(gpu, bf, traces, ants, grid, cfg.v, cfg.fs, cfg.window, g_rule)
+    assert packed[1]["stop_reason"] == oracle.STOP_NO_TARGET and packed[1]["status"] == 0
+    assert packed[6]["status"] == -4
+    assert all(packed[s]["status"] == 0 for s in range(B) if s != 6)
+    ties = 0
+    for s in (0, 1, 2, 3, 5, 6, 7, 1001, 1234, 2047, 2048, 2049):
+        scan = OracleScan(traces[s], ants, grid, cfg.v, cfg.fs, cfg.window, bf, o_rule)
+        ties += compare_localize(packed[s], scan)["tie"]
+    assert ties <= 2, f"{ties} near-ties in 12 sampled scans"
+    # the same scans below the packed form's batch size
+    plain = gpu_localize_batch(gpu, bf, traces[:2047], ants, grid, cfg.v, cfg.fs, cfg.window,
+                               g_rule)
+    differ = []
+    for s in range(2047):
+        a, b = packed[s], plain[s]
+        same = all(a[k] == b[k] for k in ("status", "stop_reason", "iters", "n_logged", "child",
+                                          "box_lo", "box_hi", "roi_lo", "roi_hi", "loc_idx"))
+        if not same:
+            differ.append(s)
+            continue
+        for k in ("metric_top", "between", "within"):
+            np.testing.assert_allclose(a[k], b[k], rtol=1e-12, err_msg=f"scan {s} {k}")
+    # decisions may part only where a metric gap or stop margin is at the level
+    # of the sums' rounding (about 1e-14)
+    for s in differ:
+        gaps = [abs(x) for x in plain[s]["metric_gap"] + plain[s]["stop_margin"]]
+        assert min(gaps) < 1e-9, f"scan {s}: decisions differ without a near-tie"
+    assert len(differ) <= 2
+
+
 def test_localize_writes_the_mixed_resolution_image(gpu):
     cfg = phantom.CONFIGS["das2d_64"]
     sc = phantom.make_scan(cfg, phantom.BASE_SEED + 2)
