@@ -85,9 +85,9 @@ def peak_source(kind: str) -> str:
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "8b5174503194e713", "bytes_per_scan": 9015808 / 256},
-    1: {"sha": "8b5174503194e713", "bytes_per_scan": 9329920 / 256},
-    2: {"sha": "8b5174503194e713", "bytes_per_scan": 6724608 / 256},
+    0: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 9063936 / 256},
+    1: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 9381888 / 256},
+    2: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 6724352 / 256},
 }
 
 
