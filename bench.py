@@ -423,14 +423,14 @@ def run_presence(args, cfg, bf, uwb, torch):
             "confirmed_rate": rates, "gpu_launches": 11 * args.steps}
 
 
-def run_ragged(args, uwb, torch, graph_replay=False):
+def run_ragged(args, uwb, torch, graph_replay=False, dtypes=("f32", "f16", "bf16")):
     """Uneven scans (16-96 antennas, 1024-4096 samples, 128^2-1024^2 grids) in one
     plan per element type: localised scans/s after tile autotuning, full-resolution
     images of the same scans, and each image's error against the FP64 oracle at
-    sampled focal points (traces stored in float32, float16, bfloat16). With
-    graph_replay, the float32 plan's localisation is also captured in a CUDA
-    graph and its replays timed (and their records compared with the direct
-    launches')."""
+    sampled focal points (traces stored in each of `dtypes`: float32, float16,
+    bfloat16). With graph_replay, the float32 plan's localisation is also captured
+    in a CUDA graph and its replays timed (and their records compared with the
+    direct launches')."""
     import oracle
     oracle.build()
     B = args.batch
@@ -458,6 +458,8 @@ def run_ragged(args, uwb, torch, graph_replay=False):
                       "points_total": int(sum(np.prod(c.grid_n) for c in cfgs))},
            "by_dtype": {}}
     for name, tdt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+        if name not in dtypes:
+            continue
         specs = [{"traces": t.to(tdt).contiguous(), "antennas": a, "grid": c.grid(), "v": c.v,
                   "fs": c.fs} for t, a, c in zip(dev_tr, dev_an, cfgs)]
         plan = uwb.UwbPlan(specs, cfgs[0].window, bf, rule)
@@ -941,7 +943,8 @@ def measure_extras(args, cfg, bf, uwb, torch, batch, traces, flush, stream, fma_
     the headline's timed region: the learned segment proposal on the headline's
     own scans; the 256^3 hemispherical workload (literal and identity DMAS);
     the 64^2 DAS workload; the uneven batch through the plan API (FP32, FP16,
-    BF16 traces) with a CUDA-graph replay."""
+    BF16 traces) with a CUDA-graph replay, and with literal pairs over its 16-96
+    antennas (FP32 traces)."""
     import copy
     extra = {}
     a = copy.copy(args)
@@ -970,6 +973,12 @@ def measure_extras(args, cfg, bf, uwb, torch, batch, traces, flush, stream, fma_
     clocks.start()
     extra["ragged"] = run_ragged(r, uwb, torch, graph_replay=True)
     extra["ragged"]["clocks"] = clocks.stop()
+    r = copy.copy(r)
+    r.ragged_literal = True
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    extra["ragged_literal"] = run_ragged(r, uwb, torch, dtypes=("f32",))
+    extra["ragged_literal"]["clocks"] = clocks.stop()
     return extra
 
 
