@@ -241,6 +241,36 @@ def test_packed_selection_batch_matches_oracle(gpu, bf):
     assert len(differ) <= 2
 
 
+def test_packed_selection_three_d_matches_oracle(gpu):
+    """The packed selection in 3-D, where each of a scan's 8 lanes scores one
+    of the 8 children alone: 2048 scans of a 32^3 grid (16^3 = 4096 decimated
+    points, the packed form's limit), sampled against the oracle and compared
+    decision by decision with the one-warp-per-scan form."""
+    cfg = phantom.with_changes(phantom.CONFIGS["hemi3d_256"], grid_n=(32, 32, 32),
+                               n_antennas=16, n_samples=1024, n_clutter=10)
+    B = 2048
+    batch = phantom.make_batch(cfg, B, first_scan=0)
+    traces, ants, grid = batch["traces"], batch["antennas"], cfg.grid()
+    g_rule, o_rule = rule_pair(gpu, min_segment=2)
+    packed = gpu_localize_batch(gpu, 0, traces, ants, grid, cfg.v, cfg.fs, cfg.window, g_rule)
+    assert packed[0]["dcount"] == [16, 16, 16]
+    assert all(r["status"] == 0 for r in packed)
+    ties = 0
+    for s in (0, 1, 2, 3, 777, 2046, 2047):
+        scan = OracleScan(traces[s], ants, grid, cfg.v, cfg.fs, cfg.window, 0, o_rule)
+        ties += compare_localize(packed[s], scan)["tie"]
+    assert ties <= 2, f"{ties} near-ties in 7 sampled scans"
+    plain = gpu_localize_batch(gpu, 0, traces[:B - 1], ants, grid, cfg.v, cfg.fs, cfg.window,
+                               g_rule)
+    differ = [s for s in range(B - 1)
+              if any(packed[s][k] != plain[s][k] for k in ("stop_reason", "iters", "child",
+                                                            "box_lo", "box_hi", "loc_idx"))]
+    for s in differ:
+        gaps = [abs(x) for x in plain[s]["metric_gap"] + plain[s]["stop_margin"]]
+        assert min(gaps) < 1e-9, f"scan {s}: decisions differ without a near-tie"
+    assert len(differ) <= 2
+
+
 def test_localize_writes_the_mixed_resolution_image(gpu):
     cfg = phantom.CONFIGS["das2d_64"]
     sc = phantom.make_scan(cfg, phantom.BASE_SEED + 2)
