@@ -71,6 +71,10 @@ extern "C" {
 #define UWB_ERR_NONFINITE -4    /* NaN or Inf in the decimated energy profile */
 #define UWB_ERR_UNSUPPORTED -5  /* sizes outside what this build handles */
 #define UWB_ERR_WORKSPACE -6    /* workspace missing, misaligned or too small */
+#define UWB_ERR_BOUNDS -7       /* bounds-checked builds only (compiled with -DUWB_CHECK): an image
+                                   kernel computed a staged-window, image or profile index outside
+                                   its buffer; the access was redirected inside it and the call's
+                                   outputs are invalid */
 
 /* beamformers */
 #define UWB_DAS 0
@@ -368,7 +372,12 @@ int uwb_localize_batch_noalloc(int batch, const float* traces, int M, int N,
  * While enabled, each call records CUDA events on its own stream around its
  * phases: 0 = decimated energy profile, 1 = segment selection and work
  * planning, 2 = final-region imaging, 3 = result decoding. The events add no
- * work to the kernels. uwb_phase_timing(1) switches timing on and discards
+ * work to the kernels. Whether timing is on or not, the localisation calls
+ * (batch, plan, learned, progressive) also open an NVTX range per phase
+ * ("uwb decimated profile", "uwb selection", "uwb final region", "uwb
+ * decode"; the learned call's first two are "uwb learned proposal" and "uwb
+ * fallback selection") around the host calls that enqueue it, for a profiler
+ * attached to the process (ncu --nvtx). uwb_phase_timing(1) switches timing on and discards
  * earlier records; uwb_phase_timing(0) switches it off. uwb_phase_times waits
  * for the recorded events, writes the summed milliseconds of each phase into
  * ms[0..3], forgets the records and returns how many calls they covered (or a

@@ -9,6 +9,7 @@ There is no CPU fallback: if the library is not built, loading fails loudly.
 from __future__ import annotations
 
 import ctypes
+import os
 import pathlib
 
 import numpy as np
@@ -26,11 +27,16 @@ __all__ = [
     "UwbError",
 ]
 
-LIB_PATH = pathlib.Path(__file__).resolve().parent / "libuwb.so"
+# UWB_LIBRARY=checked loads the bounds-checked build (build(checked=True))
+_LIB_NAMES = {"": "libuwb.so", "checked": "libuwb_checked.so"}
+if os.environ.get("UWB_LIBRARY", "") not in _LIB_NAMES:
+    raise RuntimeError(f"UWB_LIBRARY={os.environ['UWB_LIBRARY']!r}: expected 'checked' or unset")
+LIB_PATH = pathlib.Path(__file__).resolve().parent / _LIB_NAMES[os.environ.get("UWB_LIBRARY", "")]
 
 UWB_OK = 0
 UWB_ERR_ARG, UWB_ERR_CUDA, UWB_ERR_TIMEOUT = -1, -2, -3
 UWB_ERR_NONFINITE, UWB_ERR_UNSUPPORTED, UWB_ERR_WORKSPACE = -4, -5, -6
+UWB_ERR_BOUNDS = -7
 UWB_DAS, UWB_DMAS, UWB_DMAS_LITERAL = 0, 1, 2
 UWB_DECIM_MANUAL, UWB_DECIM_AUTO = 0, 1
 UWB_METRIC_HYBRID, UWB_METRIC_MEAN, UWB_METRIC_VARIANCE, UWB_METRIC_HYBRID_UNCLIPPED = 0, 1, 2, 3

@@ -1,4 +1,9 @@
-"""Builds libuwb.so in-tree with nvcc for sm_103a (translation units in parallel)."""
+"""Builds libuwb.so in-tree with nvcc for sm_103a (translation units in parallel).
+
+build(checked=True) builds libuwb_checked.so beside it, compiled with
+-DUWB_CHECK: the image kernels check every staged-window run, image index and
+profile index they compute and record UWB_ERR_BOUNDS instead of leaving their
+buffers (the package loads it when UWB_LIBRARY=checked)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +18,8 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 BUILD = ROOT / "_build"
 LIB = PKG / "libuwb.so"
+BUILD_CHECKED = ROOT / "_build_checked"
+LIB_CHECKED = PKG / "libuwb_checked.so"
 SOURCES = ["uwb_api.cu", "select_kernels.cu", "image_das.cu", "image_dmas.cu",
            "image_literal.cu", "cnn.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -33,15 +40,17 @@ def _newest_input() -> float:
     return max(f.stat().st_mtime for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> pathlib.Path:
-    if LIB.exists() and not force and LIB.stat().st_mtime >= _newest_input():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> pathlib.Path:
+    lib, build_dir = (LIB_CHECKED, BUILD_CHECKED) if checked else (LIB, BUILD)
+    flags = FLAGS + (["-DUWB_CHECK"] if checked else [])
+    if lib.exists() and not force and lib.stat().st_mtime >= _newest_input():
+        return lib
     nvcc = _nvcc()
-    BUILD.mkdir(exist_ok=True)
+    build_dir.mkdir(exist_ok=True)
 
     def compile_one(src: str) -> pathlib.Path:
-        obj = BUILD / (src.replace(".cu", ".o"))
-        cmd = [nvcc, *FLAGS, "-c", str(CSRC / src), "-o", str(obj)]
+        obj = build_dir / (src.replace(".cu", ".o"))
+        cmd = [nvcc, *flags, "-c", str(CSRC / src), "-o", str(obj)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -51,13 +60,13 @@ def build(force: bool = False, verbose: bool = False) -> pathlib.Path:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB.with_suffix(f".so.{os.getpid()}.tmp")
+    tmp = lib.with_suffix(f".so.{os.getpid()}.tmp")
     cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -122,6 +122,31 @@ __device__ __forceinline__ float sample_at(const ScanDesc& S, int dtype, int i, 
   return ld_trace(S.traces, static_cast<long long>(i) * S.pitch + o, dtype);
 }
 
+// Bounds-checked builds (nvcc -DUWB_CHECK, the library's stand-in for a
+// memory checker): the first index of every run of `count` elements a kernel
+// is about to read or write in a buffer of n elements is checked; a run that
+// leaves the buffer records UWB_ERR_BOUNDS in the status word and is moved
+// to index 0, so the access stays inside the buffer. Other builds return the
+// index unchanged, and the checks compile away.
+__device__ __forceinline__ int check_run(int* status, int first, int count, int n) {
+#ifdef UWB_CHECK
+  if (first < 0 || first > n - count) {
+    atomicExch(status, UWB_ERR_BOUNDS);
+    return 0;
+  }
+#endif
+  return first;
+}
+__device__ __forceinline__ long long check_run64(int* status, long long first, long long n) {
+#ifdef UWB_CHECK
+  if (first < 0 || first >= n) {
+    atomicExch(status, UWB_ERR_BOUNDS);
+    return 0;
+  }
+#endif
+  return first;
+}
+
 // -------------------------------------------------------------- DAS / DMAS-identity
 // Rows are the M antennas (monostatic: delay 2|r - a_i| fs / v) or, with MS,
 // the R channels (transmitter, receiver) of a multistatic recording (Eq. 2:
@@ -174,7 +199,8 @@ __device__ __forceinline__ float energy_sum(const ImgParams& P, const ScanDesc* 
       float y[WT + 1];
       if (STAGED) {
         n0 = min(max(n0, cl_lo), cl_hi);
-        const float* row = sTr + i * P.span + (n0 - nlo);
+        const float* row =
+            sTr + check_run(P.status, i * P.span + (n0 - nlo), WT + 1, P.Rcap * P.span);
 #pragma unroll
         for (int k = 0; k <= WT; ++k) y[k] = row[k];
       } else {
@@ -285,8 +311,10 @@ __device__ __forceinline__ float2 energy_sum_pair(const ImgParams& P,
       const float2 f = __ffma2_rn(fl, m1, t);
       const int nx = min(max(static_cast<int>(fl.x), cl_lo), cl_hi);
       const int ny = min(max(static_cast<int>(fl.y), cl_lo), cl_hi);
-      const float* rx = sTr + i * P.span + (nx - nlo);
-      const float* ry = sTr + i * P.span + (ny - nlo);
+      const float* rx =
+          sTr + check_run(P.status, i * P.span + (nx - nlo), WT + 1, P.Rcap * P.span);
+      const float* ry =
+          sTr + check_run(P.status, i * P.span + (ny - nlo), WT + 1, P.Rcap * P.span);
       float2 y[WT + 1];
 #pragma unroll
       for (int k = 0; k <= WT; ++k) y[k] = make_float2(rx[k], ry[k]);
@@ -403,9 +431,11 @@ __device__ __forceinline__ float energy_literal(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
+      // the passes read the words [first, first + wpad] of the row
       if (STAGED)
         n0 = static_cast<int>(smem_u32(sTr)) +
-             4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
+             4 * check_run(P.status, min(max(n0, cl_lo), cl_hi) - nlo + i * P.span, P.wpad + 1,
+                           MMAX * P.span);
     } else if (STAGED) {
       // rows M..MMAX-1 of the staged window are zero
       n0 = static_cast<int>(smem_u32(sTr)) + 4 * i * P.span;
@@ -506,9 +536,11 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
       const float fl = floorf(t);
       f = t - fl;
       n0 = static_cast<int>(fl);
+      // the passes read the words [first, first + wpad] of the row
       if (STAGED)
         n0 = static_cast<int>(smem_u32(sTr)) +
-             4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
+             4 * check_run(P.status, min(max(n0, cl_lo), cl_hi) - nlo + i * P.span, P.wpad + 1,
+                           MMAX * P.span);
     } else if (STAGED) {
       // rows M..MMAX-1 of the staged window are zero
       n0 = static_cast<int>(smem_u32(sTr)) + 4 * i * P.span;
@@ -568,7 +600,7 @@ __device__ __forceinline__ float energy_literal4(const ImgParams& P,
 // Shared-window byte address (staged) or absolute sample index (global path)
 // of sample 0 of antenna i's window for this focal point, and its fraction:
 // the same arithmetic as energy_literal's table.
-template <bool STAGED>
+template <int ROWS, bool STAGED>
 __device__ __forceinline__ int lit_delay(const ImgParams& P, const float4* __restrict__ sAnt,
                                          int i, float px, float py, float pz, float kscale,
                                          float hf, uint32_t base, int nlo, int cl_lo, int cl_hi,
@@ -582,7 +614,11 @@ __device__ __forceinline__ int lit_delay(const ImgParams& P, const float4* __res
   const float fl = floorf(t);
   f = t - fl;
   const int n0 = static_cast<int>(fl);
-  if (STAGED) return static_cast<int>(base) + 4 * (min(max(n0, cl_lo), cl_hi) - nlo + i * P.span);
+  // a window pair's passes read the words [first, first + wpad] of the row
+  if (STAGED)
+    return static_cast<int>(base) + 4 * check_run(P.status,
+                                                  min(max(n0, cl_lo), cl_hi) - nlo + i * P.span,
+                                                  P.wpad + 1, ROWS * P.span);
   return n0;
 }
 
@@ -633,7 +669,7 @@ __device__ __forceinline__ float energy_literal_blocks(const ImgParams& P,
       // the held block: its own pairs, streamed one antenna ahead
       float2 xa[32];
       float fn;
-      int an = lit_delay<STAGED>(P, sAnt, ia, px, py, pz, kscale, hf, base, nlo, cl_lo, cl_hi,
+      int an = lit_delay<32 * NB, STAGED>(P, sAnt, ia, px, py, pz, kscale, hf, base, nlo, cl_lo, cl_hi,
                                  fn);
       float2 xn = lit_pair<STAGED>(P, sS, ia, an, fn, k0);
 #pragma unroll
@@ -641,7 +677,7 @@ __device__ __forceinline__ float energy_literal_blocks(const ImgParams& P,
         if (j < na) {
           const float2 x = xn;
           if (j + 1 < na) {
-            an = lit_delay<STAGED>(P, sAnt, ia + j + 1, px, py, pz, kscale, hf, base, nlo, cl_lo,
+            an = lit_delay<32 * NB, STAGED>(P, sAnt, ia + j + 1, px, py, pz, kscale, hf, base, nlo, cl_lo,
                                    cl_hi, fn);
             xn = lit_pair<STAGED>(P, sS, ia + j + 1, an, fn, k0);
           }
@@ -662,7 +698,7 @@ __device__ __forceinline__ float energy_literal_blocks(const ImgParams& P,
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float fq;
-          const int aq = lit_delay<STAGED>(P, sAnt, j0 + q, px, py, pz, kscale, hf, base, nlo,
+          const int aq = lit_delay<32 * NB, STAGED>(P, sAnt, j0 + q, px, py, pz, kscale, hf, base, nlo,
                                            cl_lo, cl_hi, fq);
           xq[q] = lit_pair<STAGED>(P, sS, j0 + q, aq, fq, k0);
         }
@@ -685,7 +721,7 @@ __device__ __forceinline__ float energy_literal_blocks(const ImgParams& P,
 #pragma unroll 1
       for (; jb < M; ++jb) {
         float fr;
-        const int ar = lit_delay<STAGED>(P, sAnt, jb, px, py, pz, kscale, hf, base, nlo, cl_lo,
+        const int ar = lit_delay<32 * NB, STAGED>(P, sAnt, jb, px, py, pz, kscale, hf, base, nlo, cl_lo,
                                          cl_hi, fr);
         const float2 x = lit_pair<STAGED>(P, sS, jb, ar, fr, k0);
 #pragma unroll
@@ -1158,11 +1194,18 @@ __global__ void __launch_bounds__(KernelShape<BF, V, MS, RG>::threads,
 #pragma unroll
     for (int q = 0; q < PP; ++q) {
       if (!valid[q]) continue;
-      if (P.image) P.image[img_off + lin[q]] = energy[q];
+      if (P.image) {
+        const long long gp = static_cast<long long>(scan_gn<RG>(P, sS, 0)) *
+                             scan_gn<RG>(P, sS, 1) * scan_gn<RG>(P, sS, 2);
+        P.image[img_off + check_run64(P.status, lin[q], gp)] = energy[q];
+      }
       if (P.compact)
-        P.compact[cmp_off + kx[q] +
-                  static_cast<long long>(L.cnt[0]) *
-                      (ky[q] + static_cast<long long>(L.cnt[1]) * kz[q])] = energy[q];
+        P.compact[cmp_off +
+                  check_run64(P.status,
+                              kx[q] + static_cast<long long>(L.cnt[0]) *
+                                          (ky[q] + static_cast<long long>(L.cnt[1]) * kz[q]),
+                              static_cast<long long>(L.cnt[0]) * L.cnt[1] * L.cnt[2])] =
+            energy[q];
     }
     if (P.keys) {
       // larger energy wins; equal energies -> lower linear index wins

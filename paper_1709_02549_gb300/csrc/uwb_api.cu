@@ -2,6 +2,7 @@
 // layout, TMA descriptor encoding, tile/warp shape choice and the launch
 // sequence of the device-resident segment search.
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -108,12 +109,23 @@ void drop_records() {
   g_phase_records.clear();
 }
 
-// Events of one call, or nullptr when timing is off.
+// Phase names of the NVTX ranges (a profiler attached to the process shows
+// them; without one the calls return at once).
+const char* const kLocalizePhases[kPhases] = {"uwb decimated profile", "uwb selection",
+                                              "uwb final region", "uwb decode"};
+const char* const kLearnedPhases[kPhases] = {"uwb learned proposal", "uwb fallback selection",
+                                             "uwb final region", "uwb decode"};
+
+// Events of one call (when timing is on) and an NVTX range per phase: mark()
+// ends the phase that is open and opens the next.
 struct PhaseTimer {
   PhaseEvents pe;
   bool on = false;
   int next = 0;
-  explicit PhaseTimer(cudaStream_t st) : stream(st) {
+  int range = 0;  // NVTX ranges opened so far
+  const char* const* names;
+  explicit PhaseTimer(cudaStream_t st, const char* const* phase_names = kLocalizePhases)
+      : names(phase_names), stream(st) {
     std::lock_guard<std::mutex> lk(g_timing_mu);
     if (!g_timing) return;
     for (int i = 0; i <= kPhases; ++i)
@@ -125,6 +137,9 @@ struct PhaseTimer {
     on = true;
   }
   void mark() {
+    if (range > 0 && range <= kPhases) nvtxRangePop();
+    if (range < kPhases) nvtxRangePushA(names[range]);
+    ++range;
     if (on && next <= kPhases) cudaEventRecord(pe.ev[next++], stream);
   }
   void commit() {
@@ -138,6 +153,7 @@ struct PhaseTimer {
     on = false;
   }
   ~PhaseTimer() {
+    if (range > 0 && range <= kPhases) nvtxRangePop();  // a call that left early
     if (on)
       for (auto e : pe.ev) cudaEventDestroy(e);
   }
@@ -2104,7 +2120,7 @@ int uwb_localize_learned(int batch, const float* traces, int M, int N, const flo
   const int tma_m = encode_traces(geo, traces, span_m, &map_m);
   const int tma_f = encode_traces(geo, traces, span, &map_f);
   const int ctas = cnn_ctas(*dev, batch);
-  PhaseTimer timer(cs);
+  PhaseTimer timer(cs, kLearnedPhases);
   timer.mark();
 
   cnn::LearnParams lp;

@@ -14,10 +14,12 @@ import pytest
 @pytest.fixture(scope="session")
 def uwb():
     """The CUDA library's Python binding, built in-tree if needed (nvcc
-    cross-compiles without a GPU)."""
+    cross-compiles without a GPU); with UWB_LIBRARY=checked, the bounds-checked
+    build."""
+    import os
     from paper_1709_02549_gb300 import build
     try:
-        build.build()
+        build.build(checked=os.environ.get("UWB_LIBRARY") == "checked")
     except RuntimeError as e:  # no nvcc on this machine
         pytest.skip(f"libuwb.so cannot be built here: {e}")
     import paper_1709_02549_gb300 as u

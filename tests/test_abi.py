@@ -157,7 +157,8 @@ def _header_define(name):
     text = (ROOT / "include" / "uwb.h").read_text()
     m = re.search(r"#define\s+" + name + r"\s+(.+)", text)
     assert m, name
-    return eval(re.sub(r"(\d+)u\b", r"\1", m.group(1)))
+    value = re.sub(r"/\*.*", "", m.group(1)).strip()  # a trailing comment
+    return eval(re.sub(r"(\d+)u\b", r"\1", value))
 
 
 def test_binding_constants_equal_the_header(uwb):
@@ -165,3 +166,6 @@ def test_binding_constants_equal_the_header(uwb):
     assert uwb.CNN_RECORD_BYTES == _header_define("UWB_CNN_RECORD_BYTES")
     assert uwb.CNN_PARAMS == _header_define("UWB_CNN_PARAMS")
     assert uwb.CNN_PACKED_BYTES == _header_define("UWB_CNN_PACKED_BYTES")
+    for name in ("UWB_OK", "UWB_ERR_ARG", "UWB_ERR_CUDA", "UWB_ERR_TIMEOUT", "UWB_ERR_NONFINITE",
+                 "UWB_ERR_UNSUPPORTED", "UWB_ERR_WORKSPACE", "UWB_ERR_BOUNDS"):
+        assert getattr(uwb, name) == _header_define(name), name
