@@ -85,9 +85,9 @@ def peak_source(kind: str) -> str:
 # of the kernel sources whose hash is stored alongside; reported as null once
 # the sources change.
 NCU_TRAFFIC = {
-    0: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 9063936 / 256},
-    1: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 9381888 / 256},
-    2: {"sha": "7dcd9182bd75030e", "bytes_per_scan": 6724352 / 256},
+    0: {"sha": "b176f87516651c22", "bytes_per_scan": 9014272 / 256},
+    1: {"sha": "b176f87516651c22", "bytes_per_scan": 9329408 / 256},
+    2: {"sha": "b176f87516651c22", "bytes_per_scan": 6728960 / 256},
 }
 
 
