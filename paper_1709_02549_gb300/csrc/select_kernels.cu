@@ -173,6 +173,8 @@ __device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, 
   Stats st;
   st.n = b.n;
   st.sum = st.mean = st.scatter = st.var = 0.0;
+  // the division first: its float64 latency passes during the point sums
+  const double rn = 1.0 / static_cast<double>(b.n > 0 ? b.n : 1);
   Acc2 a1, a2;
   lane_sums(P, prof, b, nm, sl, SW, a1, a2);
 #pragma unroll
@@ -181,7 +183,6 @@ __device__ Stats box_stats(const SelScan& P, const float* prof, const Norm& nm, 
     a2 = acc_merge(a2, acc_shfl_xor(a2, o));
   }
   if (b.n == 0) return st;
-  const double rn = 1.0 / static_cast<double>(b.n);
   st.sum = acc_value(a1) * nm.r;
   st.mean = st.sum * rn;
   st.scatter = fmax(acc_value(a2) * nm.r * nm.r - st.sum * st.mean, 0.0);
@@ -243,6 +244,7 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& 
     }
   }
   const KBox kb = lattice_in_box(Q, clo, chi);
+  const double rn = 1.0 / static_cast<double>(kb.n > 0 ? kb.n : 1);  // before the sums
   // this group's partial sums over child c
   Acc2 a1{0.f, 0.f}, a2{0.f, 0.f};
   if (ok) lane_sums(Q, vals, kb, nm, r, G, a1, a2);
@@ -253,7 +255,6 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& 
   double m = 0.0;
   const bool valid = ok && kb.n > 0;
   if (valid) {
-    const double rn = 1.0 / static_cast<double>(kb.n);
     const double sum = acc_value(a1) * nm.r;
     const double mean = sum * rn;
     const double scatter = fmax(acc_value(a2) * nm.r * nm.r - sum * mean, 0.0);
@@ -418,25 +419,20 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     const double pooled = (sa.sum + sb.sum) / static_cast<double>(sa.n + sb.n);
     const double Bi = static_cast<double>(sa.n) * (sa.mean - pooled) * (sa.mean - pooled) +
                       static_cast<double>(sb.n) * (sb.mean - pooled) * (sb.mean - pooled);
-    double margin = 1e300;
-    bool cont = true;
-    if (i >= 2) {
-      const double mB = rel_gap(Bi, B_prev), mW = rel_gap(W_prev, Wi);
-      cont = (Bi > B_prev) && (Wi < W_prev);
-      margin = cont ? fmin(mB, mW) : fmax(-mB, -mW);
-    }
+    // the stop test; its margin and the metric gap (divisions) are logged
+    // after the loop, off this chain of dependent float64 steps
+    const bool cont = i < 2 || ((Bi > B_prev) && (Wi < W_prev));
     if (sl == 0) {
       R->child[li] = best;
       R->n_children[li] = nvalid;
       R->metric_top[li] = best_m;
-      R->metric_gap[li] = nvalid > 1 ? rel_gap(best_m, second_m) : 1e300;
+      R->metric_gap[li] = second_m;  // the runner-up until the loop ends
       for (int a = 0; a < 3; ++a) {
         R->box_lo[li][a] = Nlo[a];
         R->box_hi[li][a] = Nhi[a];
       }
       R->within[li] = Wi;
       R->between[li] = Bi;
-      R->stop_margin[li] = margin;
     }
     n_logged = i;
     if (!cont) {
@@ -458,6 +454,24 @@ __global__ void __launch_bounds__(256) k_select(const SelParams P) {
     if (i == Q.max_iters) {
       stop = UWB_STOP_CAP;
       run = false;
+    }
+  }
+  // the logged margins, one iteration per lane: every logged iteration after
+  // the first followed an accepted one, so B_{i-1} and W_{i-1} are the
+  // previous entries
+  __syncwarp();
+  if (live) {
+    for (int li = sl; li < n_logged; li += SW) {
+      const double Bi = R->between[li], Wi = R->within[li];
+      double margin = 1e300;
+      if (li >= 1) {
+        const double B_prev = R->between[li - 1], W_prev = R->within[li - 1];
+        const double mB = rel_gap(Bi, B_prev), mW = rel_gap(W_prev, Wi);
+        margin = (Bi > B_prev) && (Wi < W_prev) ? fmin(mB, mW) : fmax(-mB, -mW);
+      }
+      R->stop_margin[li] = margin;
+      R->metric_gap[li] =
+          R->n_children[li] > 1 ? rel_gap(R->metric_top[li], R->metric_gap[li]) : 1e300;
     }
   }
   if (live && sl == 0) {
