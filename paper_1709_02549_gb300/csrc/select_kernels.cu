@@ -265,7 +265,11 @@ __device__ Choice choose_child(const SelScan& Q, const float* vals, const Norm& 
   ch.nvalid = 0;
   ch.best_m = ch.second_m = 0.0;
   for (int a = 0; a < 3; ++a) ch.blo[a] = ch.bhi[a] = 0;
-  for (int cc = 0; cc < nchild; ++cc) {
+  // unrolled over the most children (8), so that every shuffle is issued
+  // ahead of the compare chain
+#pragma unroll
+  for (int cc = 0; cc < 8; ++cc) {
+    if (cc >= nchild) break;
     const double mc = __shfl_sync(0xFFFFFFFFu, m, base + cc * G);
     const int vc = __shfl_sync(0xFFFFFFFFu, valid ? 1 : 0, base + cc * G);
     if (!vc) continue;
